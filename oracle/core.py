@@ -1,0 +1,144 @@
+"""ctypes wrapper around the FP64 CPU oracle (test infrastructure only).
+
+Only the tests, the smoke check and the benchmark's CPU-baseline leg use this
+module.  It drives ``gfdtd_oracle.c``, which follows Sec. 4 of the paper
+(Eqs. Farad_discr, Ampere_discr, Dconst_discr, Bconst_discr and Table 1) and,
+for moving matter, the star-form constitutive relations obtained from
+Eq. const_3d with the footnote tensors.  See the C file's header for the exact
+statement of every update.
+"""
+import ctypes as C
+import os
+from concurrent.futures import ThreadPoolExecutor
+
+import numpy as np
+
+from . import build as _build
+
+_dp = C.POINTER(C.c_double)
+
+
+class _Problem(C.Structure):
+    _fields_ = [("kind", C.c_int32), ("interp", C.c_int32), ("n", C.c_int32),
+                ("reserved", C.c_int32), ("z", _dp), ("eps", _dp), ("mu", _dp),
+                ("beta", C.c_double), ("S", C.c_double), ("nz", C.c_int64)]
+
+
+class _Source(C.Structure):
+    _fields_ = [("node", C.c_int64), ("omega0", C.c_double), ("tau", C.c_double),
+                ("t0", C.c_double), ("amp", C.c_double)]
+
+
+class _Probe(C.Structure):
+    _fields_ = [("node", C.c_int64), ("n_bins", C.c_int32), ("reserved", C.c_int32),
+                ("omega", _dp), ("re", _dp), ("im", _dp), ("series", _dp)]
+
+
+_lib = None
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        path = _build.build()
+        L = C.CDLL(path)
+        L.orc_run.restype = C.c_int
+        L.orc_run.argtypes = [C.POINTER(_Problem), C.c_int, C.POINTER(_Source), C.c_int,
+                              C.POINTER(_Probe), C.c_int64, C.c_int64, _dp, _dp]
+        L.orc_sample_material.restype = C.c_int
+        L.orc_sample_material.argtypes = [C.POINTER(_Problem), C.c_int, C.c_int, C.c_int64, _dp]
+        _lib = L
+    return _lib
+
+
+def _ptr(a):
+    return None if a is None else a.ctypes.data_as(_dp)
+
+
+def _f64(a):
+    return np.ascontiguousarray(np.asarray(a, dtype=np.float64))
+
+
+class Instance:
+    """One 1D problem: grid, moving medium, sources and DFT probes, with FP64 state.
+
+    ``kind`` 0 = moving perturbation, 1 = moving matter; ``interp`` 0 = layers
+    (``z`` holds n-1 boundaries for n values), 1 = piecewise linear (``z`` holds
+    n knots).  Positions are in cells of the moving frame at t = 0.
+    """
+
+    def __init__(self, nz, S, beta, kind=0, interp=0, z=(), eps=(1.0,), mu=None):
+        self.nz = int(nz)
+        self.S = float(S)
+        self.beta = float(beta)
+        self.kind = int(kind)
+        self.interp = int(interp)
+        self.eps = _f64(eps)
+        self.mu = _f64(np.ones_like(self.eps) if mu is None else mu)
+        self.z = _f64(z) if len(z) else np.zeros(1)
+        n = len(self.eps)
+        assert len(self.mu) == n
+        assert len(z) == (n - 1 if interp == 0 else n)
+        self.B = np.zeros(self.nz)
+        self.D = np.zeros(self.nz)
+        self.n_done = 0
+        self.sources = []
+        self.probes = []
+
+    def add_source(self, node, omega0, tau, t0, amp=1.0):
+        self.sources.append((int(node), float(omega0), float(tau), float(t0), float(amp)))
+
+    def add_probe(self, node, omega):
+        omega = _f64(omega)
+        self.probes.append({"node": int(node), "omega": omega,
+                            "re": np.zeros(len(omega)), "im": np.zeros(len(omega)),
+                            "series": []})
+        return len(self.probes) - 1
+
+    def _problem(self):
+        return _Problem(self.kind, self.interp, len(self.eps), 0, _ptr(self.z), _ptr(self.eps),
+                        _ptr(self.mu), self.beta, self.S, self.nz)
+
+    def run(self, n_steps, record=False):
+        """Advance ``n_steps`` leapfrog steps in FP64."""
+        n_steps = int(n_steps)
+        prob = self._problem()
+        srcs = (_Source * max(1, len(self.sources)))(*[_Source(*s) for s in self.sources])
+        series = [np.zeros(n_steps) if record else None for _ in self.probes]
+        prbs = (_Probe * max(1, len(self.probes)))(*[
+            _Probe(p["node"], len(p["omega"]), 0, _ptr(p["omega"]), _ptr(p["re"]),
+                   _ptr(p["im"]), _ptr(series[i]))
+            for i, p in enumerate(self.probes)])
+        rc = lib().orc_run(C.byref(prob), len(self.sources), srcs, len(self.probes), prbs,
+                           self.n_done, n_steps, _ptr(self.B), _ptr(self.D))
+        if rc != 0:
+            raise ValueError("oracle rejected the problem")
+        self.n_done += n_steps
+        if record:
+            for i, p in enumerate(self.probes):
+                p["series"].append(series[i])
+        return self
+
+    def spectrum(self, probe_id):
+        p = self.probes[probe_id]
+        return p["re"] + 1j * p["im"]
+
+    def series(self, probe_id):
+        s = self.probes[probe_id]["series"]
+        return np.concatenate(s) if s else np.zeros(0)
+
+    def material(self, which="eps", half_node=False, h=0):
+        """eps (or mu) at every node at half level ``h`` (time h*S/2)."""
+        out = np.zeros(self.nz)
+        prob = self._problem()
+        lib().orc_sample_material(C.byref(prob), 0 if which == "eps" else 1, int(half_node),
+                                  int(h), _ptr(out))
+        return out
+
+
+def run_many(instances, n_steps, threads=None, record=False):
+    """Run independent instances concurrently on host threads (ctypes drops the GIL)."""
+    threads = threads or os.cpu_count() or 1
+    with ThreadPoolExecutor(max_workers=threads) as ex:
+        list(ex.map(lambda inst: inst.run(n_steps, record=record), instances))
+    return instances

@@ -1,0 +1,271 @@
+/*
+ * gfdtd_oracle.c -- TEST INFRASTRUCTURE ONLY.
+ *
+ * Plain, slow, FP64 CPU implementation of the generalized FDTD scheme of
+ * Deck-Leger, Bahrami, Li and Caloz, "Generalized FDTD Scheme for the
+ * Simulation of Electromagnetic Scattering in Moving Structures"
+ * (arXiv 2304.06586).  It exists to check the CUDA library; only the tests,
+ * the smoke check and the benchmark's CPU-baseline leg may load it.  It shares
+ * no code, header or constant with the CUDA path.
+ *
+ * What it computes (normalised units c = eps0 = mu0 = 1, so v = beta, and the
+ * cell size dz = 1, the time step dt = S):
+ *
+ *   Moving perturbation (Sec. 4, Eqs. Farad_discr, Ampere_discr,
+ *   Dconst_discr, Bconst_discr with the dynamic terms of Table 1):
+ *     E*_k^{n-1/2}   = D_k^{n-1/2} / eps_k^{n-1/2} - beta * Bbar_k
+ *                      Bbar_k = (B_{k-1/2} + B_{k-3/2})/2  for beta >= 0 (Table 1, Ba)
+ *                             = (B_{k+3/2} + B_{k+1/2})/2  for beta <  0 (Table 1, Bb)
+ *                      with B at level n-1
+ *     B_{k+1/2}^n    = B^{n-1} - S (E*_{k+1} - E*_k) - beta S dB
+ *                      dB = B_{k+1/2} - B_{k-1/2} (beta >= 0, Table 1 dBa)
+ *                         = B_{k+3/2} - B_{k+1/2} (beta <  0, Table 1 dBb), level n-1
+ *     H*_{k+1/2}^n   = B^n / mu^n - beta (D_{k+1} + D_k)^{n-1/2} / 2   (Table 1, Da = Db)
+ *     D_k^{n+1/2}    = D^{n-1/2} - S (H*_{k+1/2} - H*_{k-1/2}) - beta S dD
+ *                      dD = D_k - D_{k-1} (beta >= 0, Table 1 dDa)
+ *                         = D_{k+1} - D_k (beta <  0, Table 1 dDb), level n-1/2
+ *
+ *   Moving matter (the paper derives the scheme for moving perturbation
+ *   only; the moving-matter case changes the constitutive relations): with the
+ *   footnote tensors of Eq. const_3d_regular in Eq. const_3d, the 1D star
+ *   relations are eps' E* = (1 - beta^2) D - beta H* and
+ *   mu' H* = (1 - beta^2) B - beta E*.  Solved for E* and H*:
+ *     E* = D / eps_m - beta_c B,   H* = B / mu_m - beta_c D,
+ *     1/eps_m = (1-beta^2) mu' / (n'^2 - beta^2),
+ *     1/mu_m  = (1-beta^2) eps' / (n'^2 - beta^2),
+ *     beta_c  = beta (1 - beta^2) / (n'^2 - beta^2),  n'^2 = eps' mu'.
+ *   These have the moving-perturbation form, so they are discretized exactly
+ *   like Eqs. Dconst_discr / Bconst_discr with the Table 1 averages (beta_c in
+ *   place of beta in the averaged terms; beta itself in the upwind terms).  In
+ *   moving vacuum (eps' = mu' = 1) beta_c = beta and 1/eps_m = 1/mu_m = 1, so
+ *   the update is the moving-perturbation update.
+ *
+ *   Grid: D and E* live at integer nodes k in [0, nz); B and H* at k+1/2,
+ *   stored at array index k.  The state between steps is (B^n, D^{n+1/2}).
+ *   Every field outside [0, nz) is zero (the paper is silent on domain ends).
+ *
+ *   Material: eps and mu are sampled at the node's moving-frame coordinate
+ *   xi = z - beta t (Eq. const_3d_regular: eps(r - v t)).  The coordinate is
+ *   evaluated exactly in 32.32 fixed point: positions are integers in units of
+ *   2^-32 cell, the profile breakpoints are rounded to that grid, and the
+ *   displacement per half time step is dq = round(beta*S * 2^31).  A node at
+ *   position p (k*2^32 for D, k*2^32 + 2^31 for B) at half level h (time
+ *   h*S/2) has xi = p - dq*h.  Layers are half-open [z_{i-1}, z_i).
+ *
+ *   Source (Eq. spectrum_incident, real carrier): after the D update of step n,
+ *     D_ks += amp * sin(w0 (t - t0)) * exp(-((t - t0)/tau)^2),  t = (n + 1/2) S.
+ *
+ *   Probes: F = E at the probe node at level n+1/2 (moving perturbation:
+ *   E = D/eps exactly, Eq. const_1d; moving matter: E = E* + beta * Bbar with
+ *   E* from the relation above and Bbar the Table 1 average of B^n), and for
+ *   every bin
+ *     X(w) += F * exp(+i w t) * dt,   t = (n + 1/2) S,  dt = S.
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+typedef struct {
+    int32_t kind;        /* 0: moving perturbation, 1: moving matter */
+    int32_t interp;      /* 0: layers (piecewise constant), 1: piecewise linear */
+    int32_t n;           /* number of layers (interp 0) or knots (interp 1) */
+    int32_t reserved;
+    const double* z;     /* interp 0: n-1 boundaries; interp 1: n knots; cells, moving frame, t = 0 */
+    const double* eps;   /* n values (relative permittivity; eps' at rest for matter) */
+    const double* mu;    /* n values */
+    double beta;         /* v / c */
+    double S;            /* Courant number dt/dz */
+    int64_t nz;          /* cells */
+} orc_problem;
+
+typedef struct {
+    int64_t node;
+    double omega0, tau, t0, amp;
+} orc_source;
+
+typedef struct {
+    int64_t node;
+    int32_t n_bins;
+    int32_t reserved;
+    const double* omega; /* n_bins angular frequencies */
+    double* re;          /* n_bins accumulators (in/out) */
+    double* im;
+    double* series;      /* optional: F per step of this call (length n_steps) */
+} orc_probe;
+
+/* ---- material sampling (exact fixed-point moving coordinate) ------------ */
+
+typedef struct {
+    int n, interp;
+    int64_t* zq;
+    const double* val;
+} orc_profile;
+
+static int64_t to_fixed(double x) { return llround(ldexp(x, 32)); }
+
+/* index of the last breakpoint <= xi, or -1 (binary search over sorted zq) */
+static int last_at_or_below(const int64_t* zq, int m, int64_t xi)
+{
+    int lo = -1, hi = m;                 /* invariant: zq[lo] <= xi < zq[hi] */
+    while (hi - lo > 1) {
+        int mid = (lo + hi) / 2;
+        if (zq[mid] <= xi) lo = mid; else hi = mid;
+    }
+    return lo;
+}
+
+static double profile_at(const orc_profile* pr, int64_t xi)
+{
+    if (pr->interp == 0) {
+        /* value i holds on [z_{i-1}, z_i): i = number of boundaries <= xi */
+        int i = last_at_or_below(pr->zq, pr->n - 1, xi) + 1;
+        return pr->val[i];
+    }
+    if (xi <= pr->zq[0]) return pr->val[0];
+    if (xi >= pr->zq[pr->n - 1]) return pr->val[pr->n - 1];
+    int i = last_at_or_below(pr->zq, pr->n, xi);
+    double w = (double)(xi - pr->zq[i]) / (double)(pr->zq[i + 1] - pr->zq[i]);
+    return pr->val[i] + w * (pr->val[i + 1] - pr->val[i]);
+}
+
+/* position of integer node k and of half node k+1/2, in units of 2^-32 cell */
+static int64_t node_pos(int64_t k) { return k * 4294967296LL; }
+static int64_t half_pos(int64_t k) { return k * 4294967296LL + 2147483648LL; }
+
+/* ---- helpers: fields outside [0, nz) are zero ---------------------------- */
+
+static double at(const double* a, int64_t i, int64_t nz) { return (i < 0 || i >= nz) ? 0.0 : a[i]; }
+
+static double source_value(const orc_source* s, double t)
+{
+    double u = t - s->t0;
+    return s->amp * sin(s->omega0 * u) * exp(-(u / s->tau) * (u / s->tau));
+}
+
+/* E* from D and the averaged B (perturbation: Eq. Dconst_discr; matter: the
+   solved star relation), and H* from B and the averaged D (Eq. Bconst_discr). */
+static double estar(int kind, double beta, double e, double m, double d, double bbar)
+{
+    if (kind == 0) return d / e - beta * bbar;
+    double den = e * m - beta * beta;
+    double g = 1.0 - beta * beta;
+    return g * m / den * d - beta * g / den * bbar;
+}
+
+static double hstar(int kind, double beta, double e, double m, double b, double dbar)
+{
+    if (kind == 0) return b / m - beta * dbar;
+    double den = e * m - beta * beta;
+    double g = 1.0 - beta * beta;
+    return g * e / den * b - beta * g / den * dbar;
+}
+
+/* ---- the time loop ------------------------------------------------------- */
+
+int orc_run(const orc_problem* p, int n_src, const orc_source* src,
+            int n_probe, orc_probe* probes,
+            int64_t n_done, int64_t n_steps,
+            double* B, double* D)
+{
+    const int64_t nz = p->nz;
+    const double beta = p->beta, S = p->S;
+    const int pos = beta >= 0.0;
+    if (nz <= 0 || p->n < 1 || (p->interp == 1 && p->n < 2)) return -1;
+
+    int nb = p->interp == 0 ? p->n - 1 : p->n;
+    orc_profile eps = {p->n, p->interp, NULL, p->eps};
+    orc_profile mu = {p->n, p->interp, NULL, p->mu};
+    int64_t* zq = (int64_t*)malloc(sizeof(int64_t) * (size_t)(nb > 0 ? nb : 1));
+    for (int i = 0; i < nb; ++i) zq[i] = to_fixed(p->z[i]);
+    eps.zq = zq;
+    mu.zq = zq;
+    const int64_t dq = llround(ldexp(beta * S, 31));   /* beta*S/2 cells per half step */
+
+    double* Es = (double*)malloc(sizeof(double) * (size_t)nz);  /* E* (perturbation: recomputed) */
+    double* Hs = (double*)malloc(sizeof(double) * (size_t)nz);  /* H* */
+    double* Bo = (double*)malloc(sizeof(double) * (size_t)nz);  /* B^{n-1} */
+    double* Do = (double*)malloc(sizeof(double) * (size_t)nz);  /* D^{n-1/2} */
+
+    for (int64_t s = 0; s < n_steps; ++s) {
+        const int64_t n = n_done + s + 1;      /* B^{n-1} -> B^n, D^{n-1/2} -> D^{n+1/2} */
+        memcpy(Bo, B, sizeof(double) * (size_t)nz);
+        memcpy(Do, D, sizeof(double) * (size_t)nz);
+
+        /* E*^{n-1/2} (Eq. Dconst_discr with Table 1 Ba/Bb, B at level n-1) */
+        for (int64_t k = 0; k < nz; ++k) {
+            double e = profile_at(&eps, node_pos(k) - dq * (2 * n - 1));
+            double m = profile_at(&mu, node_pos(k) - dq * (2 * n - 1));
+            double bbar = pos ? 0.5 * (at(Bo, k - 1, nz) + at(Bo, k - 2, nz))
+                              : 0.5 * (at(Bo, k + 1, nz) + at(Bo, k, nz));
+            Es[k] = estar(p->kind, beta, e, m, Do[k], bbar);
+        }
+
+        /* B^n (Eq. Farad_discr with Table 1 dBa/dBb) */
+        for (int64_t k = 0; k < nz; ++k) {
+            double dB = pos ? Bo[k] - at(Bo, k - 1, nz) : at(Bo, k + 1, nz) - Bo[k];
+            B[k] = Bo[k] - S * (at(Es, k + 1, nz) - Es[k]) - beta * S * dB;
+        }
+
+        /* H*^n (Eq. Bconst_discr with Table 1 Da/Db, D at level n-1/2) */
+        for (int64_t k = 0; k < nz; ++k) {
+            double e = profile_at(&eps, half_pos(k) - dq * (2 * n));
+            double m = profile_at(&mu, half_pos(k) - dq * (2 * n));
+            double dbar = 0.5 * (Do[k] + at(Do, k + 1, nz));
+            Hs[k] = hstar(p->kind, beta, e, m, B[k], dbar);
+        }
+
+        /* D^{n+1/2} (Eq. Ampere_discr with Table 1 dDa/dDb) */
+        for (int64_t k = 0; k < nz; ++k) {
+            double dD = pos ? Do[k] - at(Do, k - 1, nz) : at(Do, k + 1, nz) - Do[k];
+            D[k] = Do[k] - S * (Hs[k] - at(Hs, k - 1, nz)) - beta * S * dD;
+        }
+
+        /* soft source at t_{n+1/2} */
+        const double t = (double)(2 * n + 1) * S * 0.5;
+        for (int i = 0; i < n_src; ++i) {
+            if (src[i].node >= 0 && src[i].node < nz) D[src[i].node] += source_value(&src[i], t);
+        }
+
+        /* probes: physical E at level n+1/2, running DFT */
+        for (int i = 0; i < n_probe; ++i) {
+            int64_t k = probes[i].node;
+            if (k < 0 || k >= nz) continue;
+            double e = profile_at(&eps, node_pos(k) - dq * (2 * n + 1));
+            double F;
+            if (p->kind == 0) {
+                F = D[k] / e;                       /* Eq. const_1d: D = eps E */
+            } else {
+                double m = profile_at(&mu, node_pos(k) - dq * (2 * n + 1));
+                double bbar = pos ? 0.5 * (at(B, k - 1, nz) + at(B, k - 2, nz))
+                                  : 0.5 * (at(B, k + 1, nz) + at(B, k, nz));
+                F = estar(1, beta, e, m, D[k], bbar) + beta * bbar;   /* E = E* + v B */
+            }
+            if (probes[i].series) probes[i].series[s] = F;
+            for (int f = 0; f < probes[i].n_bins; ++f) {
+                double w = probes[i].omega[f];
+                probes[i].re[f] += F * cos(w * t) * S;
+                probes[i].im[f] += F * sin(w * t) * S;
+            }
+        }
+    }
+    free(zq); free(Es); free(Hs); free(Bo); free(Do);
+    return 0;
+}
+
+/* eps (or mu, which = 1) sampled at every integer node (which = 0) or half
+   node (which = 1) at half level h: the same material rule the time loop uses. */
+int orc_sample_material(const orc_problem* p, int which_field, int half_node, int64_t h, double* out)
+{
+    int nb = p->interp == 0 ? p->n - 1 : p->n;
+    int64_t* zq = (int64_t*)malloc(sizeof(int64_t) * (size_t)(nb > 0 ? nb : 1));
+    for (int i = 0; i < nb; ++i) zq[i] = to_fixed(p->z[i]);
+    orc_profile pr = {p->n, p->interp, zq, which_field == 0 ? p->eps : p->mu};
+    const int64_t dq = llround(ldexp(p->beta * p->S, 31));
+    for (int64_t k = 0; k < p->nz; ++k) {
+        int64_t x = half_node ? half_pos(k) : node_pos(k);
+        out[k] = profile_at(&pr, x - dq * h);
+    }
+    free(zq);
+    return 0;
+}
