@@ -1,0 +1,287 @@
+"""Throughput benchmark of the batched generalized-FDTD engine on GB300.
+
+Workload (default): the batched moving bilayer crystal -- 4096 instances,
+Nz log-uniform in [2^12, 2^18] (2.5e8 cells), v uniform in [-0.8, 0.8]c,
+64 periods of eps 1/4 layers, FP32 fields, seeded synthetic data.  One bench
+"step" is one gfdtd_step call advancing the whole batch by --time-steps
+leapfrog steps (all of: moving material, E*, B, H*, D, source injection, DFT
+probes); the default 10 steps x 2000 time steps is the full 20000-step run.
+
+Prints one JSON line: Gcell-updates/s (value, device-resident inputs), the
+end-to-end number through the C ABI with host buffers (e2e), the plain
+one-step-per-launch kernel and the batched/plain ratio, the roofline of the
+batched kernel, the FP64 oracle timed on host cores (cpu_baseline) and the
+SM clocks seen during the timed region.  --impl reference times the oracle
+alone on the same workload.  Under torchrun every rank runs its own
+instance batch (weak scaling, no collective on the data path).
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+FLOPS_PER_CELL_UPDATE = 20        # FP32 operations of one B and D update (E*, B, H*, D)
+SM_COUNT, FP32_LANES_PER_SM, SM_MAX_MHZ = 152, 128, 2070.0
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--time-steps", type=int, default=2000, help="leapfrog steps per bench step")
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--instances", type=int, default=4096)
+    ap.add_argument("--plain-steps", type=int, default=4)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    return ap.parse_args()
+
+
+def dist_setup():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+
+    def __enter__(self):
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + q,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        self.out = ""
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.out, _ = self.proc.communicate(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+                self.out = ""
+
+    def summary(self):
+        mhz, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in (self.out or "").strip().splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                mhz.append(float(f[1]))
+                mx = float(f[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(mhz) if mhz else None, "sm_max_mhz": mx,
+                "reasons": sorted(reasons), "samples": len(mhz)}
+
+
+def configure(sim, wl, gb):
+    for k, I in enumerate(wl.instances):
+        sim.set_medium(k, I.kind, I.beta, I.interp, I.z, I.eps, I.mu, allow_unstable=True)
+        for s in I.sources:
+            sim.add_source(k, *s)
+        for p in I.probes:
+            sim.add_probe(k, p[0], p[1])
+
+
+def cpu_baseline(wl, n_inst=32, n_steps=100, seed=1):
+    """The FP64 oracle, as it stands, on a bounded sample of the workload."""
+    import oracle
+    rng = np.random.default_rng(seed)
+    pick = sorted(rng.choice(len(wl.instances), size=min(n_inst, len(wl.instances)), replace=False))
+    orcs = []
+    for k in pick:
+        I = wl.instances[k]
+        o = oracle.Instance(I.nz, wl.S, I.beta, kind=I.kind, interp=I.interp, z=I.z, eps=I.eps, mu=I.mu)
+        for s in I.sources:
+            o.add_source(*s)
+        for p in I.probes:
+            o.add_probe(p[0], p[1])
+        orcs.append(o)
+    threads = os.cpu_count() or 1
+    t0 = time.perf_counter()
+    oracle.run_many(orcs, n_steps, threads=threads)
+    dt = time.perf_counter() - t0
+    cu = sum(o.nz for o in orcs) * n_steps
+    return {"value": cu / dt / 1e9, "unit": "Gcell-updates/s", "cores": threads, "kind": "oracle",
+            "sample": "%d of %d instances x %d steps (%.3g cell-updates, %.1f s)"
+                      % (len(orcs), len(wl.instances), n_steps, cu, dt)}
+
+
+def run_reference(args, wl, rank):
+    if rank != 0:
+        return
+    per = [cpu_baseline(wl, n_inst=32, n_steps=60, seed=100 + i) for i in range(args.warmup)]
+    vals = []
+    for i in range(args.steps):
+        vals.append(cpu_baseline(wl, n_inst=32, n_steps=60, seed=200 + i))
+    v = float(np.mean([x["value"] for x in vals]))
+    del per
+    line = {"impl": "reference", "metric": "Gcell-updates/s", "value": v, "unit": "Gcell-updates/s",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": wl.description},
+            "cpu_baseline": {"value": v, "unit": "Gcell-updates/s", "cores": vals[0]["cores"],
+                             "kind": "oracle", "sample": "per step: " + vals[0]["sample"]},
+            "e2e": {"value": v, "unit": "Gcell-updates/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    rank, world, local = dist_setup()
+    from paper_2304_06586_gb300 import workloads as w
+    wl = w.config3(n_inst=args.instances, n_steps=args.time_steps, seed=w.SEED0 + 3 + 1000 * rank)
+    if args.impl == "reference":
+        return run_reference(args, wl, rank)
+
+    import torch
+    torch.cuda.set_device(local)
+    pg = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+        pg = dist
+
+    from paper_2304_06586_gb300 import binding as gb
+    gb.use_torch_allocator()
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        sim = gb.Simulation([i.nz for i in wl.instances], wl.S, gb.F32, stream=stream.cuda_stream)
+        configure(sim, wl, gb)
+        T = args.time_steps
+
+        def barrier():
+            if pg:
+                pg.barrier()
+            torch.cuda.synchronize()
+
+        for _ in range(args.warmup):
+            sim.step(T)
+        barrier()
+        st = sim.stats()
+        l0 = st["kernel_launches"]
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        with Clocks(local) as clk:
+            barrier()
+            e0.record(stream)
+            for _ in range(args.steps):
+                sim.step(T)
+            e1.record(stream)
+            barrier()
+        ms = e0.elapsed_time(e1)
+        st = sim.stats()
+        launches = st["kernel_launches"] - l0
+        if pg:
+            t = torch.tensor([ms], device="cuda")
+            pg.all_reduce(t, op=pg.ReduceOp.MAX)
+            ms = float(t.item())
+        cells = st["cells"]
+        cu = cells * T * args.steps
+        value = cu * world / (ms / 1e3) / 1e9
+
+        # batched kernel launches per bench step: one per time block per instance kind
+        blocks_per_step = int(np.ceil(T / st["time_block"]))
+        launch_ms = ms / (args.steps * blocks_per_step)           # includes the small per-chunk kernels
+        cu_per_launch = cells * st["time_block"]
+        achieved = FLOPS_PER_CELL_UPDATE * cu_per_launch / (launch_ms / 1e3) / 1e12
+        peak = 2 * FP32_LANES_PER_SM * SM_COUNT * SM_MAX_MHZ * 1e6 / 1e12
+        roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                    "frac": achieved / peak, "traffic": None,
+                    "note": "FP32 pipe: %d flops per cell-update, peak = 2 x 128 lanes x 152 SMs x "
+                            "2070 MHz; launch time = timed region / batched launches"
+                            % FLOPS_PER_CELL_UPDATE}
+
+        # end to end through the C ABI with pinned host buffers
+        e2e = None
+        if not args.no_e2e:
+            n_el, eb, _ = sim.state_layout()
+            nbytes = n_el * eb
+            hB = torch.empty(nbytes, dtype=torch.uint8, pin_memory=True)
+            hD = torch.empty(nbytes, dtype=torch.uint8, pin_memory=True)
+            sim.read_state(gb.FIELD_B, hB.data_ptr(), nbytes)
+            sim.read_state(gb.FIELD_D, hD.data_ptr(), nbytes)
+            sim.synchronize()
+            barrier()
+            t0 = time.perf_counter()
+            for _ in range(args.steps):
+                sim.write_state(gb.FIELD_B, hB.data_ptr(), nbytes)
+                sim.write_state(gb.FIELD_D, hD.data_ptr(), nbytes)
+                sim.step(T)
+                sim.read_state(gb.FIELD_B, hB.data_ptr(), nbytes)
+                sim.read_state(gb.FIELD_D, hD.data_ptr(), nbytes)
+                sim.synchronize()
+            barrier()
+            dt = time.perf_counter() - t0
+            if pg:
+                t = torch.tensor([dt], device="cuda")
+                pg.all_reduce(t, op=pg.ReduceOp.MAX)
+                dt = float(t.item())
+            e2e = {"value": cu * world / dt / 1e9, "unit": "Gcell-updates/s",
+                   "h2d_bytes_per_step": 2 * nbytes, "d2h_bytes_per_step": 2 * nbytes}
+
+        # plain kernel (one step, one instance per launch) on a few steps
+        plain = None
+        if args.plain_steps > 0:
+            sim.step_plain(1)
+            barrier()
+            p0, p1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            p0.record(stream)
+            sim.step_plain(args.plain_steps)
+            p1.record(stream)
+            barrier()
+            pms = p0.elapsed_time(p1)
+            pv = cells * args.plain_steps / (pms / 1e3) / 1e9
+            plain = {"value": pv, "unit": "Gcell-updates/s", "steps": args.plain_steps,
+                     "batched_over_plain": value / world / pv}
+        sim.close()
+
+    if rank != 0:
+        return
+    clocks = clk.summary()
+    line = {"metric": "Gcell-updates/s batched vs plain on 1 GB300 at <=1e-4 L2 vs FP64; % of roofline",
+            "value": value, "unit": "Gcell-updates/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": wl.description, "instances": len(wl.instances), "cells": cells,
+                       "time_steps_per_step": T, "tile": [st["cells_per_lane"], st["time_block"]],
+                       "l2": "inputs larger than L2 (%.2f GB of fields)" % (cells * 16 / 1e9),
+                       "parallelism": "instances sharded per rank" if world > 1 else "1 GPU"},
+            "e2e": e2e, "gpu_launches": launches, "roofline": roofline, "plain": plain,
+            "clocks": clocks}
+    if not args.no_cpu:
+        line["cpu_baseline"] = cpu_baseline(wl)
+    print(json.dumps(line), flush=True)
+    if pg:
+        pg.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,223 @@
+/*
+ * gfdtd.h -- C ABI of the GB300 (sm_103a) generalized-FDTD engine.
+ *
+ * The engine time-steps batches of independent 1D problems with the
+ * generalized Yee cell and stencil of Deck-Leger, Bahrami, Li and Caloz,
+ * "Generalized FDTD Scheme for the Simulation of Electromagnetic Scattering in
+ * Moving Structures" (arXiv 2304.06586):
+ *
+ *   Sec. 3 (Fig. 2):   the Yee cell carries the auxiliary fields
+ *                      E* = E + v x B and H* = H - v x D (Eq. star) in place of
+ *                      the tangential E and H; D sits on integer nodes k and B
+ *                      on half nodes k+1/2, as in the standard Yee cell.
+ *   Sec. 4:            the leapfrog updates Eqs. Farad_discr and Ampere_discr
+ *                      (B and D) and the constitutive updates Eqs.
+ *                      Dconst_discr and Bconst_discr (E* and H*), with the
+ *                      velocity terms of Table 1 (upwind differences dBa/dBb,
+ *                      dDa/dDb and the averages Ba/Bb, Da/Db; column chosen by
+ *                      the sign of v).
+ *   Eq. const_3d_regular: the medium is a profile eps(z - v t), mu(z - v t)
+ *                      that moves rigidly at velocity v (moving perturbation),
+ *                      or moving matter whose rest-frame profile eps', mu' is
+ *                      made bianisotropic by the motion (footnote tensors of
+ *                      Eq. const_3d_regular).
+ *   Eq. spectrum_incident: sources are Gaussian-modulated carriers.
+ *   Eqs. spectrum_scat_interface, comp_exp: probes accumulate running DFTs of
+ *                      the physical E field.
+ *
+ * Units are normalised: c = eps0 = mu0 = 1, v = beta, the cell size is 1 and
+ * the time step is S = dt/dz (the Courant number).  Time level n (B, H*) is
+ * t = n S; level n+1/2 (D, E*) is t = (n + 1/2) S.  After n steps the state of
+ * an instance is (B^n, D^{n+1/2}); a fresh context starts at n = 0 with all
+ * fields zero.  Fields outside [0, nz) are zero (perfectly conducting /
+ * magnetic walls one half cell outside the grid).
+ *
+ * Moving medium.  Positions are given in cells of the moving frame at t = 0.
+ * A node at lab position p (k for D, k + 1/2 for B) at time t samples the
+ * profile at xi = p - beta t.  xi is evaluated exactly in 32.32 fixed point:
+ * profile positions are rounded to multiples of 2^-32 cell and the
+ * displacement per half step is round(beta * S * 2^31) units of 2^-32 cell
+ * (beta * S taken as the IEEE double product, rounding half away from zero).
+ * Layers are half-open intervals [z_{i-1}, z_i).
+ *
+ * Moving matter.  With rest values eps', mu' (n'^2 = eps' mu') the 1D star
+ * relations of Eq. const_3d, solved for E* and H*, read
+ *     E* = D / eps_m - beta_c B,   H* = B / mu_m - beta_c D,
+ *     1/eps_m = (1 - beta^2) mu' / (n'^2 - beta^2),
+ *     1/mu_m  = (1 - beta^2) eps' / (n'^2 - beta^2),
+ *     beta_c  = beta (1 - beta^2) / (n'^2 - beta^2);
+ * they are discretized like Eqs. Dconst_discr / Bconst_discr with the Table 1
+ * averages (beta_c in the averaged terms, beta in the upwind terms).
+ *
+ * Conventions.  Every call returns a gfdtd_status; nothing aborts or throws
+ * across the ABI.  Host input arrays are copied before the call returns.
+ * Host output buffers are owned by the caller.  The library owns its device
+ * memory, obtained from the allocator installed with gfdtd_set_allocator (by
+ * default cudaMalloc).  Work runs asynchronously on the stream given to
+ * gfdtd_create; calls that return data to the host synchronise that stream.
+ * A context must not be used from two threads at once.
+ */
+#ifndef GFDTD_H
+#define GFDTD_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct gfdtd_ctx gfdtd_ctx;
+
+typedef enum {
+    GFDTD_OK = 0,
+    GFDTD_E_ARG = -1,          /* invalid argument (index, size, NULL pointer, range) */
+    GFDTD_E_OOM = -2,          /* device or host allocation failed */
+    GFDTD_E_CUDA = -3,         /* a CUDA runtime call failed; see gfdtd_last_error */
+    GFDTD_E_UNSTABLE = -4,     /* medium outside the scheme's stability region (n|beta| > 1) */
+    GFDTD_E_TIMEOUT = -5,      /* reserved: a bounded device wait gave up */
+    GFDTD_E_STATE = -6,        /* call not valid in the context's current state */
+    GFDTD_E_UNSUPPORTED = -7   /* option not built into this library */
+} gfdtd_status;
+
+typedef enum { GFDTD_PERTURBATION = 0, GFDTD_MATTER = 1 } gfdtd_kind;
+
+/* Field storage and update precision.  F32: FP32 storage and arithmetic.
+ * F32_KAHAN: FP32 with compensated (Kahan) B and D updates.  BF16 / F16:
+ * 16-bit storage between time blocks, FP32 arithmetic.  F64: FP64 storage and
+ * arithmetic (reference tier; GB300's FP64 rate is low). */
+typedef enum {
+    GFDTD_F32 = 0, GFDTD_F32_KAHAN = 1, GFDTD_BF16 = 2, GFDTD_F16 = 3, GFDTD_F64 = 4
+} gfdtd_prec;
+
+/* Profile interpolation.  LAYERS: n values, n-1 boundaries, value i on
+ * [z_{i-1}, z_i).  LINEAR: n knots, linear between knots, constant beyond the
+ * first and last knot. */
+typedef enum { GFDTD_LAYERS = 0, GFDTD_LINEAR = 1 } gfdtd_interp;
+
+/* Fields readable with gfdtd_read_fields.  D (level n+1/2) and B (level n) are
+ * the state; E = physical E at level n+1/2 (moving perturbation: D/eps,
+ * Eq. const_1d; moving matter: E* + beta Bbar); ESTAR = E* at level n+1/2
+ * (Eq. Dconst_discr with B^n); H = physical H at level n (moving perturbation
+ * only: B/mu, Eq. const_1d). */
+typedef enum {
+    GFDTD_FIELD_D = 0, GFDTD_FIELD_B = 1, GFDTD_FIELD_E = 2, GFDTD_FIELD_H = 3, GFDTD_FIELD_ESTAR = 4
+} gfdtd_field;
+
+/* Device allocator hooks: alloc returns a device pointer (NULL on failure),
+ * free releases it.  `stream` is the context's CUDA stream. */
+typedef void* (*gfdtd_alloc_fn)(size_t bytes, void* stream, void* user);
+typedef void (*gfdtd_free_fn)(void* ptr, size_t bytes, void* stream, void* user);
+
+/* Install process-wide allocator hooks used by contexts created afterwards.
+ * Both NULL restores cudaMalloc/cudaFree.  Returns E_ARG if exactly one is NULL. */
+gfdtd_status gfdtd_set_allocator(gfdtd_alloc_fn alloc, gfdtd_free_fn free_fn, void* user);
+
+/* Create a context for n_inst independent instances of nz[i] cells each
+ * (1 <= nz[i] <= 2^28, n_inst >= 1), Courant number S in (0, 1], field
+ * precision prec, on the CUDA stream cuda_stream (a cudaStream_t; NULL = the
+ * legacy default stream) of the current device.  Every instance starts as
+ * vacuum at rest with no sources or probes.  Allocates all field storage. */
+gfdtd_status gfdtd_create(gfdtd_ctx** out, int n_inst, const int64_t* nz, double S,
+                          gfdtd_prec prec, void* cuda_stream);
+
+/* Set the moving medium of instance `inst` (Eq. const_3d_regular): kind,
+ * velocity beta in (-1, 1), interpolation, n values (n >= 1; n >= 2 for
+ * LINEAR) of eps_r[] and mu_r[] (> 0), and positions z[] (LAYERS: n-1
+ * strictly increasing boundaries; LINEAR: n strictly increasing knots; may be
+ * NULL when n == 1 for LAYERS).  Fails with E_UNSTABLE when some value pair
+ * has n|beta| > 1 (the von Neumann limit of the scheme, Sec. 5) unless
+ * `allow_unstable` is nonzero, and with E_ARG when |beta| S >= 1. */
+gfdtd_status gfdtd_set_medium(gfdtd_ctx* ctx, int inst, gfdtd_kind kind, double beta,
+                              gfdtd_interp interp, int n, const double* z,
+                              const double* eps_r, const double* mu_r, int allow_unstable);
+
+/* Add a soft source to instance `inst` at integer node `node` in [0, nz):
+ * after the D update of every step n, D_node += amp sin(omega0 (t - t0))
+ * exp(-((t - t0)/tau)^2) with t = (n + 1/2) S (Eq. spectrum_incident, real
+ * carrier).  tau > 0. */
+gfdtd_status gfdtd_add_source(gfdtd_ctx* ctx, int inst, int64_t node, double omega0,
+                              double tau, double t0, double amp);
+
+/* Add a DFT probe at integer node `node` of instance `inst` with n_bins >= 1
+ * angular frequencies omega[] (copied).  From the next step on, every step
+ * adds E(node, t) exp(+i omega t) S to each bin, t = (n + 1/2) S, in FP64.
+ * *probe_id receives the probe's index within the instance. */
+gfdtd_status gfdtd_add_probe(gfdtd_ctx* ctx, int inst, int64_t node, int n_bins,
+                             const double* omega, int* probe_id);
+
+/* Advance every instance by n_steps >= 0 steps with the batched kernel
+ * (register-resident tiles, several steps per HBM round trip, one launch per
+ * time block for the whole batch, replayed from a CUDA graph).  The first call
+ * may autotune the tile shape; make it before capturing the stream into a
+ * graph of your own.  Asynchronous. */
+gfdtd_status gfdtd_step(gfdtd_ctx* ctx, int64_t n_steps);
+
+/* Same result as gfdtd_step with the plain kernel: one step and one instance
+ * per launch, fields in HBM.  The throughput baseline; also asynchronous. */
+gfdtd_status gfdtd_step_plain(gfdtd_ctx* ctx, int64_t n_steps);
+
+/* Copy field `which` of instance `inst` to host_dst[0..n) as doubles, n == nz.
+ * Synchronises the context's stream. */
+gfdtd_status gfdtd_read_fields(gfdtd_ctx* ctx, int inst, gfdtd_field which,
+                               double* host_dst, int64_t n);
+
+/* Overwrite the state field D or B of instance `inst` from host_src[0..n),
+ * n == nz (rounded to the storage precision).  Synchronises the stream. */
+gfdtd_status gfdtd_write_fields(gfdtd_ctx* ctx, int inst, gfdtd_field which,
+                                const double* host_src, int64_t n);
+
+/* Bulk copies of a whole state field (D or B) in device storage format and
+ * layout: instance i occupies elements [offsets[i], offsets[i] + nz[i]) of an
+ * array of gfdtd_state_elems() elements of gfdtd_state_elem_bytes() bytes
+ * (padding elements are zero).  `bytes` must equal the array size.  host
+ * buffers should be pinned for full copy bandwidth.  Asynchronous with respect
+ * to the host when host memory is pinned; synchronise with gfdtd_synchronize. */
+gfdtd_status gfdtd_read_state(gfdtd_ctx* ctx, gfdtd_field which, void* host_dst, int64_t bytes);
+gfdtd_status gfdtd_write_state(gfdtd_ctx* ctx, gfdtd_field which, const void* host_src,
+                               int64_t bytes);
+gfdtd_status gfdtd_state_layout(const gfdtd_ctx* ctx, int64_t* n_elems, int* elem_bytes,
+                                int64_t* offsets /* n_inst entries, or NULL */);
+
+/* Read the FP64 DFT accumulators of probe `probe_id` of instance `inst` into
+ * re[0..n_bins) and im[0..n_bins).  Synchronises the stream. */
+gfdtd_status gfdtd_read_spectrum(gfdtd_ctx* ctx, int inst, int probe_id, double* re, double* im);
+
+/* Steps completed so far (the n of the state (B^n, D^{n+1/2})). */
+gfdtd_status gfdtd_steps_done(const gfdtd_ctx* ctx, int64_t* n);
+
+/* Host-only von Neumann analysis (Sec. 5, App. A): max over kz dz in (0, pi]
+ * of the modulus of the eigenvalues of the one-step amplification matrix of a
+ * uniform medium (eps_r, mu_r) moving at beta with Courant number S. */
+gfdtd_status gfdtd_stability(double S, double beta, double eps_r, double mu_r,
+                             gfdtd_kind kind, double* max_abs_zeta);
+
+/* Tile shape of the batched kernel: cells per lane (8 or 16) and steps per
+ * time block (8, 16 or 32).  0, 0 selects autotuning at the next step. */
+gfdtd_status gfdtd_set_tuning(gfdtd_ctx* ctx, int cells_per_lane, int time_block);
+
+typedef struct {
+    int cells_per_lane;        /* chosen tile shape */
+    int time_block;
+    int64_t n_tiles;           /* tiles per time block for the whole batch */
+    int64_t kernel_launches;   /* library kernels launched so far (graph nodes counted) */
+    int64_t cells;             /* sum of nz */
+} gfdtd_stats;
+
+gfdtd_status gfdtd_get_stats(const gfdtd_ctx* ctx, gfdtd_stats* out);
+
+/* Wait for all work queued on the context's stream. */
+gfdtd_status gfdtd_synchronize(gfdtd_ctx* ctx);
+
+/* Text of the last error on this context (or of the last failed create when
+ * ctx is NULL).  Valid until the next call on the context. */
+const char* gfdtd_last_error(const gfdtd_ctx* ctx);
+
+/* Release the context and all its device memory.  NULL is ignored. */
+void gfdtd_destroy(gfdtd_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GFDTD_H */

@@ -1,0 +1,248 @@
+"""Thin ctypes binding of the C ABI in include/gfdtd.h.
+
+Only argument marshalling lives here; every step of the method runs in the
+CUDA library.  There is no fallback: if ``libgfdtd.so`` cannot be loaded, or
+no GPU is present when a context is created, the call raises.
+
+PyTorch supplies the CUDA stream (the current stream at creation) and, through
+``use_torch_allocator()``, the device memory of the contexts.
+"""
+import ctypes as C
+import os
+
+import numpy as np
+
+from . import build as _build
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+
+OK, E_ARG, E_OOM, E_CUDA, E_UNSTABLE, E_TIMEOUT, E_STATE, E_UNSUPPORTED = 0, -1, -2, -3, -4, -5, -6, -7
+PERTURBATION, MATTER = 0, 1
+F32, F32_KAHAN, BF16, F16, F64 = 0, 1, 2, 3, 4
+LAYERS, LINEAR = 0, 1
+FIELD_D, FIELD_B, FIELD_E, FIELD_H, FIELD_ESTAR = 0, 1, 2, 3, 4
+
+_STATUS = {E_ARG: "E_ARG", E_OOM: "E_OOM", E_CUDA: "E_CUDA", E_UNSTABLE: "E_UNSTABLE",
+           E_TIMEOUT: "E_TIMEOUT", E_STATE: "E_STATE", E_UNSUPPORTED: "E_UNSUPPORTED"}
+
+_dp = C.POINTER(C.c_double)
+_i64p = C.POINTER(C.c_int64)
+ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p, C.c_void_p)
+FREE_FN = C.CFUNCTYPE(None, C.c_void_p, C.c_size_t, C.c_void_p, C.c_void_p)
+
+
+class Stats(C.Structure):
+    _fields_ = [("cells_per_lane", C.c_int), ("time_block", C.c_int), ("n_tiles", C.c_int64),
+                ("kernel_launches", C.c_int64), ("cells", C.c_int64)]
+
+
+# every symbol of include/gfdtd.h with its (restype, argtypes)
+SIGNATURES = {
+    "gfdtd_set_allocator": (C.c_int, [ALLOC_FN, FREE_FN, C.c_void_p]),
+    "gfdtd_create": (C.c_int, [C.POINTER(C.c_void_p), C.c_int, _i64p, C.c_double, C.c_int, C.c_void_p]),
+    "gfdtd_set_medium": (C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_double, C.c_int, C.c_int, _dp, _dp,
+                                   _dp, C.c_int]),
+    "gfdtd_add_source": (C.c_int, [C.c_void_p, C.c_int, C.c_int64, C.c_double, C.c_double, C.c_double,
+                                   C.c_double]),
+    "gfdtd_add_probe": (C.c_int, [C.c_void_p, C.c_int, C.c_int64, C.c_int, _dp, C.POINTER(C.c_int)]),
+    "gfdtd_step": (C.c_int, [C.c_void_p, C.c_int64]),
+    "gfdtd_step_plain": (C.c_int, [C.c_void_p, C.c_int64]),
+    "gfdtd_read_fields": (C.c_int, [C.c_void_p, C.c_int, C.c_int, _dp, C.c_int64]),
+    "gfdtd_write_fields": (C.c_int, [C.c_void_p, C.c_int, C.c_int, _dp, C.c_int64]),
+    "gfdtd_read_state": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_int64]),
+    "gfdtd_write_state": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_int64]),
+    "gfdtd_state_layout": (C.c_int, [C.c_void_p, _i64p, C.POINTER(C.c_int), _i64p]),
+    "gfdtd_read_spectrum": (C.c_int, [C.c_void_p, C.c_int, C.c_int, _dp, _dp]),
+    "gfdtd_steps_done": (C.c_int, [C.c_void_p, _i64p]),
+    "gfdtd_stability": (C.c_int, [C.c_double, C.c_double, C.c_double, C.c_double, C.c_int, _dp]),
+    "gfdtd_set_tuning": (C.c_int, [C.c_void_p, C.c_int, C.c_int]),
+    "gfdtd_get_stats": (C.c_int, [C.c_void_p, C.POINTER(Stats)]),
+    "gfdtd_synchronize": (C.c_int, [C.c_void_p]),
+    "gfdtd_last_error": (C.c_char_p, [C.c_void_p]),
+    "gfdtd_destroy": (None, [C.c_void_p]),
+}
+
+_lib = None
+
+
+def library_path():
+    return _build.LIB
+
+
+def load(build_if_missing=True):
+    """Load (building first if needed) the C-ABI library; raises if it cannot."""
+    global _lib
+    if _lib is None:
+        path = _build.build() if build_if_missing else _build.LIB
+        if not os.path.exists(path):
+            raise RuntimeError("libgfdtd.so is not built: %s" % path)
+        L = C.CDLL(path)
+        for name, (res, args) in SIGNATURES.items():
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = L
+    return _lib
+
+
+class GfdtdError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__("%s: %s" % (_STATUS.get(status, status), msg))
+        self.status = status
+
+
+def _f64(a):
+    return np.ascontiguousarray(np.asarray(a, dtype=np.float64))
+
+
+def _ptr(a):
+    return a.ctypes.data_as(_dp)
+
+
+# ------------------------------------------------------------ torch memory
+
+_alloc_refs = None
+
+
+def use_torch_allocator():
+    """Route the library's device allocations through PyTorch's caching allocator."""
+    global _alloc_refs
+    import torch
+    L = load()
+
+    def _alloc(nbytes, stream, user):
+        try:
+            return torch.cuda.caching_allocator_alloc(int(nbytes), torch.cuda.current_device(),
+                                                      stream or 0)
+        except Exception:   # noqa: BLE001 -- reported to the library as a NULL pointer
+            return None
+
+    def _free(ptr, nbytes, stream, user):
+        torch.cuda.caching_allocator_delete(ptr)
+
+    _alloc_refs = (ALLOC_FN(_alloc), FREE_FN(_free))
+    rc = L.gfdtd_set_allocator(_alloc_refs[0], _alloc_refs[1], None)
+    if rc != OK:
+        raise GfdtdError(rc, "gfdtd_set_allocator")
+
+
+def stability(S, beta, eps_r, mu_r=1.0, kind=PERTURBATION):
+    """gfdtd_stability: max |zeta| of a uniform moving medium (host computation)."""
+    out = C.c_double()
+    rc = load().gfdtd_stability(S, beta, eps_r, mu_r, kind, C.byref(out))
+    if rc != OK:
+        raise GfdtdError(rc, "gfdtd_stability")
+    return out.value
+
+
+class Simulation:
+    """A gfdtd_ctx: a batch of independent 1D instances on the current CUDA device."""
+
+    def __init__(self, nz, S, prec=F32, stream=None):
+        L = load()
+        self._L = L
+        nz = np.ascontiguousarray(np.atleast_1d(np.asarray(nz, dtype=np.int64)))
+        self.nz = nz
+        self.S = float(S)
+        self.prec = prec
+        if stream is None:
+            import torch
+            stream = torch.cuda.current_stream().cuda_stream
+        h = C.c_void_p()
+        rc = L.gfdtd_create(C.byref(h), len(nz), nz.ctypes.data_as(_i64p), self.S, prec,
+                            C.c_void_p(stream))
+        if rc != OK:
+            raise GfdtdError(rc, L.gfdtd_last_error(None).decode())
+        self._h = h
+
+    # -- helpers
+    def _check(self, rc, what):
+        if rc != OK:
+            raise GfdtdError(rc, "%s: %s" % (what, self._L.gfdtd_last_error(self._h).decode()))
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._L.gfdtd_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:   # noqa: BLE001
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    # -- ABI calls
+    def set_medium(self, inst, kind=PERTURBATION, beta=0.0, interp=LAYERS, z=(), eps=(1.0,), mu=None,
+                   allow_unstable=False):
+        eps = _f64(eps)
+        mu = _f64(np.ones_like(eps) if mu is None else mu)
+        z = _f64(z) if len(z) else np.zeros(1)
+        self._check(self._L.gfdtd_set_medium(self._h, inst, kind, float(beta), interp, len(eps), _ptr(z),
+                                             _ptr(eps), _ptr(mu), int(bool(allow_unstable))),
+                    "set_medium")
+
+    def add_source(self, inst, node, omega0, tau, t0, amp=1.0):
+        self._check(self._L.gfdtd_add_source(self._h, inst, int(node), float(omega0), float(tau),
+                                             float(t0), float(amp)), "add_source")
+
+    def add_probe(self, inst, node, omega):
+        omega = _f64(np.atleast_1d(omega))
+        pid = C.c_int()
+        self._check(self._L.gfdtd_add_probe(self._h, inst, int(node), len(omega), _ptr(omega),
+                                            C.byref(pid)), "add_probe")
+        return pid.value
+
+    def step(self, n):
+        self._check(self._L.gfdtd_step(self._h, int(n)), "step")
+
+    def step_plain(self, n):
+        self._check(self._L.gfdtd_step_plain(self._h, int(n)), "step_plain")
+
+    def read_fields(self, inst, which=FIELD_D):
+        out = np.empty(int(self.nz[inst]))
+        self._check(self._L.gfdtd_read_fields(self._h, inst, which, _ptr(out), len(out)), "read_fields")
+        return out
+
+    def write_fields(self, inst, which, values):
+        v = _f64(values)
+        self._check(self._L.gfdtd_write_fields(self._h, inst, which, _ptr(v), len(v)), "write_fields")
+
+    def state_layout(self):
+        n, eb = C.c_int64(), C.c_int()
+        offs = np.zeros(len(self.nz), dtype=np.int64)
+        self._check(self._L.gfdtd_state_layout(self._h, C.byref(n), C.byref(eb), offs.ctypes.data_as(_i64p)),
+                    "state_layout")
+        return n.value, eb.value, offs
+
+    def read_state(self, which, host_ptr, nbytes):
+        self._check(self._L.gfdtd_read_state(self._h, which, C.c_void_p(host_ptr), int(nbytes)), "read_state")
+
+    def write_state(self, which, host_ptr, nbytes):
+        self._check(self._L.gfdtd_write_state(self._h, which, C.c_void_p(host_ptr), int(nbytes)), "write_state")
+
+    def read_spectrum(self, inst, probe_id, n_bins):
+        re, im = np.zeros(n_bins), np.zeros(n_bins)
+        self._check(self._L.gfdtd_read_spectrum(self._h, inst, probe_id, _ptr(re), _ptr(im)), "read_spectrum")
+        return re + 1j * im
+
+    def steps_done(self):
+        n = C.c_int64()
+        self._check(self._L.gfdtd_steps_done(self._h, C.byref(n)), "steps_done")
+        return n.value
+
+    def set_tuning(self, cells_per_lane=0, time_block=0):
+        self._check(self._L.gfdtd_set_tuning(self._h, cells_per_lane, time_block), "set_tuning")
+
+    def stats(self):
+        s = Stats()
+        self._check(self._L.gfdtd_get_stats(self._h, C.byref(s)), "get_stats")
+        return {k: getattr(s, k) for k, _ in Stats._fields_}
+
+    def synchronize(self):
+        self._check(self._L.gfdtd_synchronize(self._h), "synchronize")

@@ -1,0 +1,907 @@
+// gfdtd_api.cu -- host implementation of the C ABI declared in include/gfdtd.h.
+//
+// A context holds a batch of independent 1D instances.  All fields live in two
+// ping-pong buffers per field (B, D) of padded per-instance segments; the
+// moving-medium profiles live in small tables; time stepping is enqueued in
+// chunks of at most kChunk steps, each chunk being [source amplitudes ->
+// time-block launches -> DFT fold -> step counter advance], captured once
+// per (chunk length, buffer parity) into a CUDA graph and replayed.
+#include "../../include/gfdtd.h"
+#include "gfdtd_internal.cuh"
+
+#include <algorithm>
+#include <cmath>
+#include <complex>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <string>
+#include <utility>
+#include <vector>
+
+namespace gfdtd {
+int block_shapes(int prec, int* C, int* TB, int max);
+}
+
+using namespace gfdtd;
+
+namespace {
+
+constexpr int kChunk = 1024;           // steps per chunk (probe/source buffers hold one chunk)
+constexpr int kBlock = 128;            // threads per block of the batched kernel
+
+gfdtd_alloc_fn g_alloc = nullptr;
+gfdtd_free_fn g_free = nullptr;
+void* g_user = nullptr;
+std::string g_create_error;
+
+int elem_bytes_of(gfdtd_prec p) {
+  switch (p) {
+    case GFDTD_F32: return 4;
+    case GFDTD_BF16: case GFDTD_F16: return 2;
+    case GFDTD_F64: return 8;
+    default: return 0;
+  }
+}
+
+long long to_fixed(double x) { return llround(ldexp(x, 32)); }
+
+struct Medium {
+  gfdtd_kind kind = GFDTD_PERTURBATION;
+  double beta = 0.0;
+  gfdtd_interp interp = GFDTD_LAYERS;
+  std::vector<double> z, eps{1.0}, mu{1.0};
+};
+
+struct Probe {
+  int inst;
+  long long node;
+  std::vector<double> omega;
+};
+
+struct DevBuf {
+  void* p = nullptr;
+  size_t bytes = 0;
+};
+
+}  // namespace
+
+struct gfdtd_ctx {
+  int n_inst = 0;
+  double S = 0.5;
+  gfdtd_prec prec = GFDTD_F32;
+  int eb = 4;
+  cudaStream_t stream = nullptr;
+  cudaStream_t cap_stream = nullptr;   // internal stream used only for graph capture
+  gfdtd_alloc_fn alloc = nullptr;
+  gfdtd_free_fn free_fn = nullptr;
+  void* user = nullptr;
+  std::string err;
+
+  std::vector<long long> nz, off;
+  long long total = 0;                 // elements per field buffer
+  std::vector<Medium> media;
+  std::vector<std::vector<SrcDev>> sources;   // per instance
+  std::vector<Probe> probes;                  // in creation order
+  std::vector<std::vector<int>> inst_probes;  // per instance: indices into `probes`
+
+  // device state
+  DevBuf B[2], D[2];
+  int cur = 0;                          // buffer holding the current state
+  DevBuf d_ndone;
+  long long n_done = 0;
+
+  // device tables (rebuilt by finalize)
+  bool dirty = true;
+  DevBuf d_inst, d_zq, d_tabE, d_tabH, d_srcs, d_prbs, d_amp, d_samples, d_omega, d_binprb,
+      d_acc_re, d_acc_im, d_tiles[2], d_tmp;
+  std::vector<InstDev> h_inst;
+  std::vector<int> prb_global;          // probe creation index -> global (instance-sorted) index
+  std::vector<int> prb_bin0;
+  int n_src = 0, n_prb = 0, n_bins = 0;
+  std::vector<double> acc_keep_re, acc_keep_im;   // accumulators per creation-order bin
+
+  // tiling
+  int C = 0, TB = 0;                    // chosen tile shape (0 = autotune)
+  bool tuned = false;
+  int n_tiles[2] = {0, 0};              // [perturbation, matter]
+  int grid[2] = {0, 0};
+  int num_sms = 0;
+
+  // graphs keyed by (chunk length, parity)
+  std::map<std::pair<int, int>, cudaGraphExec_t> graphs;
+  long long launches = 0;
+};
+
+// ------------------------------------------------------------------ helpers
+
+static gfdtd_status fail(gfdtd_ctx* c, gfdtd_status s, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  if (c) c->err = buf; else g_create_error = buf;
+  return s;
+}
+
+#define CK(ctx, call)                                                                   \
+  do {                                                                                  \
+    cudaError_t e_ = (call);                                                            \
+    if (e_ != cudaSuccess)                                                              \
+      return fail(ctx, GFDTD_E_CUDA, "%s: %s (%s:%d)", #call, cudaGetErrorString(e_),    \
+                  __FILE__, __LINE__);                                                  \
+  } while (0)
+
+#define CKI(ctx, expr)                                                                  \
+  do {                                                                                  \
+    int e_ = (expr);                                                                    \
+    if (e_ != 0)                                                                        \
+      return fail(ctx, GFDTD_E_CUDA, "%s: %s (%s:%d)", #expr,                            \
+                  cudaGetErrorString((cudaError_t)e_), __FILE__, __LINE__);             \
+  } while (0)
+
+static gfdtd_status dalloc(gfdtd_ctx* c, DevBuf& b, size_t bytes) {
+  if (b.p && b.bytes >= bytes && bytes > 0) return GFDTD_OK;
+  if (b.p) {
+    if (c->free_fn) c->free_fn(b.p, b.bytes, c->stream, c->user);
+    else cudaFree(b.p);
+    b.p = nullptr;
+    b.bytes = 0;
+  }
+  if (bytes == 0) return GFDTD_OK;
+  if (c->alloc) {
+    b.p = c->alloc(bytes, c->stream, c->user);
+    if (!b.p) return fail(c, GFDTD_E_OOM, "device allocation of %zu bytes failed", bytes);
+  } else {
+    cudaError_t e = cudaMalloc(&b.p, bytes);
+    if (e != cudaSuccess) {
+      b.p = nullptr;
+      cudaGetLastError();
+      return fail(c, GFDTD_E_OOM, "cudaMalloc(%zu): %s", bytes, cudaGetErrorString(e));
+    }
+  }
+  b.bytes = bytes;
+  return GFDTD_OK;
+}
+
+static void dfree(gfdtd_ctx* c, DevBuf& b) {
+  if (!b.p) return;
+  if (c->free_fn) c->free_fn(b.p, b.bytes, c->stream, c->user);
+  else cudaFree(b.p);
+  b.p = nullptr;
+  b.bytes = 0;
+}
+
+template <typename V>
+static gfdtd_status upload(gfdtd_ctx* c, DevBuf& b, const std::vector<V>& v) {
+  const size_t bytes = std::max<size_t>(v.size() * sizeof(V), 16);
+  gfdtd_status s = dalloc(c, b, bytes);
+  if (s) return s;
+  if (!v.empty()) CK(c, cudaMemcpyAsync(b.p, v.data(), v.size() * sizeof(V), cudaMemcpyHostToDevice, c->stream));
+  return GFDTD_OK;
+}
+
+static void drop_graphs(gfdtd_ctx* c) {
+  for (auto& kv : c->graphs) cudaGraphExecDestroy(kv.second);
+  c->graphs.clear();
+}
+
+// Host von Neumann amplification (Sec. 5): 2x2 matrix of one Fourier mode.
+static double max_zeta(double S, double beta, double ie, double im, double bc) {
+  using cd = std::complex<double>;
+  const cd I(0.0, 1.0);
+  double worst = 0.0;
+  const int nth = 4096;
+  for (int i = 1; i <= nth; ++i) {
+    const double th = M_PI * i / nth;
+    cd bsum, adv;
+    if (beta >= 0) { bsum = std::exp(-0.5 * I * th) + std::exp(-1.5 * I * th); adv = 1.0 - std::exp(-I * th); }
+    else { bsum = std::exp(1.5 * I * th) + std::exp(0.5 * I * th); adv = std::exp(I * th) - 1.0; }
+    const cd curl = 2.0 * I * std::sin(th / 2);
+    const double avg = std::cos(th / 2);
+    // E* = ie D - bc bsum/2 B;  B' = (1 - beta S adv) B - S curl E*
+    const cd EsB = -bc * 0.5 * bsum, EsD = ie;
+    const cd BB = 1.0 - beta * S * adv - S * curl * EsB, BD = -S * curl * EsD;
+    // H* = im B' - bc avg D;  D' = (1 - beta S adv) D - S curl H*
+    const cd HB = im * BB, HD = im * BD - bc * avg;
+    const cd DB = -S * curl * HB, DD = 1.0 - beta * S * adv - S * curl * HD;
+    const cd tr = BB + DD, det = BB * DD - BD * DB;
+    const cd disc = std::sqrt(tr * tr - 4.0 * det);
+    worst = std::max(worst, std::max(std::abs(0.5 * (tr + disc)), std::abs(0.5 * (tr - disc))));
+  }
+  return worst;
+}
+
+static void medium_coefs(gfdtd_kind kind, double beta, double e, double m, double* ie, double* im,
+                         double* bc) {
+  if (kind == GFDTD_PERTURBATION) {
+    *ie = 1.0 / e; *im = 1.0 / m; *bc = beta;
+    return;
+  }
+  const double den = e * m - beta * beta, g = 1.0 - beta * beta;
+  *ie = g * m / den; *im = g * e / den; *bc = beta * g / den;
+}
+
+// ------------------------------------------------------------------ finalize
+
+static gfdtd_status build_tiles(gfdtd_ctx* c, int C, int TB, std::vector<int2> out[2]) {
+  out[0].clear(); out[1].clear();
+  for (int i = 0; i < c->n_inst; ++i) {
+    const bool pos = c->media[i].beta >= 0.0;
+    const int W = 32 * C - (pos ? 4 * TB : 3 * TB);
+    const int kindx = c->media[i].kind == GFDTD_MATTER ? 1 : 0;
+    for (long long x0 = 0; x0 < c->nz[i]; x0 += W) out[kindx].push_back(make_int2(i, (int)x0));
+  }
+  if (out[0].size() + out[1].size() > (size_t)INT32_MAX)
+    return fail(c, GFDTD_E_ARG, "too many tiles");
+  return GFDTD_OK;
+}
+
+static gfdtd_status set_tiles(gfdtd_ctx* c, int C, int TB) {
+  std::vector<int2> t[2];
+  gfdtd_status s = build_tiles(c, C, TB, t);
+  if (s) return s;
+  for (int k = 0; k < 2; ++k) {
+    s = upload(c, c->d_tiles[k], t[k]);
+    if (s) return s;
+    c->n_tiles[k] = (int)t[k].size();
+    int nb = 0;
+    CKI(c, block_occupancy(c->prec, k, C, TB, kBlock, &nb));
+    nb = std::max(nb, 1);
+    const int want = (c->n_tiles[k] + (kBlock / 32) - 1) / (kBlock / 32);
+    c->grid[k] = std::max(1, std::min(c->num_sms * nb, want));
+  }
+  c->C = C;
+  c->TB = TB;
+  drop_graphs(c);
+  return GFDTD_OK;
+}
+
+static gfdtd_status finalize(gfdtd_ctx* c) {
+  if (!c->dirty) return GFDTD_OK;
+  const double S = c->S;
+  // preserve accumulators of existing probes across a rebuild
+  if (c->n_bins > 0) {
+    std::vector<double> re(c->n_bins), im(c->n_bins);
+    CK(c, cudaMemcpyAsync(re.data(), c->d_acc_re.p, c->n_bins * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    CK(c, cudaMemcpyAsync(im.data(), c->d_acc_im.p, c->n_bins * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    CK(c, cudaStreamSynchronize(c->stream));
+    size_t pos = 0;
+    c->acc_keep_re.assign(c->acc_keep_re.size(), 0.0);
+    // old layout: global probe order; map back to creation order
+    for (size_t p = 0; p < c->prb_global.size(); ++p) {
+      const int g = c->prb_global[p];
+      const int b0 = c->prb_bin0[g];
+      const size_t nb = c->probes[p].omega.size();
+      for (size_t j = 0; j < nb; ++j) {
+        c->acc_keep_re[pos + j] = re[b0 + j];
+        c->acc_keep_im[pos + j] = im[b0 + j];
+      }
+      pos += nb;
+    }
+  }
+  std::vector<InstDev> inst(c->n_inst);
+  std::vector<long long> zq;
+  std::vector<double2> tabE, tabH;
+  std::vector<SrcDev> srcs;
+  std::vector<PrbDev> prbs;
+  std::vector<double> omega, acc_re, acc_im;
+  std::vector<int> binprb;
+  c->prb_global.assign(c->probes.size(), 0);
+  c->prb_bin0.clear();
+  // creation-order bin offsets of each probe
+  std::vector<size_t> keep_off(c->probes.size() + 1, 0);
+  for (size_t p = 0; p < c->probes.size(); ++p) keep_off[p + 1] = keep_off[p] + c->probes[p].omega.size();
+  for (int i = 0; i < c->n_inst; ++i) {
+    const Medium& m = c->media[i];
+    InstDev& d = inst[i];
+    d.off = c->off[i];
+    d.nz = (int)c->nz[i];
+    d.nz_pad = (int)((c->nz[i] + 31) / 32 * 32);
+    d.dq = llround(ldexp(m.beta * S, 31));
+    d.n = (int)m.eps.size();
+    d.tab = (int)tabE.size();
+    d.a = 1.0 - std::fabs(m.beta) * S;
+    d.c = std::fabs(m.beta) * S;
+    d.S = S;
+    d.inv_S = 1.0 / S;
+    d.beta = m.beta;
+    d.cb = 0.5 * S * m.beta;
+    int flags = 0;
+    if (m.beta >= 0.0) flags |= F_POS;
+    if (m.kind == GFDTD_MATTER) flags |= F_MATTER;
+    const int nvals = (int)m.eps.size();
+    if (m.interp == GFDTD_LINEAR) {
+      flags |= F_LINEAR;
+      for (int k = 0; k < nvals; ++k) {
+        zq.push_back(to_fixed(m.z[k]));
+        tabE.push_back(make_double2(m.eps[k], m.mu[k]));
+        tabH.push_back(make_double2(m.eps[k], m.mu[k]));
+      }
+    } else {
+      bool econst = true, mconst = true;
+      for (int k = 0; k < nvals; ++k) {
+        if (k < nvals - 1) zq.push_back(to_fixed(m.z[k]));
+        double ie, im, bc;
+        medium_coefs(m.kind, m.beta, m.eps[k], m.mu[k], &ie, &im, &bc);
+        const double2 e = make_double2(S * ie, 0.5 * S * bc);
+        const double2 h = make_double2(S * im, 0.5 * S * bc);
+        if (k > 0 && (e.x != tabE[d.tab].x || e.y != tabE[d.tab].y)) econst = false;
+        if (k > 0 && (h.x != tabH[d.tab].x || h.y != tabH[d.tab].y)) mconst = false;
+        tabE.push_back(e);
+        tabH.push_back(h);
+      }
+      while (zq.size() < tabE.size()) zq.push_back(0);   // keep zq aligned with the tables
+      if (econst) flags |= F_EPS_CONST;
+      if (mconst) flags |= F_MU_CONST;
+    }
+    while (zq.size() < tabE.size()) zq.push_back(0);
+    d.flags = flags;
+    d.src0 = (int)srcs.size();
+    d.nsrc = (int)c->sources[i].size();
+    for (const SrcDev& s : c->sources[i]) srcs.push_back(s);
+    d.prb0 = (int)prbs.size();
+    d.nprb = (int)c->inst_probes[i].size();
+    for (int p : c->inst_probes[i]) {
+      const Probe& pr = c->probes[p];
+      PrbDev pd;
+      pd.inst = i;
+      pd.node = (int)pr.node;
+      pd.nbins = (int)pr.omega.size();
+      pd.bin0 = (int)omega.size();
+      c->prb_global[p] = (int)prbs.size();
+      c->prb_bin0.push_back(pd.bin0);
+      for (size_t j = 0; j < pr.omega.size(); ++j) {
+        omega.push_back(pr.omega[j]);
+        binprb.push_back((int)prbs.size());
+        acc_re.push_back(c->acc_keep_re[keep_off[p] + j]);
+        acc_im.push_back(c->acc_keep_im[keep_off[p] + j]);
+      }
+      prbs.push_back(pd);
+    }
+  }
+  c->h_inst = inst;
+  c->n_src = (int)srcs.size();
+  c->n_prb = (int)prbs.size();
+  c->n_bins = (int)omega.size();
+  gfdtd_status s;
+  if ((s = upload(c, c->d_inst, inst)) || (s = upload(c, c->d_zq, zq)) || (s = upload(c, c->d_tabE, tabE)) ||
+      (s = upload(c, c->d_tabH, tabH)) || (s = upload(c, c->d_srcs, srcs)) ||
+      (s = upload(c, c->d_prbs, prbs)) || (s = upload(c, c->d_omega, omega)) ||
+      (s = upload(c, c->d_binprb, binprb)) || (s = upload(c, c->d_acc_re, acc_re)) ||
+      (s = upload(c, c->d_acc_im, acc_im)))
+    return s;
+  if ((s = dalloc(c, c->d_amp, std::max<size_t>(16, (size_t)c->n_src * kChunk * sizeof(double)))) ||
+      (s = dalloc(c, c->d_samples, std::max<size_t>(16, (size_t)c->n_prb * kChunk * sizeof(double)))))
+    return s;
+  c->dirty = false;
+  drop_graphs(c);
+  if (c->C > 0) {
+    s = set_tiles(c, c->C, c->TB);
+    if (s) return s;
+  }
+  return GFDTD_OK;
+}
+
+// ------------------------------------------------------------ enqueueing
+
+static Tables tables_of(gfdtd_ctx* c) {
+  Tables t;
+  t.zq = (const long long*)c->d_zq.p;
+  t.tabE = (const double2*)c->d_tabE.p;
+  t.tabH = (const double2*)c->d_tabH.p;
+  return t;
+}
+
+// Enqueue one time-block launch (both kinds) reading buffer `from`.
+static gfdtd_status enqueue_block(gfdtd_ctx* c, cudaStream_t st, int from, int s0, int nsteps,
+                                  bool record, bool sources) {
+  for (int k = 0; k < 2; ++k) {
+    if (c->n_tiles[k] == 0) continue;
+    // BlockArgs<T> has the same layout for every T (pointers), so fill the float version
+    BlockArgs<float> a;
+    a.inst = (const InstDev*)c->d_inst.p;
+    a.tiles = (const int2*)c->d_tiles[k].p;
+    a.n_tiles = c->n_tiles[k];
+    a.tb = tables_of(c);
+    a.srcs = (const SrcDev*)c->d_srcs.p;
+    a.src_amp = sources ? (const double*)c->d_amp.p : nullptr;
+    a.prbs = (const PrbDev*)c->d_prbs.p;
+    a.samples = (double*)c->d_samples.p;
+    a.chunk_stride = kChunk;
+    a.Bin = (const float*)c->B[from].p;
+    a.Din = (const float*)c->D[from].p;
+    a.Bout = (float*)c->B[1 - from].p;
+    a.Dout = (float*)c->D[1 - from].p;
+    a.n_done = (const long long*)c->d_ndone.p;
+    a.s0 = s0;
+    a.nsteps = nsteps;
+    a.record = record ? 1 : 0;
+    CKI(c, block_launch(c->prec, k, c->C, c->TB, &a, c->grid[k], kBlock, st));
+    ++c->launches;
+  }
+  return GFDTD_OK;
+}
+
+static gfdtd_status enqueue_fold_advance(gfdtd_ctx* c, cudaStream_t st, int nsteps) {
+  if (c->n_bins > 0) {
+    FoldArgs f;
+    f.prbs = (const PrbDev*)c->d_prbs.p;
+    f.n_prb = c->n_prb;
+    f.samples = (const double*)c->d_samples.p;
+    f.chunk_stride = kChunk;
+    f.nsteps = nsteps;
+    f.n_done = (const long long*)c->d_ndone.p;
+    f.omega = (const double*)c->d_omega.p;
+    f.bin_probe = (const int*)c->d_binprb.p;
+    f.n_bins_total = c->n_bins;
+    f.acc_re = (double*)c->d_acc_re.p;
+    f.acc_im = (double*)c->d_acc_im.p;
+    f.S = c->S;
+    CKI(c, fold_launch(f, st));
+    ++c->launches;
+  }
+  CKI(c, advance_launch((long long*)c->d_ndone.p, nsteps, st));
+  ++c->launches;
+  return GFDTD_OK;
+}
+
+// One chunk of the batched path; returns the number of block launches (for parity).
+static gfdtd_status enqueue_chunk(gfdtd_ctx* c, cudaStream_t st, int from, int nsteps, int* nlaunch) {
+  if (c->n_src > 0) {
+    CKI(c, src_amp_launch((const SrcDev*)c->d_srcs.p, c->n_src, (double*)c->d_amp.p, kChunk, nsteps,
+                          (const long long*)c->d_ndone.p, c->S, st));
+    ++c->launches;
+  }
+  int b = from, m = 0;
+  for (int s0 = 0; s0 < nsteps; s0 += c->TB) {
+    gfdtd_status s = enqueue_block(c, st, b, s0, std::min(c->TB, nsteps - s0), true, true);
+    if (s) return s;
+    b = 1 - b;
+    ++m;
+  }
+  *nlaunch = m;
+  return enqueue_fold_advance(c, st, nsteps);
+}
+
+static gfdtd_status run_chunk(gfdtd_ctx* c, int nsteps) {
+  const auto key = std::make_pair(nsteps, c->cur);
+  auto it = c->graphs.find(key);
+  int m = (nsteps + c->TB - 1) / c->TB;
+  if (it == c->graphs.end()) {
+    cudaGraph_t g = nullptr;
+    CK(c, cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal));
+    const long long before = c->launches;
+    gfdtd_status s = enqueue_chunk(c, c->cap_stream, c->cur, nsteps, &m);
+    cudaError_t e = cudaStreamEndCapture(c->cap_stream, &g);
+    if (s) { if (g) cudaGraphDestroy(g); return s; }
+    CK(c, e);
+    c->launches = before;   // counted at replay
+    cudaGraphExec_t ex = nullptr;
+    e = cudaGraphInstantiate(&ex, g, 0);
+    cudaGraphDestroy(g);
+    CK(c, e);
+    it = c->graphs.emplace(key, ex).first;
+  }
+  CK(c, cudaGraphLaunch(it->second, c->stream));
+  const int kinds = (c->n_tiles[0] > 0) + (c->n_tiles[1] > 0);
+  c->launches += (long long)m * kinds + (c->n_src > 0) + (c->n_bins > 0) + 1;
+  if (m & 1) c->cur = 1 - c->cur;
+  c->n_done += nsteps;
+  return GFDTD_OK;
+}
+
+// Time the candidate tile shapes on the actual batch (reads the current
+// buffer, writes the other, records nothing) and keep the fastest.
+static gfdtd_status autotune(gfdtd_ctx* c) {
+  int Cs[16], TBs[16];
+  const int n = block_shapes(c->prec, Cs, TBs, 16);
+  if (n == 0) return fail(c, GFDTD_E_UNSUPPORTED, "no tile shape built for this precision");
+  if (n == 1) return set_tiles(c, Cs[0], TBs[0]);
+  cudaEvent_t e0, e1;
+  CK(c, cudaEventCreate(&e0));
+  CK(c, cudaEventCreate(&e1));
+  double best = 1e300;
+  int bi = 0;
+  for (int i = 0; i < n; ++i) {
+    gfdtd_status s = set_tiles(c, Cs[i], TBs[i]);
+    if (s) return s;
+    s = enqueue_block(c, c->stream, c->cur, 0, TBs[i], false, false);
+    if (s) return s;
+    CK(c, cudaEventRecord(e0, c->stream));
+    const int reps = 3;
+    for (int r = 0; r < reps; ++r) {
+      s = enqueue_block(c, c->stream, c->cur, 0, TBs[i], false, false);
+      if (s) return s;
+    }
+    CK(c, cudaEventRecord(e1, c->stream));
+    CK(c, cudaEventSynchronize(e1));
+    float ms = 0.f;
+    CK(c, cudaEventElapsedTime(&ms, e0, e1));
+    const double per_step = ms / (reps * TBs[i]);
+    if (per_step < best) { best = per_step; bi = i; }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  return set_tiles(c, Cs[bi], TBs[bi]);
+}
+
+static gfdtd_status check_inst(gfdtd_ctx* c, int inst) {
+  if (!c) return GFDTD_E_ARG;
+  if (inst < 0 || inst >= c->n_inst) return fail(c, GFDTD_E_ARG, "instance %d out of range", inst);
+  return GFDTD_OK;
+}
+
+// ================================================================== the ABI
+
+extern "C" {
+
+gfdtd_status gfdtd_set_allocator(gfdtd_alloc_fn alloc, gfdtd_free_fn free_fn, void* user) {
+  if ((alloc == nullptr) != (free_fn == nullptr)) return GFDTD_E_ARG;
+  g_alloc = alloc;
+  g_free = free_fn;
+  g_user = user;
+  return GFDTD_OK;
+}
+
+gfdtd_status gfdtd_create(gfdtd_ctx** out, int n_inst, const int64_t* nz, double S,
+                          gfdtd_prec prec, void* cuda_stream) {
+  if (!out) return fail(nullptr, GFDTD_E_ARG, "out is NULL");
+  *out = nullptr;
+  if (n_inst < 1 || !nz) return fail(nullptr, GFDTD_E_ARG, "need n_inst >= 1 and nz");
+  if (!(S > 0.0 && S <= 1.0)) return fail(nullptr, GFDTD_E_ARG, "S must be in (0, 1]");
+  if (prec == GFDTD_F32_KAHAN) return fail(nullptr, GFDTD_E_UNSUPPORTED, "F32_KAHAN is not built");
+  const int eb = elem_bytes_of(prec);
+  if (eb == 0) return fail(nullptr, GFDTD_E_ARG, "unknown precision %d", (int)prec);
+  for (int i = 0; i < n_inst; ++i)
+    if (nz[i] < 1 || nz[i] > (1LL << 28))
+      return fail(nullptr, GFDTD_E_ARG, "nz[%d] = %lld out of [1, 2^28]", i, (long long)nz[i]);
+  gfdtd_ctx* c = new (std::nothrow) gfdtd_ctx;
+  if (!c) return fail(nullptr, GFDTD_E_OOM, "host allocation failed");
+  c->n_inst = n_inst;
+  c->S = S;
+  c->prec = prec;
+  c->eb = eb;
+  c->stream = (cudaStream_t)cuda_stream;
+  c->alloc = g_alloc;
+  c->free_fn = g_free;
+  c->user = g_user;
+  c->nz.assign(nz, nz + n_inst);
+  c->off.resize(n_inst);
+  long long o = 0;
+  for (int i = 0; i < n_inst; ++i) {
+    c->off[i] = o;
+    o += (nz[i] + 31) / 32 * 32;
+  }
+  c->total = o + 32;   // one spare padded segment
+  c->media.assign(n_inst, Medium());
+  c->sources.assign(n_inst, {});
+  c->inst_probes.assign(n_inst, {});
+  int dev = 0;
+  gfdtd_status s = GFDTD_OK;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, dev);
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking);
+  if (e != cudaSuccess) {
+    g_create_error = std::string("CUDA initialisation failed: ") + cudaGetErrorString(e);
+    delete c;
+    return GFDTD_E_CUDA;
+  }
+  const size_t bytes = (size_t)c->total * eb;
+  for (int k = 0; k < 2 && !s; ++k) {
+    s = dalloc(c, c->B[k], bytes);
+    if (!s) s = dalloc(c, c->D[k], bytes);
+  }
+  if (!s) s = dalloc(c, c->d_ndone, 16);
+  if (!s) {
+    for (int k = 0; k < 2; ++k) {
+      cudaMemsetAsync(c->B[k].p, 0, bytes, c->stream);
+      cudaMemsetAsync(c->D[k].p, 0, bytes, c->stream);
+    }
+    cudaMemsetAsync(c->d_ndone.p, 0, 16, c->stream);
+    if (cudaGetLastError() != cudaSuccess) s = fail(c, GFDTD_E_CUDA, "memset failed");
+  }
+  if (s) {
+    g_create_error = c->err;
+    gfdtd_destroy(c);
+    return s;
+  }
+  *out = c;
+  return GFDTD_OK;
+}
+
+gfdtd_status gfdtd_set_medium(gfdtd_ctx* c, int inst, gfdtd_kind kind, double beta,
+                              gfdtd_interp interp, int n, const double* z, const double* eps_r,
+                              const double* mu_r, int allow_unstable) {
+  gfdtd_status s = check_inst(c, inst);
+  if (s) return s;
+  if (kind != GFDTD_PERTURBATION && kind != GFDTD_MATTER) return fail(c, GFDTD_E_ARG, "bad kind");
+  if (interp != GFDTD_LAYERS && interp != GFDTD_LINEAR) return fail(c, GFDTD_E_ARG, "bad interp");
+  if (!(beta > -1.0 && beta < 1.0)) return fail(c, GFDTD_E_ARG, "beta must be in (-1, 1)");
+  if (std::fabs(beta) * c->S >= 1.0) return fail(c, GFDTD_E_ARG, "|beta| S must be < 1");
+  if (n < 1 || (interp == GFDTD_LINEAR && n < 2) || !eps_r || !mu_r)
+    return fail(c, GFDTD_E_ARG, "need n >= 1 values (n >= 2 knots for LINEAR)");
+  const int nz_pos = interp == GFDTD_LAYERS ? n - 1 : n;
+  if (nz_pos > 0 && !z) return fail(c, GFDTD_E_ARG, "z is NULL");
+  for (int i = 0; i < n; ++i)
+    if (!(eps_r[i] > 0.0) || !(mu_r[i] > 0.0)) return fail(c, GFDTD_E_ARG, "eps and mu must be > 0");
+  for (int i = 0; i < nz_pos; ++i) {
+    if (!std::isfinite(z[i]) || std::fabs(z[i]) > 1e9) return fail(c, GFDTD_E_ARG, "bad position");
+    if (i > 0 && !(z[i] > z[i - 1])) return fail(c, GFDTD_E_ARG, "positions must increase");
+  }
+  if (!allow_unstable) {
+    for (int i = 0; i < n; ++i) {
+      bool seen = false;   // each distinct (eps, mu) pair is analysed once
+      for (int j = 0; j < i && !seen; ++j) seen = eps_r[j] == eps_r[i] && mu_r[j] == mu_r[i];
+      if (seen) continue;
+      double ie, im, bc;
+      medium_coefs(kind, beta, eps_r[i], mu_r[i], &ie, &im, &bc);
+      const double g = max_zeta(c->S, beta, ie, im, bc);
+      if (g > 1.0 + 1e-9)
+        return fail(c, GFDTD_E_UNSTABLE, "eps=%g mu=%g beta=%g: max|zeta| = %.9f > 1 (n|beta| > 1)",
+                    eps_r[i], mu_r[i], beta, g);
+    }
+  }
+  Medium& m = c->media[inst];
+  m.kind = kind;
+  m.beta = beta;
+  m.interp = interp;
+  m.z.assign(z ? z : eps_r, (z ? z : eps_r) + (z ? nz_pos : 0));
+  m.eps.assign(eps_r, eps_r + n);
+  m.mu.assign(mu_r, mu_r + n);
+  c->dirty = true;
+  return GFDTD_OK;
+}
+
+gfdtd_status gfdtd_add_source(gfdtd_ctx* c, int inst, int64_t node, double omega0, double tau,
+                              double t0, double amp) {
+  gfdtd_status s = check_inst(c, inst);
+  if (s) return s;
+  if (node < 0 || node >= c->nz[inst]) return fail(c, GFDTD_E_ARG, "source node out of range");
+  if (!(tau > 0.0) || !std::isfinite(omega0) || !std::isfinite(t0) || !std::isfinite(amp))
+    return fail(c, GFDTD_E_ARG, "bad source parameters");
+  if (c->sources[inst].size() >= 32) return fail(c, GFDTD_E_ARG, "at most 32 sources per instance");
+  SrcDev d;
+  d.inst = inst;
+  d.node = (int)node;
+  d.omega0 = omega0;
+  d.tau = tau;
+  d.t0 = t0;
+  d.amp = amp;
+  c->sources[inst].push_back(d);
+  c->dirty = true;
+  return GFDTD_OK;
+}
+
+gfdtd_status gfdtd_add_probe(gfdtd_ctx* c, int inst, int64_t node, int n_bins, const double* omega,
+                             int* probe_id) {
+  gfdtd_status s = check_inst(c, inst);
+  if (s) return s;
+  if (node < 0 || node >= c->nz[inst]) return fail(c, GFDTD_E_ARG, "probe node out of range");
+  if (n_bins < 1 || !omega || !probe_id) return fail(c, GFDTD_E_ARG, "need n_bins >= 1, omega, probe_id");
+  if (c->inst_probes[inst].size() >= 32) return fail(c, GFDTD_E_ARG, "at most 32 probes per instance");
+  Probe p;
+  p.inst = inst;
+  p.node = node;
+  p.omega.assign(omega, omega + n_bins);
+  c->probes.push_back(p);
+  c->inst_probes[inst].push_back((int)c->probes.size() - 1);
+  c->acc_keep_re.resize(c->acc_keep_re.size() + n_bins, 0.0);
+  c->acc_keep_im.resize(c->acc_keep_im.size() + n_bins, 0.0);
+  *probe_id = (int)c->inst_probes[inst].size() - 1;
+  c->dirty = true;
+  return GFDTD_OK;
+}
+
+gfdtd_status gfdtd_step(gfdtd_ctx* c, int64_t n_steps) {
+  if (!c) return GFDTD_E_ARG;
+  if (n_steps < 0) return fail(c, GFDTD_E_ARG, "n_steps < 0");
+  gfdtd_status s = finalize(c);
+  if (s) return s;
+  if (c->C == 0) {
+    s = autotune(c);
+    if (s) return s;
+  }
+  while (n_steps > 0) {
+    const int ch = (int)std::min<int64_t>(n_steps, kChunk);
+    s = run_chunk(c, ch);
+    if (s) return s;
+    n_steps -= ch;
+  }
+  return GFDTD_OK;
+}
+
+gfdtd_status gfdtd_step_plain(gfdtd_ctx* c, int64_t n_steps) {
+  if (!c) return GFDTD_E_ARG;
+  if (n_steps < 0) return fail(c, GFDTD_E_ARG, "n_steps < 0");
+  gfdtd_status s = finalize(c);
+  if (s) return s;
+  while (n_steps > 0) {
+    const int ch = (int)std::min<int64_t>(n_steps, kChunk);
+    for (int st = 0; st < ch; ++st) {
+      for (int i = 0; i < c->n_inst; ++i) {
+        PlainArgs<float> a;
+        a.inst = (const InstDev*)c->d_inst.p;
+        a.i = i;
+        a.tb = tables_of(c);
+        a.srcs = (const SrcDev*)c->d_srcs.p;
+        a.prbs = (const PrbDev*)c->d_prbs.p;
+        a.samples = (double*)c->d_samples.p;
+        a.chunk_stride = kChunk;
+        a.s = st;
+        a.n = c->n_done + st + 1;
+        a.Bin = (const float*)c->B[c->cur].p;
+        a.Din = (const float*)c->D[c->cur].p;
+        a.Bout = (float*)c->B[1 - c->cur].p;
+        a.Dout = (float*)c->D[1 - c->cur].p;
+        CKI(c, plain_launch(c->prec, &a, (int)c->nz[i], c->stream));
+        ++c->launches;
+      }
+      c->cur = 1 - c->cur;
+    }
+    s = enqueue_fold_advance(c, c->stream, ch);
+    if (s) return s;
+    c->n_done += ch;
+    n_steps -= ch;
+  }
+  return GFDTD_OK;
+}
+
+gfdtd_status gfdtd_read_fields(gfdtd_ctx* c, int inst, gfdtd_field which, double* dst, int64_t n) {
+  gfdtd_status s = check_inst(c, inst);
+  if (s) return s;
+  if (!dst || n != c->nz[inst]) return fail(c, GFDTD_E_ARG, "n must equal nz and dst non-NULL");
+  if (which < GFDTD_FIELD_D || which > GFDTD_FIELD_ESTAR) return fail(c, GFDTD_E_ARG, "bad field");
+  if (which == GFDTD_FIELD_H && c->media[inst].kind == GFDTD_MATTER)
+    return fail(c, GFDTD_E_UNSUPPORTED, "H is not available for moving matter");
+  s = finalize(c);
+  if (s) return s;
+  s = dalloc(c, c->d_tmp, (size_t)n * sizeof(double));
+  if (s) return s;
+  const size_t o = (size_t)c->off[inst] * c->eb;
+  if (which == GFDTD_FIELD_D || which == GFDTD_FIELD_B) {
+    const DevBuf& b = which == GFDTD_FIELD_D ? c->D[c->cur] : c->B[c->cur];
+    CKI(c, convert_launch(c->prec, 1, (const char*)b.p + o, c->d_tmp.p, n, c->stream));
+  } else {
+    CKI(c, derived_launch(c->prec, (int)which, (const InstDev*)c->d_inst.p, inst, tables_of(c),
+                          c->B[c->cur].p, c->D[c->cur].p, (double*)c->d_tmp.p, (int)n, c->n_done,
+                          c->stream));
+  }
+  CK(c, cudaMemcpyAsync(dst, c->d_tmp.p, (size_t)n * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+  CK(c, cudaStreamSynchronize(c->stream));
+  return GFDTD_OK;
+}
+
+gfdtd_status gfdtd_write_fields(gfdtd_ctx* c, int inst, gfdtd_field which, const double* src, int64_t n) {
+  gfdtd_status s = check_inst(c, inst);
+  if (s) return s;
+  if (!src || n != c->nz[inst]) return fail(c, GFDTD_E_ARG, "n must equal nz and src non-NULL");
+  if (which != GFDTD_FIELD_D && which != GFDTD_FIELD_B) return fail(c, GFDTD_E_ARG, "only D or B can be written");
+  s = dalloc(c, c->d_tmp, (size_t)n * sizeof(double));
+  if (s) return s;
+  CK(c, cudaMemcpyAsync(c->d_tmp.p, src, (size_t)n * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+  const DevBuf& b = which == GFDTD_FIELD_D ? c->D[c->cur] : c->B[c->cur];
+  CKI(c, convert_launch(c->prec, 0, c->d_tmp.p, (char*)b.p + (size_t)c->off[inst] * c->eb, n, c->stream));
+  CK(c, cudaStreamSynchronize(c->stream));
+  return GFDTD_OK;
+}
+
+gfdtd_status gfdtd_state_layout(const gfdtd_ctx* c, int64_t* n_elems, int* elem_bytes, int64_t* offsets) {
+  if (!c) return GFDTD_E_ARG;
+  if (n_elems) *n_elems = c->total;
+  if (elem_bytes) *elem_bytes = c->eb;
+  if (offsets) for (int i = 0; i < c->n_inst; ++i) offsets[i] = c->off[i];
+  return GFDTD_OK;
+}
+
+gfdtd_status gfdtd_read_state(gfdtd_ctx* c, gfdtd_field which, void* dst, int64_t bytes) {
+  if (!c) return GFDTD_E_ARG;
+  if (which != GFDTD_FIELD_D && which != GFDTD_FIELD_B) return fail(c, GFDTD_E_ARG, "only D or B");
+  if (!dst || bytes != c->total * c->eb) return fail(c, GFDTD_E_ARG, "bytes must be %lld", c->total * c->eb);
+  const DevBuf& b = which == GFDTD_FIELD_D ? c->D[c->cur] : c->B[c->cur];
+  CK(c, cudaMemcpyAsync(dst, b.p, (size_t)bytes, cudaMemcpyDeviceToHost, c->stream));
+  return GFDTD_OK;
+}
+
+gfdtd_status gfdtd_write_state(gfdtd_ctx* c, gfdtd_field which, const void* src, int64_t bytes) {
+  if (!c) return GFDTD_E_ARG;
+  if (which != GFDTD_FIELD_D && which != GFDTD_FIELD_B) return fail(c, GFDTD_E_ARG, "only D or B");
+  if (!src || bytes != c->total * c->eb) return fail(c, GFDTD_E_ARG, "bytes must be %lld", c->total * c->eb);
+  const DevBuf& b = which == GFDTD_FIELD_D ? c->D[c->cur] : c->B[c->cur];
+  CK(c, cudaMemcpyAsync(b.p, src, (size_t)bytes, cudaMemcpyHostToDevice, c->stream));
+  return GFDTD_OK;
+}
+
+gfdtd_status gfdtd_read_spectrum(gfdtd_ctx* c, int inst, int probe_id, double* re, double* im) {
+  gfdtd_status s = check_inst(c, inst);
+  if (s) return s;
+  if (probe_id < 0 || probe_id >= (int)c->inst_probes[inst].size() || !re || !im)
+    return fail(c, GFDTD_E_ARG, "bad probe id or NULL output");
+  s = finalize(c);
+  if (s) return s;
+  const int p = c->inst_probes[inst][probe_id];
+  const int g = c->prb_global[p];
+  const int b0 = c->prb_bin0[g];
+  const size_t nb = c->probes[p].omega.size();
+  CK(c, cudaMemcpyAsync(re, (double*)c->d_acc_re.p + b0, nb * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+  CK(c, cudaMemcpyAsync(im, (double*)c->d_acc_im.p + b0, nb * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+  CK(c, cudaStreamSynchronize(c->stream));
+  return GFDTD_OK;
+}
+
+gfdtd_status gfdtd_steps_done(const gfdtd_ctx* c, int64_t* n) {
+  if (!c || !n) return GFDTD_E_ARG;
+  *n = c->n_done;
+  return GFDTD_OK;
+}
+
+gfdtd_status gfdtd_stability(double S, double beta, double eps_r, double mu_r, gfdtd_kind kind,
+                             double* out) {
+  if (!out || !(S > 0.0 && S <= 1.0) || !(beta > -1.0 && beta < 1.0) || !(eps_r > 0.0) || !(mu_r > 0.0))
+    return GFDTD_E_ARG;
+  if (kind != GFDTD_PERTURBATION && kind != GFDTD_MATTER) return GFDTD_E_ARG;
+  double ie, im, bc;
+  medium_coefs(kind, beta, eps_r, mu_r, &ie, &im, &bc);
+  *out = max_zeta(S, beta, ie, im, bc);
+  return GFDTD_OK;
+}
+
+gfdtd_status gfdtd_set_tuning(gfdtd_ctx* c, int cells_per_lane, int time_block) {
+  if (!c) return GFDTD_E_ARG;
+  if (cells_per_lane == 0 && time_block == 0) {
+    c->C = 0;
+    c->TB = 0;
+    drop_graphs(c);
+    return GFDTD_OK;
+  }
+  int Cs[16], TBs[16];
+  const int n = block_shapes(c->prec, Cs, TBs, 16);
+  for (int i = 0; i < n; ++i) {
+    if (Cs[i] == cells_per_lane && TBs[i] == time_block) {
+      gfdtd_status s = finalize(c);
+      if (s) return s;
+      return set_tiles(c, cells_per_lane, time_block);
+    }
+  }
+  return fail(c, GFDTD_E_UNSUPPORTED, "tile shape %d x %d not built for this precision",
+              cells_per_lane, time_block);
+}
+
+gfdtd_status gfdtd_get_stats(const gfdtd_ctx* c, gfdtd_stats* out) {
+  if (!c || !out) return GFDTD_E_ARG;
+  out->cells_per_lane = c->C;
+  out->time_block = c->TB;
+  out->n_tiles = (int64_t)c->n_tiles[0] + c->n_tiles[1];
+  out->kernel_launches = c->launches;
+  long long cells = 0;
+  for (long long v : c->nz) cells += v;
+  out->cells = cells;
+  return GFDTD_OK;
+}
+
+gfdtd_status gfdtd_synchronize(gfdtd_ctx* c) {
+  if (!c) return GFDTD_E_ARG;
+  CK(c, cudaStreamSynchronize(c->stream));
+  return GFDTD_OK;
+}
+
+const char* gfdtd_last_error(const gfdtd_ctx* c) {
+  return c ? c->err.c_str() : g_create_error.c_str();
+}
+
+void gfdtd_destroy(gfdtd_ctx* c) {
+  if (!c) return;
+  cudaStreamSynchronize(c->stream);
+  drop_graphs(c);
+  DevBuf* bufs[] = {&c->B[0], &c->B[1], &c->D[0], &c->D[1], &c->d_ndone, &c->d_inst, &c->d_zq,
+                    &c->d_tabE, &c->d_tabH, &c->d_srcs, &c->d_prbs, &c->d_amp, &c->d_samples,
+                    &c->d_omega, &c->d_binprb, &c->d_acc_re, &c->d_acc_im, &c->d_tiles[0],
+                    &c->d_tiles[1], &c->d_tmp};
+  for (DevBuf* b : bufs) dfree(c, *b);
+  if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
+  delete c;
+}
+
+}  // extern "C"

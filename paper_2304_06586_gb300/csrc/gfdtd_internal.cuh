@@ -1,0 +1,133 @@
+// gfdtd_internal.cuh -- device-side data layout shared by the kernels and the
+// host API of the generalized-FDTD engine (not part of the public ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <stdint.h>
+
+namespace gfdtd {
+
+// Instance flags.
+enum : int {
+  F_POS = 1,         // beta >= 0: Table 1 first column (Ba, dBa, dDa); else second column
+  F_MATTER = 2,      // moving matter: per-node coupling beta_c (see gfdtd.h)
+  F_LINEAR = 4,      // piecewise-linear profile (per-cell interpolation)
+  F_MU_CONST = 8,    // layers profile whose H-side coefficients are all equal
+  F_EPS_CONST = 16,  // layers profile whose E-side coefficients are all equal
+};
+
+// One instance of the batch, as the kernels see it.
+struct InstDev {
+  long long off;     // element offset of cell 0 in the field arrays (multiple of 32)
+  long long dq;      // moving-frame displacement per half step, units of 2^-32 cell
+  int nz;            // cells
+  int nz_pad;        // nz rounded up to a multiple of 32
+  int flags;
+  int n;             // layers (LAYERS) or knots (LINEAR)
+  int tab;           // first entry of this instance in the profile tables
+  int src0, nsrc;    // sources: global indices [src0, src0 + nsrc)
+  int prb0, nprb;    // probes: global indices [prb0, prb0 + nprb)
+  double a;          // 1 - |beta| S   (upwind difference weight of the centre cell)
+  double c;          // |beta| S       (weight of the upwind neighbour)
+  double S;          // Courant number
+  double inv_S;
+  double beta;
+  double cb;         // S beta / 2: coupling in the Table 1 averages (moving perturbation)
+};
+
+// Profile tables (concatenated over instances).
+//   zq[tab + i]   : boundary (LAYERS, i < n-1) or knot (LINEAR, i < n) in 2^-32 cell
+//   tabE[tab + i] : LAYERS: (S/eps_eff, S beta_c / 2) of layer i at integer nodes
+//                   LINEAR: (eps, mu) at knot i
+//   tabH[tab + i] : LAYERS: (S/mu_eff, S beta_c / 2) of layer i at half nodes
+struct Tables {
+  const long long* zq;
+  const double2* tabE;
+  const double2* tabH;
+};
+
+struct SrcDev {
+  int inst;
+  int node;
+  double omega0, tau, t0, amp;
+};
+
+struct PrbDev {
+  int inst;
+  int node;
+  int nbins;
+  int bin0;          // first bin in the omega / accumulator arrays
+};
+
+// Arguments of one time-block launch of the batched kernel.
+template <typename T>
+struct BlockArgs {
+  const InstDev* inst;
+  const int2* tiles;          // (instance, x0) of every tile
+  int n_tiles;
+  Tables tb;
+  const SrcDev* srcs;
+  const double* src_amp;      // [source][step in chunk]
+  const PrbDev* prbs;
+  double* samples;            // [probe][step in chunk]
+  int chunk_stride;           // row length of src_amp and samples
+  const T* Bin;
+  const T* Din;
+  T* Bout;
+  T* Dout;
+  const long long* n_done;    // steps completed at the start of the chunk (device)
+  int s0;                     // first step of this launch within the chunk
+  int nsteps;                 // steps in this launch (<= time block)
+  int record;                 // nonzero: write probe samples
+};
+
+// Arguments of the plain kernel (one instance, one step).
+template <typename T>
+struct PlainArgs {
+  const InstDev* inst;
+  int i;                      // instance index
+  Tables tb;
+  const SrcDev* srcs;
+  const PrbDev* prbs;
+  double* samples;
+  int chunk_stride;
+  int s;                      // step within the chunk
+  long long n;                // the step being taken (1-based)
+  const T* Bin;
+  const T* Din;
+  T* Bout;
+  T* Dout;
+};
+
+struct FoldArgs {
+  const PrbDev* prbs;
+  int n_prb;
+  const double* samples;
+  int chunk_stride;
+  int nsteps;                 // samples per probe in this chunk
+  const long long* n_done;    // steps completed at the start of the chunk
+  const double* omega;        // all bins
+  const int* bin_probe;       // probe of every bin
+  int n_bins_total;
+  double* acc_re;
+  double* acc_im;
+  double S;
+};
+
+// Kernel launchers (gfdtd_kernels.cu).
+int block_launch(int prec, int matter, int C, int TB, const void* args, int grid, int block,
+                 cudaStream_t st);
+int block_occupancy(int prec, int matter, int C, int TB, int block, int* blocks_per_sm);
+int block_shapes(int prec, int* C, int* TB, int max);   // tile shapes built for a precision
+int plain_launch(int prec, const void* args, int nz, cudaStream_t st);
+int src_amp_launch(const SrcDev* srcs, int nsrc, double* amp, int stride, int nsteps,
+                   const long long* n_done, double S, cudaStream_t st);
+int fold_launch(const FoldArgs& a, cudaStream_t st);
+int advance_launch(long long* n_done, long long by, cudaStream_t st);
+int convert_launch(int prec, int to_double, const void* src, void* dst, long long n, cudaStream_t st);
+int derived_launch(int prec, int which, const InstDev* inst, int i, Tables tb, const void* B,
+                   const void* D, double* out, int nz, long long n_done, cudaStream_t st);
+
+}  // namespace gfdtd

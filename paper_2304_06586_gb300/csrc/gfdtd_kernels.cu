@@ -1,0 +1,293 @@
+// gfdtd_kernels.cu -- the plain one-step kernel, source amplitudes, running
+// DFT probes, state conversions and the dispatch to the batched kernels.
+#include "gfdtd_block.cuh"
+
+namespace gfdtd {
+
+int block_launch_f32(int, int, int, const void*, int, int, cudaStream_t);
+int block_launch_bf16(int, int, int, const void*, int, int, cudaStream_t);
+int block_launch_f16(int, int, int, const void*, int, int, cudaStream_t);
+int block_launch_f64(int, int, int, const void*, int, int, cudaStream_t);
+int block_occupancy_f32(int, int, int, int, int*);
+int block_occupancy_bf16(int, int, int, int, int*);
+int block_occupancy_f16(int, int, int, int, int*);
+int block_occupancy_f64(int, int, int, int, int*);
+int block_shapes_f32(int*, int*, int);
+int block_shapes_bf16(int*, int*, int);
+int block_shapes_f16(int*, int*, int);
+int block_shapes_f64(int*, int*, int);
+
+// prec takes the values of gfdtd_prec: 0 F32, 2 BF16, 3 F16, 4 F64.
+int block_launch(int prec, int matter, int C, int TB, const void* args, int grid, int block,
+                 cudaStream_t st) {
+  switch (prec) {
+    case 0: return block_launch_f32(matter, C, TB, args, grid, block, st);
+    case 2: return block_launch_bf16(matter, C, TB, args, grid, block, st);
+    case 3: return block_launch_f16(matter, C, TB, args, grid, block, st);
+    case 4: return block_launch_f64(matter, C, TB, args, grid, block, st);
+  }
+  return (int)cudaErrorInvalidValue;
+}
+
+int block_occupancy(int prec, int matter, int C, int TB, int block, int* nb) {
+  switch (prec) {
+    case 0: return block_occupancy_f32(matter, C, TB, block, nb);
+    case 2: return block_occupancy_bf16(matter, C, TB, block, nb);
+    case 3: return block_occupancy_f16(matter, C, TB, block, nb);
+    case 4: return block_occupancy_f64(matter, C, TB, block, nb);
+  }
+  return (int)cudaErrorInvalidValue;
+}
+
+int block_shapes(int prec, int* C, int* TB, int max) {
+  switch (prec) {
+    case 0: return block_shapes_f32(C, TB, max);
+    case 2: return block_shapes_bf16(C, TB, max);
+    case 3: return block_shapes_f16(C, TB, max);
+    case 4: return block_shapes_f64(C, TB, max);
+  }
+  return 0;
+}
+
+// ------------------------------------------------------------ plain kernel
+//
+// One thread per cell, one step per launch, one instance per launch.  Every
+// thread recomputes from the old fields in HBM the E', B' and H' values its D
+// update needs, and finds the material of each node by binary search.
+
+template <bool MATTER, typename T>
+__device__ void plain_cell(const PlainArgs<T>& A, const InstDev& I, int k) {
+  using R = typename Real<T>::type;
+  const int nz = I.nz;
+  const T* __restrict__ Bi = A.Bin + I.off;
+  const T* __restrict__ Di = A.Din + I.off;
+  auto ld = [&](const T* p, int j) -> R { return (j >= 0 && j < nz) ? (R)p[j] : (R)0; };
+  const bool pos = (I.flags & F_POS) != 0;
+  const R a = (R)I.a, cc = (R)I.c;
+  const long long n = A.n;
+  const long long offE = I.dq * (2 * n - 1), offH = I.dq * (2 * n) - HALF_CELL;
+
+  auto Ep = [&](int j) -> R {   // E' at node j, level n-1/2
+    if (j < 0 || j >= nz) return (R)0;
+    R se, cb;
+    node_coef<MATTER, true>(I, A.tb, offE, j, se, cb);
+    const R bs = pos ? ld(Bi, j - 1) + ld(Bi, j - 2) : ld(Bi, j) + ld(Bi, j + 1);
+    return se * ld(Di, j) - cb * bs;
+  };
+  auto Bn = [&](int j) -> R {   // B^n at half node j
+    if (j < 0 || j >= nz) return (R)0;
+    const R bu = pos ? ld(Bi, j - 1) : ld(Bi, j + 1);
+    return a * ld(Bi, j) + (cc * bu + (Ep(j) - Ep(j + 1)));
+  };
+  auto Hp = [&](int j, R bn) -> R {   // H' at half node j, level n
+    if (j < 0 || j >= nz) return (R)0;
+    R sm, cb;
+    node_coef<MATTER, false>(I, A.tb, offH, j, sm, cb);
+    return sm * bn - cb * (ld(Di, j) + ld(Di, j + 1));
+  };
+  const R bk = Bn(k), bkm = Bn(k - 1);
+  const R du = pos ? ld(Di, k - 1) : ld(Di, k + 1);
+  R d = a * ld(Di, k) + (cc * du + (Hp(k - 1, bkm) - Hp(k, bk)));
+  const double t = (double)(2 * n + 1) * I.S * 0.5;
+  for (int q = 0; q < I.nsrc; ++q) {
+    const SrcDev sd = A.srcs[I.src0 + q];
+    if (sd.node == k) {
+      const double u = t - sd.t0;
+      d += (R)(sd.amp * sin(sd.omega0 * u) * exp(-(u / sd.tau) * (u / sd.tau)));
+    }
+  }
+  for (int q = 0; q < I.nprb; ++q) {
+    if (A.prbs[I.prb0 + q].node == k) {
+      R se, cb;
+      node_coef<MATTER, true>(I, A.tb, I.dq * (2 * n + 1), k, se, cb);
+      R F = d * se;
+      if (MATTER) {
+        const R bbar = pos ? (R)0.5 * (bkm + Bn(k - 2)) : (R)0.5 * (bk + Bn(k + 1));
+        F += ((R)I.beta * (R)I.S - (R)2 * cb) * bbar;
+      }
+      A.samples[(long long)(I.prb0 + q) * A.chunk_stride + A.s] = (double)(F * (R)I.inv_S);
+    }
+  }
+  A.Bout[I.off + k] = (T)bk;
+  A.Dout[I.off + k] = (T)d;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) plain_kernel(const PlainArgs<T> A) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  const InstDev I = A.inst[A.i];
+  if (k >= I.nz) return;
+  if (I.flags & F_MATTER) plain_cell<true>(A, I, k);
+  else plain_cell<false>(A, I, k);
+}
+
+template <typename T>
+static int plain_t(const void* args, int nz, cudaStream_t st) {
+  const int bs = 256;
+  plain_kernel<T><<<(nz + bs - 1) / bs, bs, 0, st>>>(*static_cast<const PlainArgs<T>*>(args));
+  return (int)cudaGetLastError();
+}
+
+int plain_launch(int prec, const void* args, int nz, cudaStream_t st) {
+  switch (prec) {
+    case 0: return plain_t<float>(args, nz, st);
+    case 2: return plain_t<__nv_bfloat16>(args, nz, st);
+    case 3: return plain_t<__half>(args, nz, st);
+    case 4: return plain_t<double>(args, nz, st);
+  }
+  return (int)cudaErrorInvalidValue;
+}
+
+// ------------------------------------------------- sources, DFT, bookkeeping
+
+// Source amplitudes of one chunk of steps, s(t_{n+1/2}) for n = n_done + 1 ...
+__global__ void src_amp_kernel(const SrcDev* srcs, int nsrc, double* amp, int stride, int nsteps,
+                               const long long* n_done, double S) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= nsrc * nsteps) return;
+  const int q = i / nsteps, s = i % nsteps;
+  const long long n = *n_done + s + 1;
+  const SrcDev sd = srcs[q];
+  const double t = (double)(2 * n + 1) * S * 0.5;
+  const double u = t - sd.t0;
+  amp[(long long)q * stride + s] = sd.amp * sin(sd.omega0 * u) * exp(-(u / sd.tau) * (u / sd.tau));
+}
+
+int src_amp_launch(const SrcDev* srcs, int nsrc, double* amp, int stride, int nsteps,
+                   const long long* n_done, double S, cudaStream_t st) {
+  const int total = nsrc * nsteps;
+  if (total == 0) return 0;
+  src_amp_kernel<<<(total + 255) / 256, 256, 0, st>>>(srcs, nsrc, amp, stride, nsteps, n_done, S);
+  return (int)cudaGetLastError();
+}
+
+// X(w) += sum_s F_s exp(i w t_s) S over one chunk of samples, one thread per
+// bin.  The phasor advances by a fixed rotation exp(i w S) and is recomputed
+// directly every 64 samples, so its error stays at the level of FP64 rounding.
+__global__ void fold_kernel(const FoldArgs A) {
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= A.n_bins_total) return;
+  const int p = A.bin_probe[b];
+  const double* __restrict__ f = A.samples + (long long)p * A.chunk_stride;
+  const double w = A.omega[b];
+  const long long n1 = *A.n_done + 1;
+  double rs, rc;
+  sincos(w * A.S, &rs, &rc);
+  double re = 0.0, im = 0.0, pc = 0.0, ps = 0.0;
+  for (int s = 0; s < A.nsteps; ++s) {
+    if ((s & 63) == 0) {
+      const double t = (double)(2 * (n1 + s) + 1) * A.S * 0.5;
+      sincos(w * t, &ps, &pc);
+    } else {
+      const double nc = pc * rc - ps * rs;
+      ps = ps * rc + pc * rs;
+      pc = nc;
+    }
+    const double F = __ldg(f + s);
+    re = fma(F, pc, re);
+    im = fma(F, ps, im);
+  }
+  A.acc_re[b] += re * A.S;
+  A.acc_im[b] += im * A.S;
+}
+
+int fold_launch(const FoldArgs& a, cudaStream_t st) {
+  if (a.n_bins_total == 0 || a.nsteps == 0) return 0;
+  fold_kernel<<<(a.n_bins_total + 127) / 128, 128, 0, st>>>(a);
+  return (int)cudaGetLastError();
+}
+
+__global__ void advance_kernel(long long* n_done, long long by) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) *n_done += by;
+}
+
+int advance_launch(long long* n_done, long long by, cudaStream_t st) {
+  advance_kernel<<<1, 32, 0, st>>>(n_done, by);
+  return (int)cudaGetLastError();
+}
+
+// ------------------------------------------------------------- conversions
+
+template <typename T>
+__global__ void to_double_kernel(const T* src, double* dst, long long n) {
+  const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (i < n) dst[i] = (double)(typename Real<T>::type)src[i];
+}
+template <typename T>
+__global__ void from_double_kernel(const double* src, T* dst, long long n) {
+  const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (i < n) dst[i] = (T)(typename Real<T>::type)src[i];
+}
+
+template <typename T>
+static int convert_t(int to_double, const void* src, void* dst, long long n, cudaStream_t st) {
+  if (n == 0) return 0;
+  const unsigned blocks = (unsigned)((n + 255) / 256);
+  if (to_double) to_double_kernel<T><<<blocks, 256, 0, st>>>((const T*)src, (double*)dst, n);
+  else from_double_kernel<T><<<blocks, 256, 0, st>>>((const double*)src, (T*)dst, n);
+  return (int)cudaGetLastError();
+}
+
+int convert_launch(int prec, int to_double, const void* src, void* dst, long long n, cudaStream_t st) {
+  switch (prec) {
+    case 0: return convert_t<float>(to_double, src, dst, n, st);
+    case 2: return convert_t<__nv_bfloat16>(to_double, src, dst, n, st);
+    case 3: return convert_t<__half>(to_double, src, dst, n, st);
+    case 4: return convert_t<double>(to_double, src, dst, n, st);
+  }
+  return (int)cudaErrorInvalidValue;
+}
+
+// Derived fields of one instance at the state (B^n, D^{n+1/2}), in FP64:
+// which 2 = E (level n+1/2), 3 = H (level n, moving perturbation), 4 = E*.
+template <bool MATTER, typename T>
+__device__ void derived_cell(int which, const InstDev& I, const Tables& tb, const T* Bi,
+                             const T* Di, double* out, long long n, int k) {
+  using R = typename Real<T>::type;
+  auto ld = [&](const T* p, int j) -> double {
+    return (j >= 0 && j < I.nz) ? (double)(R)p[j] : 0.0;
+  };
+  if (which == 3) {
+    double sm, cb;
+    node_coef<MATTER, false>(I, tb, I.dq * (2 * n) - HALF_CELL, k, sm, cb);
+    out[k] = ld(Bi, k) * sm / I.S;
+    return;
+  }
+  double se, cb;
+  node_coef<MATTER, true>(I, tb, I.dq * (2 * n + 1), k, se, cb);
+  const bool pos = (I.flags & F_POS) != 0;
+  const double bbar = pos ? 0.5 * (ld(Bi, k - 1) + ld(Bi, k - 2)) : 0.5 * (ld(Bi, k) + ld(Bi, k + 1));
+  const double estar = (se * ld(Di, k) - 2.0 * cb * bbar) / I.S;
+  out[k] = which == 4 ? estar : estar + I.beta * bbar;
+}
+
+template <typename T>
+__global__ void derived_kernel(int which, const InstDev* inst, int i, Tables tb, const T* B,
+                               const T* D, double* out, long long n) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  const InstDev I = inst[i];
+  if (k >= I.nz) return;
+  if (I.flags & F_MATTER) derived_cell<true>(which, I, tb, B + I.off, D + I.off, out, n, k);
+  else derived_cell<false>(which, I, tb, B + I.off, D + I.off, out, n, k);
+}
+
+template <typename T>
+static int derived_t(int which, const InstDev* inst, int i, Tables tb, const void* B, const void* D,
+                     double* out, int nz, long long n, cudaStream_t st) {
+  derived_kernel<T><<<(nz + 255) / 256, 256, 0, st>>>(which, inst, i, tb, (const T*)B, (const T*)D,
+                                                      out, n);
+  return (int)cudaGetLastError();
+}
+
+int derived_launch(int prec, int which, const InstDev* inst, int i, Tables tb, const void* B,
+                   const void* D, double* out, int nz, long long n, cudaStream_t st) {
+  switch (prec) {
+    case 0: return derived_t<float>(which, inst, i, tb, B, D, out, nz, n, st);
+    case 2: return derived_t<__nv_bfloat16>(which, inst, i, tb, B, D, out, nz, n, st);
+    case 3: return derived_t<__half>(which, inst, i, tb, B, D, out, nz, n, st);
+    case 4: return derived_t<double>(which, inst, i, tb, B, D, out, nz, n, st);
+  }
+  return (int)cudaErrorInvalidValue;
+}
+
+}  // namespace gfdtd

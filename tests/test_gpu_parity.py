@@ -1,0 +1,243 @@
+"""GPU parity: the CUDA path (through the C ABI) against the FP64 oracle.
+
+Tolerance: relative L2 <= 1e-4 for FP32 fields and spectra (the bar the
+method's target states); FP64 tier <= 1e-11; 16-bit storage tiers are
+reported with a loose bound.  Inputs are seeded; sizes span several tiles
+with ragged tails; both signs of v, zero v, narrow layers (several
+boundaries per lane), non-uniform mu, moving matter and piecewise-linear
+profiles are covered.
+"""
+import numpy as np
+import pytest
+
+from helpers import make_oracle, make_sim, rel_l2
+from paper_2304_06586_gb300 import binding as gb
+from paper_2304_06586_gb300 import workloads as w
+
+pytestmark = pytest.mark.gpu
+
+TOL32 = 1e-4
+SHAPES = [(16, 8), (16, 16), (16, 32), (8, 16)]
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _gpu():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    gb.load()
+
+
+def _mixed_workload(seed=7, kind=w.PERTURBATION, interp=w.LAYERS):
+    """Ragged instances: tiny, tile-boundary and multi-tile sizes, both signs of v."""
+    rng = np.random.default_rng(seed)
+    sizes = [1, 7, 32, 33, 100, 517, 1000, 3001, 9000, 20000]
+    betas = [0.3, -0.3, 0.0, 0.45, -0.45, 0.2, -0.1, 0.49, -0.49, 0.33]
+    out = []
+    for nz, v in zip(sizes, betas):
+        if interp == w.LAYERS:
+            nl = int(rng.integers(1, 12))
+            # include narrow layers (down to 2 cells) so a lane sees several boundaries
+            widths = rng.integers(2, 60, size=nl - 1) if nl > 1 else np.zeros(0)
+            z = rng.uniform(-0.2, 0.5) * nz + np.cumsum(widths) + rng.uniform(0, 1)
+            eps = rng.uniform(1.0, 4.0, size=nl)
+            mu = rng.uniform(1.0, 1.5, size=nl) if rng.uniform() < 0.5 else np.ones(nl)
+        else:
+            nk = int(rng.integers(2, 40))
+            z = np.sort(rng.uniform(-0.1, 0.9, size=nk)) * nz + np.arange(nk) * 0.7
+            eps = rng.uniform(1.0, 4.0, size=nk)
+            mu = np.ones(nk)
+        srcs = [w.gaussian_source(int(rng.integers(0, nz)), 20.0, 3.0)] if nz > 50 else []
+        prbs = [(int(rng.integers(0, nz)), np.linspace(0.1, 0.5, 5))] if nz > 50 else []
+        if nz > 50:
+            prbs.append((nz - 1, np.linspace(0.2, 0.4, 3)))
+        out.append(w.InstanceSpec(nz=nz, beta=v, kind=kind, interp=interp, z=np.asarray(z, float),
+                                  eps=eps, mu=mu, sources=srcs, probes=prbs))
+    return w.Workload("mixed", 0.5, 0, out)
+
+
+def storage_round(x, prec):
+    """Round on the host to the field storage precision, so both sides start alike."""
+    if prec == gb.F32:
+        return x.astype(np.float32).astype(np.float64)
+    if prec == gb.F16:
+        return x.astype(np.float16).astype(np.float64)
+    if prec == gb.BF16:
+        import torch
+        return torch.from_numpy(x).to(torch.bfloat16).to(torch.float64).numpy()
+    return x
+
+
+def _seed_fields(wl, sim, orcs, seed=11):
+    rng = np.random.default_rng(seed)
+    for k, I in enumerate(wl.instances):
+        B, D = (storage_round(f, sim.prec) for f in w.random_fields(I.nz, rng))
+        sim.write_fields(k, gb.FIELD_B, B)
+        sim.write_fields(k, gb.FIELD_D, D)
+        orcs[k].B[:] = B
+        orcs[k].D[:] = D
+
+
+def _compare(wl, sim, orcs, tol, spectra=True):
+    worst = 0.0
+    for k, I in enumerate(wl.instances):
+        for which, ref in ((gb.FIELD_B, orcs[k].B), (gb.FIELD_D, orcs[k].D)):
+            e = rel_l2(sim.read_fields(k, which), ref)
+            worst = max(worst, e)
+            assert e <= tol, (k, I.nz, I.beta, which, e)
+        if spectra:
+            for p, (node, om) in enumerate(I.probes):
+                e = rel_l2(sim.read_spectrum(k, p, len(om)), orcs[k].spectrum(p))
+                worst = max(worst, e)
+                assert e <= tol, (k, "probe", p, e)
+    return worst
+
+
+@pytest.mark.parametrize("shape", SHAPES)
+@pytest.mark.parametrize("kind", [w.PERTURBATION, w.MATTER])
+def test_batched_layers_random_fields(shape, kind):
+    wl = _mixed_workload(kind=kind)
+    sim = make_sim(wl, tuning=shape)
+    orcs = make_oracle(wl)
+    _seed_fields(wl, sim, orcs)
+    n = 3 * shape[1] + 5          # several time blocks and a partial one
+    sim.step(n)
+    for o in orcs:
+        o.run(n)
+    assert sim.steps_done() == n
+    _compare(wl, sim, orcs, TOL32)
+
+
+@pytest.mark.parametrize("kind", [w.PERTURBATION, w.MATTER])
+def test_batched_linear_profiles(kind):
+    wl = _mixed_workload(seed=8, kind=kind, interp=w.LINEAR)
+    sim = make_sim(wl, tuning=(16, 16))
+    orcs = make_oracle(wl)
+    _seed_fields(wl, sim, orcs)
+    sim.step(53)
+    for o in orcs:
+        o.run(53)
+    _compare(wl, sim, orcs, TOL32)
+
+
+@pytest.mark.parametrize("kind", [w.PERTURBATION, w.MATTER])
+def test_plain_kernel_matches_oracle(kind):
+    wl = _mixed_workload(seed=9, kind=kind)
+    sim = make_sim(wl)
+    orcs = make_oracle(wl)
+    _seed_fields(wl, sim, orcs)
+    sim.step_plain(21)
+    for o in orcs:
+        o.run(21)
+    _compare(wl, sim, orcs, TOL32)
+
+
+def test_chunking_and_shapes_are_bitwise_consistent():
+    """The result does not depend on how steps are grouped into calls, chunks or tiles."""
+    wl = _mixed_workload(seed=10)
+    res = []
+    for shape, parts in (((16, 16), [1500]), ((16, 16), [700, 3, 797]), ((16, 8), [1500]),
+                         ((8, 16), [1024, 476])):
+        sim = make_sim(wl, tuning=shape)
+        rng = np.random.default_rng(3)
+        for k, I in enumerate(wl.instances):
+            B, D = (storage_round(f, gb.F32) for f in w.random_fields(I.nz, rng, 1e-3))
+            sim.write_fields(k, gb.FIELD_B, B)
+            sim.write_fields(k, gb.FIELD_D, D)
+        for p in parts:
+            sim.step(p)
+        res.append([sim.read_fields(k, gb.FIELD_D) for k in range(len(wl.instances))])
+    for r in res[1:]:
+        for a, b in zip(res[0], r):
+            np.testing.assert_array_equal(a, b)
+
+
+def test_sources_and_probes_from_rest():
+    """Interface workload (Fig. 5 geometry) from zero fields: fields and DFT spectra."""
+    wl = w.config1()
+    wl.n_steps = 3000
+    sim = make_sim(wl)
+    orcs = make_oracle(wl)
+    sim.step(wl.n_steps)
+    orcs[0].run(wl.n_steps)
+    _compare(wl, sim, orcs, TOL32)
+
+
+def test_derived_fields():
+    wl = _mixed_workload(seed=12)
+    sim = make_sim(wl, tuning=(16, 16))
+    orcs = make_oracle(wl)
+    _seed_fields(wl, sim, orcs)
+    sim.step(40)
+    for o in orcs:
+        o.run(40)
+    for k, I in enumerate(wl.instances):
+        n = sim.steps_done()
+        eps = orcs[k].material("eps", False, 2 * n + 1)
+        mu = orcs[k].material("mu", True, 2 * n)
+        E = orcs[k].D / eps
+        assert rel_l2(sim.read_fields(k, gb.FIELD_E), E) <= TOL32
+        assert rel_l2(sim.read_fields(k, gb.FIELD_H), orcs[k].B / mu) <= TOL32
+        Bp = np.concatenate(([0.0, 0.0], orcs[k].B, [0.0]))
+        kk = np.arange(I.nz)
+        bbar = 0.5 * (Bp[kk + 1] + Bp[kk]) if I.beta >= 0 else 0.5 * (Bp[kk + 2] + Bp[kk + 3])
+        assert rel_l2(sim.read_fields(k, gb.FIELD_ESTAR), E - I.beta * bbar) <= TOL32
+
+
+@pytest.mark.parametrize("prec,tol", [(gb.F64, 1e-11), (gb.BF16, 3e-2), (gb.F16, 5e-3)])
+def test_precision_tiers(prec, tol):
+    wl = _mixed_workload(seed=13)
+    sim = make_sim(wl, prec=prec)
+    orcs = make_oracle(wl)
+    _seed_fields(wl, sim, orcs)
+    sim.step(64)
+    for o in orcs:
+        o.run(64)
+    worst = _compare(wl, sim, orcs, tol, spectra=(prec == gb.F64))
+    print("precision tier", prec, "worst relative L2", worst)
+
+
+def test_crystal_small_matches_oracle():
+    """Config-3 shape at reduced size (stable velocities), from rest, sources and probes."""
+    wl = w.config3(n_inst=48, nz_lo=1 << 10, nz_hi=1 << 13, n_steps=600, stable_only=True)
+    sim = make_sim(wl, allow_unstable=False)
+    orcs = make_oracle(wl)
+    sim.step(wl.n_steps)
+    import oracle
+    oracle.run_many(orcs, wl.n_steps)
+    _compare(wl, sim, orcs, TOL32)
+
+
+def test_matter_slab_reduced():
+    wl = w.config2(velocities=(-0.5, 0.0, 0.5), nz=1 << 13, n_steps=2500)
+    sim = make_sim(wl)
+    orcs = make_oracle(wl)
+    sim.step(wl.n_steps)
+    for o in orcs:
+        o.run(wl.n_steps)
+    _compare(wl, sim, orcs, TOL32)
+
+
+def test_full_size_crystal_sampled():
+    """Config 3 at full size in the benchmark's launch configuration, checked on
+    sampled instances that the oracle steps on their own."""
+    wl = w.config3(n_steps=64)
+    sim = make_sim(wl)
+    rng = np.random.default_rng(5)
+    sample = sorted(rng.choice(len(wl.instances), size=4, replace=False).tolist())
+    start = {}
+    for k in sample:
+        start[k] = [storage_round(f, gb.F32) for f in w.random_fields(wl.instances[k].nz, rng, 1.0)]
+        sim.write_fields(k, gb.FIELD_B, start[k][0])
+        sim.write_fields(k, gb.FIELD_D, start[k][1])
+    sim.step(wl.n_steps)
+    sub = w.Workload("sample", wl.S, wl.n_steps, [wl.instances[k] for k in sample])
+    orcs = make_oracle(sub)
+    for o, k in zip(orcs, sample):
+        o.B[:], o.D[:] = start[k]
+    import oracle
+    oracle.run_many(orcs, wl.n_steps)
+    for o, k in zip(orcs, sample):
+        # unstable instances (n|v| > 1) grow, relative error stays relative
+        assert rel_l2(sim.read_fields(k, gb.FIELD_D), o.D) <= TOL32
+        assert rel_l2(sim.read_fields(k, gb.FIELD_B), o.B) <= TOL32
