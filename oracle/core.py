@@ -47,6 +47,11 @@ def lib():
                               C.POINTER(_Probe), C.c_int64, C.c_int64, _dp, _dp]
         L.orc_sample_material.restype = C.c_int
         L.orc_sample_material.argtypes = [C.POINTER(_Problem), C.c_int, C.c_int, C.c_int64, _dp]
+        L.orc_step_transpose.restype = C.c_int
+        L.orc_step_transpose.argtypes = [C.POINTER(_Problem), C.c_int64, _dp, _dp, _dp, _dp, _dp, _dp]
+        L.orc_adjoint.restype = C.c_int
+        L.orc_adjoint.argtypes = [C.POINTER(_Problem), C.c_int, C.POINTER(_Source), C.POINTER(_Probe),
+                                  C.c_int64, C.c_int64, _dp, _dp, _dp, _dp]
         _lib = L
     return _lib
 
@@ -126,6 +131,36 @@ class Instance:
     def series(self, probe_id):
         s = self.probes[probe_id]["series"]
         return np.concatenate(s) if s else np.zeros(0)
+
+    def step_transpose(self, n, aBn, aDn, D_old):
+        """Transpose of step n (the linear map (B^{n-1}, D^{n-1/2}) -> (B^n, D^{n+1/2})).
+
+        Returns (aB, aD, geps) with geps[k] = dL/deps_k at level n-1/2.
+        """
+        aB, aD, g = np.zeros(self.nz), np.zeros(self.nz), np.zeros(self.nz)
+        rc = lib().orc_step_transpose(C.byref(self._problem()), int(n), _ptr(_f64(aBn)), _ptr(_f64(aDn)),
+                                      _ptr(_f64(D_old)), _ptr(aB), _ptr(aD), _ptr(g))
+        if rc != 0:
+            raise ValueError("transpose needs a moving-perturbation problem")
+        return aB, aD, g
+
+    def adjoint(self, probe_id, bins, n_steps):
+        """L = sum over `bins` of |X_f|^2 of probe `probe_id`, accumulated over the next
+        n_steps from the current state, and dL/d(eps value) of every profile value.
+        The instance's state is left unchanged."""
+        p = self.probes[probe_id]
+        om = _f64(np.asarray(p["omega"])[list(bins)])
+        scratch = np.zeros(len(om))
+        prb = _Probe(p["node"], len(om), 0, _ptr(om), _ptr(scratch), _ptr(scratch), None)
+        srcs = (_Source * max(1, len(self.sources)))(*[_Source(*s) for s in self.sources])
+        loss = C.c_double()
+        grad = np.zeros(len(self.eps))
+        rc = lib().orc_adjoint(C.byref(self._problem()), len(self.sources), srcs, C.byref(prb),
+                               self.n_done, int(n_steps), _ptr(self.B), _ptr(self.D),
+                               C.byref(loss), _ptr(grad))
+        if rc != 0:
+            raise ValueError("adjoint needs a moving-perturbation problem and n_steps >= 1")
+        return loss.value, grad
 
     def material(self, which="eps", half_node=False, h=0):
         """eps (or mu) at every node at half level ``h`` (time h*S/2)."""

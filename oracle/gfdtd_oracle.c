@@ -269,3 +269,170 @@ int orc_sample_material(const orc_problem* p, int which_field, int half_node, in
     free(zq);
     return 0;
 }
+
+/* ---- discrete adjoint (moving perturbation) ------------------------------
+ *
+ * The forward step n is linear in (B, D):
+ *   E_k  = D_k/eps_k - beta bbar_k(B)                 (level n-1/2)
+ *   B'_k = B_k - S (E_{k+1} - E_k) - beta S dB_k(B)
+ *   H_k  = B'_k/mu_k - beta (D_k + D_{k+1})/2          (level n)
+ *   D'_k = D_k - S (H_k - H_{k-1}) - beta S dD_k(D)
+ * (the source adds a constant).  orc_step_transpose applies the transpose of
+ * this map, operation by operation in reverse order, to adjoint fields
+ * (aB', aD') and returns (aB, aD); it also adds dL/deps_k at level n-1/2,
+ * i.e. aE_k * (-D_k / eps_k^2), into geps[k].  Indices outside [0, nz) are
+ * absent, exactly as the forward map's zero ghost fields.
+ */
+int orc_step_transpose(const orc_problem* p, int64_t n, const double* aBn, const double* aDn,
+                       const double* D_old, double* aB, double* aD, double* geps)
+{
+    const int64_t nz = p->nz;
+    const double beta = p->beta, S = p->S;
+    const int pos = beta >= 0.0;
+    if (p->kind != 0) return -1;
+    int nb = p->interp == 0 ? p->n - 1 : p->n;
+    int64_t* zq = (int64_t*)malloc(sizeof(int64_t) * (size_t)(nb > 0 ? nb : 1));
+    for (int i = 0; i < nb; ++i) zq[i] = to_fixed(p->z[i]);
+    orc_profile eps = {p->n, p->interp, zq, p->eps};
+    orc_profile mu = {p->n, p->interp, zq, p->mu};
+    const int64_t dq = llround(ldexp(beta * S, 31));
+    double* aH = (double*)calloc((size_t)nz, sizeof(double));
+    double* aBp = (double*)calloc((size_t)nz, sizeof(double));
+    double* aE = (double*)calloc((size_t)nz, sizeof(double));
+    for (int64_t k = 0; k < nz; ++k) { aB[k] = 0.0; aD[k] = 0.0; aBp[k] = aBn[k]; }
+
+    /* D'_k = D_k - S (H_k - H_{k-1}) - beta S dD_k(D) */
+    for (int64_t k = 0; k < nz; ++k) {
+        aD[k] += aDn[k];
+        aH[k] += -S * aDn[k];
+        if (k - 1 >= 0) aH[k - 1] += S * aDn[k];
+        if (pos) {                 /* dD_k = D_k - D_{k-1} */
+            aD[k] += -beta * S * aDn[k];
+            if (k - 1 >= 0) aD[k - 1] += beta * S * aDn[k];
+        } else {                   /* dD_k = D_{k+1} - D_k */
+            if (k + 1 < nz) aD[k + 1] += -beta * S * aDn[k];
+            aD[k] += beta * S * aDn[k];
+        }
+    }
+    /* H_k = B'_k/mu_k - beta (D_k + D_{k+1})/2 */
+    for (int64_t k = 0; k < nz; ++k) {
+        double m = profile_at(&mu, half_pos(k) - dq * (2 * n));
+        aBp[k] += aH[k] / m;
+        aD[k] += -0.5 * beta * aH[k];
+        if (k + 1 < nz) aD[k + 1] += -0.5 * beta * aH[k];
+    }
+    /* B'_k = B_k - S (E_{k+1} - E_k) - beta S dB_k(B) */
+    for (int64_t k = 0; k < nz; ++k) {
+        aB[k] += aBp[k];
+        aE[k] += S * aBp[k];
+        if (k + 1 < nz) aE[k + 1] += -S * aBp[k];
+        if (pos) {                 /* dB_k = B_k - B_{k-1} */
+            aB[k] += -beta * S * aBp[k];
+            if (k - 1 >= 0) aB[k - 1] += beta * S * aBp[k];
+        } else {                   /* dB_k = B_{k+1} - B_k */
+            if (k + 1 < nz) aB[k + 1] += -beta * S * aBp[k];
+            aB[k] += beta * S * aBp[k];
+        }
+    }
+    /* E_k = D_k/eps_k - beta bbar_k(B) */
+    for (int64_t k = 0; k < nz; ++k) {
+        double e = profile_at(&eps, node_pos(k) - dq * (2 * n - 1));
+        aD[k] += aE[k] / e;
+        if (geps) geps[k] += aE[k] * (-D_old[k] / (e * e));
+        if (pos) {                 /* bbar_k = (B_{k-1} + B_{k-2})/2 */
+            if (k - 1 >= 0) aB[k - 1] += -0.5 * beta * aE[k];
+            if (k - 2 >= 0) aB[k - 2] += -0.5 * beta * aE[k];
+        } else {                   /* bbar_k = (B_{k+1} + B_k)/2 */
+            if (k + 1 < nz) aB[k + 1] += -0.5 * beta * aE[k];
+            aB[k] += -0.5 * beta * aE[k];
+        }
+    }
+    free(aH); free(aBp); free(aE); free(zq);
+    return 0;
+}
+
+/* Add g * d eps(xi)/d value_i for the node at moving coordinate xi into grad[i]. */
+static void scatter_eps_grad(const orc_profile* pr, int64_t xi, double g, double* grad)
+{
+    if (pr->interp == 0) {
+        grad[last_at_or_below(pr->zq, pr->n - 1, xi) + 1] += g;
+        return;
+    }
+    if (xi <= pr->zq[0]) { grad[0] += g; return; }
+    if (xi >= pr->zq[pr->n - 1]) { grad[pr->n - 1] += g; return; }
+    int i = last_at_or_below(pr->zq, pr->n, xi);
+    double w = (double)(xi - pr->zq[i]) / (double)(pr->zq[i + 1] - pr->zq[i]);
+    grad[i] += g * (1.0 - w);
+    grad[i + 1] += g * w;
+}
+
+/* Loss and gradient.  From the state (B0, D0) at step n0, runs n_steps forward
+ * steps storing D after every step, forms L = sum_f |X_f|^2 of the probe's
+ * bins (X accumulated over these steps only, as in orc_run), then sweeps back
+ * with orc_step_transpose and returns dL/d(eps value i) of the profile in
+ * grad[0..n). */
+int orc_adjoint(const orc_problem* p, int n_src, const orc_source* src, const orc_probe* probe,
+                int64_t n0, int64_t n_steps, const double* B0, const double* D0,
+                double* loss, double* grad)
+{
+    const int64_t nz = p->nz;
+    const double S = p->S;
+    if (p->kind != 0 || n_steps < 1) return -1;
+    double* Dh = (double*)malloc(sizeof(double) * (size_t)nz * (size_t)(n_steps + 1));
+    double* B = (double*)malloc(sizeof(double) * (size_t)nz);
+    double* series = (double*)malloc(sizeof(double) * (size_t)n_steps);
+    double* re = (double*)calloc((size_t)probe->n_bins, sizeof(double));
+    double* im = (double*)calloc((size_t)probe->n_bins, sizeof(double));
+    memcpy(B, B0, sizeof(double) * (size_t)nz);
+    memcpy(Dh, D0, sizeof(double) * (size_t)nz);
+    orc_probe pr = *probe;
+    pr.re = re; pr.im = im; pr.series = NULL;
+    for (int64_t s = 0; s < n_steps; ++s) {
+        double* Dn = Dh + (size_t)(s + 1) * (size_t)nz;
+        memcpy(Dn, Dh + (size_t)s * (size_t)nz, sizeof(double) * (size_t)nz);
+        pr.series = series + s;
+        orc_run(p, n_src, src, 1, &pr, n0 + s, 1, B, Dn);
+    }
+    double L = 0.0;
+    for (int f = 0; f < probe->n_bins; ++f) L += re[f] * re[f] + im[f] * im[f];
+    *loss = L;
+
+    int nb = p->interp == 0 ? p->n - 1 : p->n;
+    int64_t* zq = (int64_t*)malloc(sizeof(int64_t) * (size_t)(nb > 0 ? nb : 1));
+    for (int i = 0; i < nb; ++i) zq[i] = to_fixed(p->z[i]);
+    orc_profile eps = {p->n, p->interp, zq, p->eps};
+    const int64_t dq = llround(ldexp(p->beta * S, 31));
+    for (int i = 0; i < p->n; ++i) grad[i] = 0.0;
+    double* aB = (double*)calloc((size_t)nz, sizeof(double));
+    double* aD = (double*)calloc((size_t)nz, sizeof(double));
+    double* aB0 = (double*)calloc((size_t)nz, sizeof(double));
+    double* aD0 = (double*)calloc((size_t)nz, sizeof(double));
+    double* geps = (double*)calloc((size_t)nz, sizeof(double));
+    const int64_t kp = probe->node;
+    for (int64_t s = n_steps - 1; s >= 0; --s) {
+        const int64_t n = n0 + s + 1;
+        const double t = (double)(2 * n + 1) * S * 0.5;
+        /* dL/dF_n = 2 S sum_f (Re X_f cos(w t) + Im X_f sin(w t)) */
+        double g = 0.0;
+        for (int f = 0; f < probe->n_bins; ++f) {
+            double w = probe->omega[f];
+            g += 2.0 * S * (re[f] * cos(w * t) + im[f] * sin(w * t));
+        }
+        const double* Dn = Dh + (size_t)(s + 1) * (size_t)nz;
+        if (kp >= 0 && kp < nz) {
+            /* F_n = D_kp / eps_kp (level n+1/2) */
+            double e = profile_at(&eps, node_pos(kp) - dq * (2 * n + 1));
+            aD[kp] += g / e;
+            scatter_eps_grad(&eps, node_pos(kp) - dq * (2 * n + 1), g * (-Dn[kp] / (e * e)), grad);
+        }
+        for (int64_t k = 0; k < nz; ++k) geps[k] = 0.0;
+        orc_step_transpose(p, n, aB, aD, Dh + (size_t)s * (size_t)nz, aB0, aD0, geps);
+        for (int64_t k = 0; k < nz; ++k)
+            if (geps[k] != 0.0) scatter_eps_grad(&eps, node_pos(k) - dq * (2 * n - 1), geps[k], grad);
+        memcpy(aB, aB0, sizeof(double) * (size_t)nz);
+        memcpy(aD, aD0, sizeof(double) * (size_t)nz);
+    }
+    free(Dh); free(B); free(series); free(re); free(im); free(zq);
+    free(aB); free(aD); free(aB0); free(aD0); free(geps);
+    return 0;
+}
