@@ -43,6 +43,7 @@ def parse():
     ap.add_argument("--plain-steps", type=int, default=4)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--tile", default="", help="cells_per_lane,time_block[,blocks_per_sm] (default: autotune)")
     return ap.parse_args()
 
 
@@ -176,6 +177,8 @@ def main():
     with torch.cuda.stream(stream):
         sim = gb.Simulation([i.nz for i in wl.instances], wl.S, gb.F32, stream=stream.cuda_stream)
         configure(sim, wl, gb)
+        if args.tile:
+            sim.set_tuning(*[int(x) for x in args.tile.split(",")])
         T = args.time_steps
 
         def barrier():
@@ -271,7 +274,7 @@ def main():
             "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": wl.description, "instances": len(wl.instances), "cells": cells,
-                       "time_steps_per_step": T, "tile": [st["cells_per_lane"], st["time_block"]],
+                       "time_steps_per_step": T, "tile": [st["cells_per_lane"], st["time_block"], st["blocks_per_sm"]],
                        "l2": "inputs larger than L2 (%.2f GB of fields)" % (cells * 16 / 1e9),
                        "parallelism": "instances sharded per rank" if world > 1 else "1 GPU"},
             "e2e": e2e, "gpu_launches": launches, "roofline": roofline, "plain": plain,

@@ -192,13 +192,17 @@ gfdtd_status gfdtd_steps_done(const gfdtd_ctx* ctx, int64_t* n);
 gfdtd_status gfdtd_stability(double S, double beta, double eps_r, double mu_r,
                              gfdtd_kind kind, double* max_abs_zeta);
 
-/* Tile shape of the batched kernel: cells per lane (8 or 16) and steps per
- * time block (8, 16 or 32).  0, 0 selects autotuning at the next step. */
-gfdtd_status gfdtd_set_tuning(gfdtd_ctx* ctx, int cells_per_lane, int time_block);
+/* Tile shape of the batched kernel: cells per lane (8 or 16), steps per time
+ * block (8, 16 or 32) and the number of 128-thread blocks per SM the fast
+ * kernel's registers are limited to (4 or 5; 0 = first built match).  The
+ * shapes built depend on the precision; E_UNSUPPORTED if the shape is not
+ * built.  0, 0, 0 selects autotuning at the next step. */
+gfdtd_status gfdtd_set_tuning(gfdtd_ctx* ctx, int cells_per_lane, int time_block, int blocks_per_sm);
 
 typedef struct {
     int cells_per_lane;        /* chosen tile shape */
     int time_block;
+    int blocks_per_sm;
     int64_t n_tiles;           /* tiles per time block for the whole batch */
     int64_t kernel_launches;   /* library kernels launched so far (graph nodes counted) */
     int64_t cells;             /* sum of nz */

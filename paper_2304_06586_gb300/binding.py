@@ -32,7 +32,8 @@ FREE_FN = C.CFUNCTYPE(None, C.c_void_p, C.c_size_t, C.c_void_p, C.c_void_p)
 
 
 class Stats(C.Structure):
-    _fields_ = [("cells_per_lane", C.c_int), ("time_block", C.c_int), ("n_tiles", C.c_int64),
+    _fields_ = [("cells_per_lane", C.c_int), ("time_block", C.c_int), ("blocks_per_sm", C.c_int),
+                ("n_tiles", C.c_int64),
                 ("kernel_launches", C.c_int64), ("cells", C.c_int64)]
 
 
@@ -55,7 +56,7 @@ SIGNATURES = {
     "gfdtd_read_spectrum": (C.c_int, [C.c_void_p, C.c_int, C.c_int, _dp, _dp]),
     "gfdtd_steps_done": (C.c_int, [C.c_void_p, _i64p]),
     "gfdtd_stability": (C.c_int, [C.c_double, C.c_double, C.c_double, C.c_double, C.c_int, _dp]),
-    "gfdtd_set_tuning": (C.c_int, [C.c_void_p, C.c_int, C.c_int]),
+    "gfdtd_set_tuning": (C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_int]),
     "gfdtd_get_stats": (C.c_int, [C.c_void_p, C.POINTER(Stats)]),
     "gfdtd_synchronize": (C.c_int, [C.c_void_p]),
     "gfdtd_last_error": (C.c_char_p, [C.c_void_p]),
@@ -236,8 +237,9 @@ class Simulation:
         self._check(self._L.gfdtd_steps_done(self._h, C.byref(n)), "steps_done")
         return n.value
 
-    def set_tuning(self, cells_per_lane=0, time_block=0):
-        self._check(self._L.gfdtd_set_tuning(self._h, cells_per_lane, time_block), "set_tuning")
+    def set_tuning(self, cells_per_lane=0, time_block=0, blocks_per_sm=0):
+        self._check(self._L.gfdtd_set_tuning(self._h, cells_per_lane, time_block, blocks_per_sm),
+                    "set_tuning")
 
     def stats(self):
         s = Stats()

@@ -7,7 +7,7 @@
 // time-block launches -> DFT fold -> step counter advance], captured once
 // per (chunk length, buffer parity) into a CUDA graph and replayed.
 #include "../../include/gfdtd.h"
-#include "gfdtd_internal.cuh"
+#include "gfdtd_block.cuh"
 
 #include <algorithm>
 #include <cmath>
@@ -21,7 +21,7 @@
 #include <vector>
 
 namespace gfdtd {
-int block_shapes(int prec, int* C, int* TB, int max);
+int block_shapes(int prec, int* C, int* TB, int* MB, int max);
 }
 
 using namespace gfdtd;
@@ -38,7 +38,7 @@ std::string g_create_error;
 
 int elem_bytes_of(gfdtd_prec p) {
   switch (p) {
-    case GFDTD_F32: return 4;
+    case GFDTD_F32: case GFDTD_F32_KAHAN: return 4;
     case GFDTD_BF16: case GFDTD_F16: return 2;
     case GFDTD_F64: return 8;
     default: return 0;
@@ -88,6 +88,7 @@ struct gfdtd_ctx {
 
   // device state
   DevBuf B[2], D[2];
+  DevBuf cB[2], cD[2];                  // Kahan compensation (F32_KAHAN only)
   int cur = 0;                          // buffer holding the current state
   DevBuf d_ndone;
   long long n_done = 0;
@@ -95,7 +96,7 @@ struct gfdtd_ctx {
   // device tables (rebuilt by finalize)
   bool dirty = true;
   DevBuf d_inst, d_zq, d_tabE, d_tabH, d_srcs, d_prbs, d_amp, d_samples, d_omega, d_binprb,
-      d_acc_re, d_acc_im, d_tiles[2], d_tmp;
+      d_acc_re, d_acc_im, d_tiles[3], d_tmp, d_tabE32, d_tabH32;
   std::vector<InstDev> h_inst;
   std::vector<int> prb_global;          // probe creation index -> global (instance-sorted) index
   std::vector<int> prb_bin0;
@@ -103,10 +104,10 @@ struct gfdtd_ctx {
   std::vector<double> acc_keep_re, acc_keep_im;   // accumulators per creation-order bin
 
   // tiling
-  int C = 0, TB = 0;                    // chosen tile shape (0 = autotune)
+  int C = 0, TB = 0, MB = 0;            // chosen tile shape (0 = autotune)
   bool tuned = false;
-  int n_tiles[2] = {0, 0};              // [perturbation, matter]
-  int grid[2] = {0, 0};
+  int n_tiles[3] = {0, 0, 0};           // [general perturbation, general matter, fast interior]
+  int grid[3] = {0, 0, 0};
   int num_sms = 0;
 
   // graphs keyed by (chunk length, parity)
@@ -226,35 +227,58 @@ static void medium_coefs(gfdtd_kind kind, double beta, double e, double m, doubl
 
 // ------------------------------------------------------------------ finalize
 
-static gfdtd_status build_tiles(gfdtd_ctx* c, int C, int TB, std::vector<int2> out[2]) {
-  out[0].clear(); out[1].clear();
+static std::vector<float2> to_f32(const std::vector<double2>& v) {
+  std::vector<float2> out(v.size());
+  for (size_t i = 0; i < v.size(); ++i) out[i] = make_float2((float)v[i].x, (float)v[i].y);
+  return out;
+}
+
+// Tiles of every instance, split by kernel variant: 0 general moving
+// perturbation, 1 general moving matter, 2 fast interior tiles (see
+// fast_kernel).  Each list is ordered by the sign of v so that warps running
+// at the same time execute the same code.
+static gfdtd_status build_tiles(gfdtd_ctx* c, int C, int TB, std::vector<int2> out[3]) {
+  std::vector<int2> part[3][2];
   for (int i = 0; i < c->n_inst; ++i) {
-    const bool pos = c->media[i].beta >= 0.0;
+    const InstDev& d = c->h_inst[i];
+    const bool pos = (d.flags & F_POS) != 0;
     const int W = 32 * C - (pos ? 4 * TB : 3 * TB);
-    const int kindx = c->media[i].kind == GFDTD_MATTER ? 1 : 0;
-    for (long long x0 = 0; x0 < c->nz[i]; x0 += W) out[kindx].push_back(make_int2(i, (int)x0));
+    const int L = pos ? 3 * TB : TB;
+    const bool matter = (d.flags & F_MATTER) != 0;
+    const bool fast_ok = fast_eligible(d, C) && c->prec != GFDTD_F32_KAHAN;
+    for (long long x0 = 0; x0 < c->nz[i]; x0 += W) {
+      const long long base = x0 - L;
+      const bool edge = base < 0 || base + 32LL * C > c->nz[i];
+      const int v = matter ? 1 : (fast_ok && !edge ? 2 : 0);
+      part[v][pos ? 0 : 1].push_back(make_int2(i, (int)x0));
+    }
   }
-  if (out[0].size() + out[1].size() > (size_t)INT32_MAX)
+  for (int v = 0; v < 3; ++v) {
+    out[v] = part[v][0];
+    out[v].insert(out[v].end(), part[v][1].begin(), part[v][1].end());
+  }
+  if (out[0].size() + out[1].size() + out[2].size() > (size_t)INT32_MAX)
     return fail(c, GFDTD_E_ARG, "too many tiles");
   return GFDTD_OK;
 }
 
-static gfdtd_status set_tiles(gfdtd_ctx* c, int C, int TB) {
-  std::vector<int2> t[2];
+static gfdtd_status set_tiles(gfdtd_ctx* c, int C, int TB, int MB) {
+  std::vector<int2> t[3];
   gfdtd_status s = build_tiles(c, C, TB, t);
   if (s) return s;
-  for (int k = 0; k < 2; ++k) {
+  for (int k = 0; k < 3; ++k) {
     s = upload(c, c->d_tiles[k], t[k]);
     if (s) return s;
     c->n_tiles[k] = (int)t[k].size();
     int nb = 0;
-    CKI(c, block_occupancy(c->prec, k, C, TB, kBlock, &nb));
+    CKI(c, block_occupancy(c->prec, k, C, TB, MB, kBlock, &nb));
     nb = std::max(nb, 1);
     const int want = (c->n_tiles[k] + (kBlock / 32) - 1) / (kBlock / 32);
     c->grid[k] = std::max(1, std::min(c->num_sms * nb, want));
   }
   c->C = C;
   c->TB = TB;
+  c->MB = MB;
   drop_graphs(c);
   return GFDTD_OK;
 }
@@ -302,6 +326,7 @@ static gfdtd_status finalize(gfdtd_ctx* c) {
     d.nz_pad = (int)((c->nz[i] + 31) / 32 * 32);
     d.dq = llround(ldexp(m.beta * S, 31));
     d.n = (int)m.eps.size();
+    d.minw = 0;
     d.tab = (int)tabE.size();
     d.a = 1.0 - std::fabs(m.beta) * S;
     d.c = std::fabs(m.beta) * S;
@@ -334,6 +359,10 @@ static gfdtd_status finalize(gfdtd_ctx* c) {
         tabH.push_back(h);
       }
       while (zq.size() < tabE.size()) zq.push_back(0);   // keep zq aligned with the tables
+      // boundaries move rigidly, so their node indices stay at least floor(width) - 1 apart
+      double wmin = 1e30;
+      for (int k = 1; k + 1 < nvals; ++k) wmin = std::min(wmin, m.z[k] - m.z[k - 1]);
+      d.minw = wmin > 1e9 ? (1 << 30) : std::max(0, (int)std::floor(wmin) - 1);
       if (econst) flags |= F_EPS_CONST;
       if (mconst) flags |= F_MU_CONST;
     }
@@ -368,7 +397,8 @@ static gfdtd_status finalize(gfdtd_ctx* c) {
   c->n_bins = (int)omega.size();
   gfdtd_status s;
   if ((s = upload(c, c->d_inst, inst)) || (s = upload(c, c->d_zq, zq)) || (s = upload(c, c->d_tabE, tabE)) ||
-      (s = upload(c, c->d_tabH, tabH)) || (s = upload(c, c->d_srcs, srcs)) ||
+      (s = upload(c, c->d_tabH, tabH)) || (s = upload(c, c->d_tabE32, to_f32(tabE))) ||
+      (s = upload(c, c->d_tabH32, to_f32(tabH))) || (s = upload(c, c->d_srcs, srcs)) ||
       (s = upload(c, c->d_prbs, prbs)) || (s = upload(c, c->d_omega, omega)) ||
       (s = upload(c, c->d_binprb, binprb)) || (s = upload(c, c->d_acc_re, acc_re)) ||
       (s = upload(c, c->d_acc_im, acc_im)))
@@ -379,7 +409,7 @@ static gfdtd_status finalize(gfdtd_ctx* c) {
   c->dirty = false;
   drop_graphs(c);
   if (c->C > 0) {
-    s = set_tiles(c, c->C, c->TB);
+    s = set_tiles(c, c->C, c->TB, c->MB);
     if (s) return s;
   }
   return GFDTD_OK;
@@ -392,13 +422,15 @@ static Tables tables_of(gfdtd_ctx* c) {
   t.zq = (const long long*)c->d_zq.p;
   t.tabE = (const double2*)c->d_tabE.p;
   t.tabH = (const double2*)c->d_tabH.p;
+  t.tabE32 = (const float2*)c->d_tabE32.p;
+  t.tabH32 = (const float2*)c->d_tabH32.p;
   return t;
 }
 
 // Enqueue one time-block launch (both kinds) reading buffer `from`.
 static gfdtd_status enqueue_block(gfdtd_ctx* c, cudaStream_t st, int from, int s0, int nsteps,
                                   bool record, bool sources) {
-  for (int k = 0; k < 2; ++k) {
+  for (int k = 0; k < 3; ++k) {
     if (c->n_tiles[k] == 0) continue;
     // BlockArgs<T> has the same layout for every T (pointers), so fill the float version
     BlockArgs<float> a;
@@ -415,11 +447,15 @@ static gfdtd_status enqueue_block(gfdtd_ctx* c, cudaStream_t st, int from, int s
     a.Din = (const float*)c->D[from].p;
     a.Bout = (float*)c->B[1 - from].p;
     a.Dout = (float*)c->D[1 - from].p;
+    a.cBin = (const float*)c->cB[from].p;
+    a.cDin = (const float*)c->cD[from].p;
+    a.cBout = (float*)c->cB[1 - from].p;
+    a.cDout = (float*)c->cD[1 - from].p;
     a.n_done = (const long long*)c->d_ndone.p;
     a.s0 = s0;
     a.nsteps = nsteps;
     a.record = record ? 1 : 0;
-    CKI(c, block_launch(c->prec, k, c->C, c->TB, &a, c->grid[k], kBlock, st));
+    CKI(c, block_launch(c->prec, k, c->C, c->TB, c->MB, &a, c->grid[k], kBlock, st));
     ++c->launches;
   }
   return GFDTD_OK;
@@ -486,7 +522,7 @@ static gfdtd_status run_chunk(gfdtd_ctx* c, int nsteps) {
     it = c->graphs.emplace(key, ex).first;
   }
   CK(c, cudaGraphLaunch(it->second, c->stream));
-  const int kinds = (c->n_tiles[0] > 0) + (c->n_tiles[1] > 0);
+  const int kinds = (c->n_tiles[0] > 0) + (c->n_tiles[1] > 0) + (c->n_tiles[2] > 0);
   c->launches += (long long)m * kinds + (c->n_src > 0) + (c->n_bins > 0) + 1;
   if (m & 1) c->cur = 1 - c->cur;
   c->n_done += nsteps;
@@ -496,17 +532,17 @@ static gfdtd_status run_chunk(gfdtd_ctx* c, int nsteps) {
 // Time the candidate tile shapes on the actual batch (reads the current
 // buffer, writes the other, records nothing) and keep the fastest.
 static gfdtd_status autotune(gfdtd_ctx* c) {
-  int Cs[16], TBs[16];
-  const int n = block_shapes(c->prec, Cs, TBs, 16);
+  int Cs[16], TBs[16], MBs[16];
+  const int n = block_shapes(c->prec, Cs, TBs, MBs, 16);
   if (n == 0) return fail(c, GFDTD_E_UNSUPPORTED, "no tile shape built for this precision");
-  if (n == 1) return set_tiles(c, Cs[0], TBs[0]);
+  if (n == 1) return set_tiles(c, Cs[0], TBs[0], MBs[0]);
   cudaEvent_t e0, e1;
   CK(c, cudaEventCreate(&e0));
   CK(c, cudaEventCreate(&e1));
   double best = 1e300;
   int bi = 0;
   for (int i = 0; i < n; ++i) {
-    gfdtd_status s = set_tiles(c, Cs[i], TBs[i]);
+    gfdtd_status s = set_tiles(c, Cs[i], TBs[i], MBs[i]);
     if (s) return s;
     s = enqueue_block(c, c->stream, c->cur, 0, TBs[i], false, false);
     if (s) return s;
@@ -525,7 +561,7 @@ static gfdtd_status autotune(gfdtd_ctx* c) {
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
-  return set_tiles(c, Cs[bi], TBs[bi]);
+  return set_tiles(c, Cs[bi], TBs[bi], MBs[bi]);
 }
 
 static gfdtd_status check_inst(gfdtd_ctx* c, int inst) {
@@ -552,7 +588,6 @@ gfdtd_status gfdtd_create(gfdtd_ctx** out, int n_inst, const int64_t* nz, double
   *out = nullptr;
   if (n_inst < 1 || !nz) return fail(nullptr, GFDTD_E_ARG, "need n_inst >= 1 and nz");
   if (!(S > 0.0 && S <= 1.0)) return fail(nullptr, GFDTD_E_ARG, "S must be in (0, 1]");
-  if (prec == GFDTD_F32_KAHAN) return fail(nullptr, GFDTD_E_UNSUPPORTED, "F32_KAHAN is not built");
   const int eb = elem_bytes_of(prec);
   if (eb == 0) return fail(nullptr, GFDTD_E_ARG, "unknown precision %d", (int)prec);
   for (int i = 0; i < n_inst; ++i)
@@ -593,12 +628,16 @@ gfdtd_status gfdtd_create(gfdtd_ctx** out, int n_inst, const int64_t* nz, double
   for (int k = 0; k < 2 && !s; ++k) {
     s = dalloc(c, c->B[k], bytes);
     if (!s) s = dalloc(c, c->D[k], bytes);
+    if (!s && prec == GFDTD_F32_KAHAN) s = dalloc(c, c->cB[k], bytes);
+    if (!s && prec == GFDTD_F32_KAHAN) s = dalloc(c, c->cD[k], bytes);
   }
   if (!s) s = dalloc(c, c->d_ndone, 16);
   if (!s) {
     for (int k = 0; k < 2; ++k) {
       cudaMemsetAsync(c->B[k].p, 0, bytes, c->stream);
       cudaMemsetAsync(c->D[k].p, 0, bytes, c->stream);
+      if (c->cB[k].p) cudaMemsetAsync(c->cB[k].p, 0, bytes, c->stream);
+      if (c->cD[k].p) cudaMemsetAsync(c->cD[k].p, 0, bytes, c->stream);
     }
     cudaMemsetAsync(c->d_ndone.p, 0, 16, c->stream);
     if (cudaGetLastError() != cudaSuccess) s = fail(c, GFDTD_E_CUDA, "memset failed");
@@ -715,6 +754,8 @@ gfdtd_status gfdtd_step(gfdtd_ctx* c, int64_t n_steps) {
 
 gfdtd_status gfdtd_step_plain(gfdtd_ctx* c, int64_t n_steps) {
   if (!c) return GFDTD_E_ARG;
+  if (c->prec == GFDTD_F32_KAHAN)
+    return fail(c, GFDTD_E_UNSUPPORTED, "the plain kernel has no compensated tier");
   if (n_steps < 0) return fail(c, GFDTD_E_ARG, "n_steps < 0");
   gfdtd_status s = finalize(c);
   if (s) return s;
@@ -784,6 +825,8 @@ gfdtd_status gfdtd_write_fields(gfdtd_ctx* c, int inst, gfdtd_field which, const
   CK(c, cudaMemcpyAsync(c->d_tmp.p, src, (size_t)n * sizeof(double), cudaMemcpyHostToDevice, c->stream));
   const DevBuf& b = which == GFDTD_FIELD_D ? c->D[c->cur] : c->B[c->cur];
   CKI(c, convert_launch(c->prec, 0, c->d_tmp.p, (char*)b.p + (size_t)c->off[inst] * c->eb, n, c->stream));
+  const DevBuf& cb = which == GFDTD_FIELD_D ? c->cD[c->cur] : c->cB[c->cur];
+  if (cb.p) CK(c, cudaMemsetAsync((char*)cb.p + (size_t)c->off[inst] * c->eb, 0, (size_t)n * c->eb, c->stream));
   CK(c, cudaStreamSynchronize(c->stream));
   return GFDTD_OK;
 }
@@ -811,6 +854,8 @@ gfdtd_status gfdtd_write_state(gfdtd_ctx* c, gfdtd_field which, const void* src,
   if (!src || bytes != c->total * c->eb) return fail(c, GFDTD_E_ARG, "bytes must be %lld", c->total * c->eb);
   const DevBuf& b = which == GFDTD_FIELD_D ? c->D[c->cur] : c->B[c->cur];
   CK(c, cudaMemcpyAsync(b.p, src, (size_t)bytes, cudaMemcpyHostToDevice, c->stream));
+  const DevBuf& cb = which == GFDTD_FIELD_D ? c->cD[c->cur] : c->cB[c->cur];
+  if (cb.p) CK(c, cudaMemsetAsync(cb.p, 0, (size_t)bytes, c->stream));
   return GFDTD_OK;
 }
 
@@ -848,32 +893,35 @@ gfdtd_status gfdtd_stability(double S, double beta, double eps_r, double mu_r, g
   return GFDTD_OK;
 }
 
-gfdtd_status gfdtd_set_tuning(gfdtd_ctx* c, int cells_per_lane, int time_block) {
+gfdtd_status gfdtd_set_tuning(gfdtd_ctx* c, int cells_per_lane, int time_block, int blocks_per_sm) {
   if (!c) return GFDTD_E_ARG;
   if (cells_per_lane == 0 && time_block == 0) {
     c->C = 0;
     c->TB = 0;
+    c->MB = 0;
     drop_graphs(c);
     return GFDTD_OK;
   }
-  int Cs[16], TBs[16];
-  const int n = block_shapes(c->prec, Cs, TBs, 16);
+  int Cs[16], TBs[16], MBs[16];
+  const int n = block_shapes(c->prec, Cs, TBs, MBs, 16);
   for (int i = 0; i < n; ++i) {
-    if (Cs[i] == cells_per_lane && TBs[i] == time_block) {
+    if (Cs[i] == cells_per_lane && TBs[i] == time_block &&
+        (blocks_per_sm == 0 || MBs[i] == blocks_per_sm)) {
       gfdtd_status s = finalize(c);
       if (s) return s;
-      return set_tiles(c, cells_per_lane, time_block);
+      return set_tiles(c, Cs[i], TBs[i], MBs[i]);
     }
   }
-  return fail(c, GFDTD_E_UNSUPPORTED, "tile shape %d x %d not built for this precision",
-              cells_per_lane, time_block);
+  return fail(c, GFDTD_E_UNSUPPORTED, "tile shape %d x %d (%d blocks/SM) not built for this precision",
+              cells_per_lane, time_block, blocks_per_sm);
 }
 
 gfdtd_status gfdtd_get_stats(const gfdtd_ctx* c, gfdtd_stats* out) {
   if (!c || !out) return GFDTD_E_ARG;
   out->cells_per_lane = c->C;
   out->time_block = c->TB;
-  out->n_tiles = (int64_t)c->n_tiles[0] + c->n_tiles[1];
+  out->blocks_per_sm = c->MB;
+  out->n_tiles = (int64_t)c->n_tiles[0] + c->n_tiles[1] + c->n_tiles[2];
   out->kernel_launches = c->launches;
   long long cells = 0;
   for (long long v : c->nz) cells += v;
@@ -895,10 +943,11 @@ void gfdtd_destroy(gfdtd_ctx* c) {
   if (!c) return;
   cudaStreamSynchronize(c->stream);
   drop_graphs(c);
-  DevBuf* bufs[] = {&c->B[0], &c->B[1], &c->D[0], &c->D[1], &c->d_ndone, &c->d_inst, &c->d_zq,
+  DevBuf* bufs[] = {&c->B[0], &c->B[1], &c->D[0], &c->D[1], &c->cB[0], &c->cB[1], &c->cD[0],
+                    &c->cD[1], &c->d_ndone, &c->d_inst, &c->d_zq,
                     &c->d_tabE, &c->d_tabH, &c->d_srcs, &c->d_prbs, &c->d_amp, &c->d_samples,
                     &c->d_omega, &c->d_binprb, &c->d_acc_re, &c->d_acc_im, &c->d_tiles[0],
-                    &c->d_tiles[1], &c->d_tmp};
+                    &c->d_tiles[1], &c->d_tiles[2], &c->d_tmp, &c->d_tabE32, &c->d_tabH32};
   for (DevBuf* b : bufs) dfree(c, *b);
   if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
   delete c;

@@ -144,21 +144,21 @@ __device__ __forceinline__ int count_at_or_left(const long long* __restrict__ zq
 // `idx` = number of knots at or left of k; evaluated in the arithmetic type R.
 template <bool MATTER, bool ESIDE, typename R>
 __device__ __forceinline__ void linear_coef(const InstDev& I, const long long* __restrict__ zq,
-                                            const double2* __restrict__ raw, int idx, int k,
-                                            long long off, R& cx, R& cy) {
+                                            const typename TabOf<R>::V* __restrict__ raw, int idx,
+                                            int k, long long off, R& cx, R& cy) {
   const int n = I.n;
   R e, m;
   if (idx <= 0) {
-    const double2 v = __ldg(raw); e = (R)v.x; m = (R)v.y;
+    const auto v = __ldg(raw); e = v.x; m = v.y;
   } else if (idx >= n) {
-    const double2 v = __ldg(raw + n - 1); e = (R)v.x; m = (R)v.y;
+    const auto v = __ldg(raw + n - 1); e = v.x; m = v.y;
   } else {
     const long long z0 = __ldg(zq + idx - 1), z1 = __ldg(zq + idx);
     const long long xi = ((long long)k << 32) - off;
     const R wgt = (R)(xi - z0) / (R)(z1 - z0);
-    const double2 v0 = __ldg(raw + idx - 1), v1 = __ldg(raw + idx);
-    e = (R)v0.x + wgt * ((R)v1.x - (R)v0.x);
-    m = (R)v0.y + wgt * ((R)v1.y - (R)v0.y);
+    const auto v0 = __ldg(raw + idx - 1), v1 = __ldg(raw + idx);
+    e = v0.x + wgt * (v1.x - v0.x);
+    m = v0.y + wgt * (v1.y - v0.y);
   }
   const R S = (R)I.S;
   if (!MATTER) {
@@ -177,15 +177,15 @@ template <bool MATTER, bool ESIDE, typename R>
 __device__ __forceinline__ void node_coef(const InstDev& I, const Tables& tb, long long off, int k,
                                           R& cx, R& cy) {
   const long long* zq = tb.zq + I.tab;
-  const double2* tv = (ESIDE ? tb.tabE : tb.tabH) + I.tab;
+  const auto* tv = TabOf<R>::get(tb, ESIDE) + I.tab;
   if (I.flags & F_LINEAR) {
     const int idx = count_at_or_left(zq, I.n, off, k);
     linear_coef<MATTER, ESIDE>(I, zq, tv, idx, k, off, cx, cy);
     return;
   }
-  const double2 v = __ldg(tv + count_at_or_left(zq, I.n - 1, off, k));
-  cx = (R)v.x;
-  cy = MATTER ? (R)v.y : (R)I.cb;
+  const auto v = __ldg(tv + count_at_or_left(zq, I.n - 1, off, k));
+  cx = v.x;
+  cy = MATTER ? v.y : (R)I.cb;
 }
 
 // Per-lane material of the run of C cells starting at k0 at one half level.
@@ -194,7 +194,7 @@ template <int C, bool MATTER, bool ESIDE, typename R>
 __device__ __forceinline__ void lane_coefs(const InstDev& I, const Tables& tb, long long off,
                                            int k0, int& li, R (&cx)[C], R (&cy)[C]) {
   const long long* __restrict__ zq = tb.zq + I.tab;
-  const double2* __restrict__ tv = (ESIDE ? tb.tabE : tb.tabH) + I.tab;
+  const auto* __restrict__ tv = TabOf<R>::get(tb, ESIDE) + I.tab;
   if (I.flags & F_LINEAR) {
     const int nk = I.n;
     while (li < nk && node_of(__ldg(zq + li), off) <= k0) ++li;
@@ -212,20 +212,28 @@ __device__ __forceinline__ void lane_coefs(const InstDev& I, const Tables& tb, l
   while (li < nb && node_of(__ldg(zq + li), off) <= k0) ++li;
   while (li > 0 && node_of(__ldg(zq + li - 1), off) > k0) --li;
   const int K1 = li < nb ? node_of(__ldg(zq + li), off) : INT_MAX;
+  const auto v0 = __ldg(tv + li);
+  const auto v1 = __ldg(tv + min(li + 1, nl - 1));
+  if (I.minw > C) {
+    // layers wider than a lane's run: at most one boundary among its cells
+#pragma unroll
+    for (int c = 0; c < C; ++c) {
+      const bool past = k0 + c >= K1;
+      cx[c] = past ? v1.x : v0.x;
+      if (MATTER) cy[c] = past ? v1.y : v0.y;
+    }
+    return;
+  }
   const int K2 = li + 1 < nb ? node_of(__ldg(zq + li + 1), off) : INT_MAX;
   const bool many = li + 2 < nb && node_of(__ldg(zq + li + 2), off) < k0 + C;
   if (!many) {
-    // at most two layer boundaries inside this lane's cells
-    const double2 w0 = __ldg(tv + li);
-    const double2 w1 = __ldg(tv + min(li + 1, nl - 1));
-    const double2 w2 = __ldg(tv + min(li + 2, nl - 1));
-    const R v0x = (R)w0.x, v1x = (R)w1.x, v2x = (R)w2.x;
-    const R v0y = (R)w0.y, v1y = (R)w1.y, v2y = (R)w2.y;
+    // at most two layer boundaries among this lane's cells
+    const auto v2 = __ldg(tv + min(li + 2, nl - 1));
 #pragma unroll
     for (int c = 0; c < C; ++c) {
       const int k = k0 + c;
-      cx[c] = k >= K2 ? v2x : (k >= K1 ? v1x : v0x);
-      if (MATTER) cy[c] = k >= K2 ? v2y : (k >= K1 ? v1y : v0y);
+      cx[c] = k >= K2 ? v2.x : (k >= K1 ? v1.x : v0.x);
+      if (MATTER) cy[c] = k >= K2 ? v2.y : (k >= K1 ? v1.y : v0.y);
     }
   } else {
     int idx = li;
@@ -233,9 +241,9 @@ __device__ __forceinline__ void lane_coefs(const InstDev& I, const Tables& tb, l
     for (int c = 0; c < C; ++c) {
       const int k = k0 + c;
       while (idx < nb && node_of(__ldg(zq + idx), off) <= k) ++idx;
-      const double2 v = __ldg(tv + idx);
-      cx[c] = (R)v.x;
-      if (MATTER) cy[c] = (R)v.y;
+      const auto v = __ldg(tv + idx);
+      cx[c] = v.x;
+      if (MATTER) cy[c] = v.y;
     }
   }
 }
@@ -250,7 +258,16 @@ __device__ __forceinline__ R pick(const R (&x)[C], int c) {
 
 // ------------------------------------------------------------- one tile
 
-template <int C, int TB, bool POS, bool MATTER, bool EDGE, typename T>
+// Kahan-compensated addition x += d with compensation cmp (F32_KAHAN tier).
+template <typename R>
+__device__ __forceinline__ void kahan_add(R& x, R& cmp, R d) {
+  const R y = d - cmp;
+  const R t = x + y;
+  cmp = (t - x) - y;
+  x = t;
+}
+
+template <int C, int TB, bool POS, bool MATTER, bool EDGE, typename T, bool KAHAN = false>
 __device__ __forceinline__ void run_tile(const BlockArgs<T>& A, const InstDev& I, int x0, int W,
                                          long long n0) {
   using R = typename Real<T>::type;
@@ -263,14 +280,20 @@ __device__ __forceinline__ void run_tile(const BlockArgs<T>& A, const InstDev& I
   R B[C], D[C], X[C];
   load_cells<T, R, C>(A.Bin + I.off, k0, I.nz_pad, B);
   load_cells<T, R, C>(A.Din + I.off, k0, I.nz_pad, D);
+  R cBv[KAHAN ? C : 1], cDv[KAHAN ? C : 1];
+  if constexpr (KAHAN) {
+    load_cells<T, R, KAHAN ? C : 1>(A.cBin + I.off, k0, I.nz_pad, cBv);
+    load_cells<T, R, KAHAN ? C : 1>(A.cDin + I.off, k0, I.nz_pad, cDv);
+  }
 
   const R a = (R)I.a, cc = (R)I.c;
   const bool eps_const = (I.flags & F_EPS_CONST) != 0;
   const bool mu_const = (I.flags & F_MU_CONST) != 0;
   const long long dq = I.dq;
-  const double2 e0 = __ldg(A.tb.tabE + I.tab), h0 = __ldg(A.tb.tabH + I.tab);
-  const R se0 = (R)e0.x, sm0 = (R)h0.x;
-  const R cbe0 = MATTER ? (R)e0.y : (R)I.cb, cbh0 = MATTER ? (R)h0.y : (R)I.cb;
+  const auto e0 = __ldg(TabOf<R>::get(A.tb, true) + I.tab);
+  const auto h0 = __ldg(TabOf<R>::get(A.tb, false) + I.tab);
+  const R se0 = e0.x, sm0 = h0.x;
+  const R cbe0 = MATTER ? e0.y : (R)I.cb, cbh0 = MATTER ? h0.y : (R)I.cb;
   int liE = 0, liH = 0;
   if (!eps_const || !mu_const) {
     const int nb = (I.flags & F_LINEAR) ? I.n : I.n - 1;
@@ -335,7 +358,8 @@ __device__ __forceinline__ void run_tile(const BlockArgs<T>& A, const InstDev& I
         for (int c = C - 1; c >= 0; --c) {
           const R bu = c >= 1 ? B[c - 1] : bl1;
           const R en = c + 1 < C ? X[c + 1] : er;
-          B[c] = a * B[c] + (cc * bu + (X[c] - en));
+          if (KAHAN) kahan_add(B[c], cBv[KAHAN ? c : 0], (X[c] - en) + cc * (bu - B[c]));
+          else B[c] = a * B[c] + (cc * bu + (X[c] - en));
           if (EDGE) B[c] = ((unsigned)(k0 + c) < (unsigned)nz) ? B[c] : (R)0;
         }
       } else {
@@ -343,7 +367,8 @@ __device__ __forceinline__ void run_tile(const BlockArgs<T>& A, const InstDev& I
         for (int c = 0; c < C; ++c) {
           const R bu = c + 1 < C ? B[c + 1] : br1;
           const R en = c + 1 < C ? X[c + 1] : er;
-          B[c] = a * B[c] + (cc * bu + (X[c] - en));
+          if (KAHAN) kahan_add(B[c], cBv[KAHAN ? c : 0], (X[c] - en) + cc * (bu - B[c]));
+          else B[c] = a * B[c] + (cc * bu + (X[c] - en));
           if (EDGE) B[c] = ((unsigned)(k0 + c) < (unsigned)nz) ? B[c] : (R)0;
         }
       }
@@ -376,7 +401,8 @@ __device__ __forceinline__ void run_tile(const BlockArgs<T>& A, const InstDev& I
         for (int c = C - 1; c >= 0; --c) {
           const R du = c >= 1 ? D[c - 1] : dl;
           const R hp = c >= 1 ? X[c - 1] : hl;
-          D[c] = a * D[c] + (cc * du + (hp - X[c]));
+          if (KAHAN) kahan_add(D[c], cDv[KAHAN ? c : 0], (hp - X[c]) + cc * (du - D[c]));
+          else D[c] = a * D[c] + (cc * du + (hp - X[c]));
           if (EDGE) D[c] = ((unsigned)(k0 + c) < (unsigned)nz) ? D[c] : (R)0;
         }
       } else {
@@ -384,7 +410,8 @@ __device__ __forceinline__ void run_tile(const BlockArgs<T>& A, const InstDev& I
         for (int c = 0; c < C; ++c) {
           const R du = c + 1 < C ? D[c + 1] : dr;
           const R hp = c >= 1 ? X[c - 1] : hl;
-          D[c] = a * D[c] + (cc * du + (hp - X[c]));
+          if (KAHAN) kahan_add(D[c], cDv[KAHAN ? c : 0], (hp - X[c]) + cc * (du - D[c]));
+          else D[c] = a * D[c] + (cc * du + (hp - X[c]));
           if (EDGE) D[c] = ((unsigned)(k0 + c) < (unsigned)nz) ? D[c] : (R)0;
         }
       }
@@ -437,12 +464,188 @@ __device__ __forceinline__ void run_tile(const BlockArgs<T>& A, const InstDev& I
   store_cells<T, R, C>(A.Dout + I.off, k0, x0, hi, D);
 }
 
+// ------------------------------------------------ fast tile (common case)
+//
+// Moving perturbation, uniform mu, layered eps whose layers are wider than a
+// lane's run (or uniform eps), tile away from the domain ends.  E' and H' are
+// not formed: substituting them gives, with P_j = se_j D_j (level n-1/2),
+//   v >= 0:  B'_j = (a + cb) B_j + c B_{j-1} - cb B_{j-2} + P_j - P_{j+1}
+//            D'_k = a D_k + (c - cb) D_{k-1} + cb D_{k+1} + sm (B'_{k-1} - B'_k)
+//   v <  0:  B'_j = (a - cb) B_j + c B_{j+1} + cb B_{j+2} + P_j - P_{j+1}
+//            D'_k = a D_k + (c + cb) D_{k+1} - cb D_{k-1} + sm (B'_{k-1} - B'_k)
+// (the same equations, regrouped).  The material of a lane is tracked with
+// the two layer boundaries around its first cell k0: d = zq + dq h - k0 2^32
+// grows by 2 dq per step, and cells c >= ceil(d / 2^32) of the run lie beyond
+// the boundary.
+
+struct BoundaryTrack {
+  long long dprev, dnext;     // zq_b + dq h - k0 2^32 of the boundaries around k0
+  int bnext;                  // index of the next boundary (first with d > 0)
+};
+
+constexpr long long FAR_AWAY = 1LL << 61;
+
+__device__ __forceinline__ long long track_d(const long long* __restrict__ zq, int b, int nb,
+                                             long long off) {
+  if (b < 0) return -FAR_AWAY;
+  if (b >= nb) return FAR_AWAY;
+  return __ldg(zq + b) + off;
+}
+
+template <int C, int TB, bool POS, typename T>
+__device__ __forceinline__ void run_tile_fast(const BlockArgs<T>& A, const InstDev& I, int x0, int W,
+                                              long long n0) {
+  using R = typename Real<T>::type;
+  using V2 = typename TabOf<R>::V;
+  const int lane = threadIdx.x & 31;
+  constexpr int L = POS ? 3 * TB : TB;
+  const int base = x0 - L;
+  const int k0 = base + lane * C;
+
+  R B[C], D[C], P[C];
+  load_cells<T, R, C>(A.Bin + I.off, k0, I.nz_pad, B);
+  load_cells<T, R, C>(A.Din + I.off, k0, I.nz_pad, D);
+
+  const R a = (R)I.a, cc = (R)I.c, cb = (R)I.cb;
+  const R bB0 = POS ? a + cb : a - cb;            // weight of B_j
+  const R bD1 = POS ? cc - cb : cc + cb;          // weight of the upwind D neighbour
+  const R bD2 = POS ? cb : -cb;                   // weight of the downwind D neighbour
+  const V2* __restrict__ tv = TabOf<R>::get(A.tb, true) + I.tab;
+  const long long* __restrict__ zq = A.tb.zq + I.tab;
+  const R sm = (R)__ldg(TabOf<R>::get(A.tb, false) + I.tab).x;
+  const int nb = I.n - 1;
+  const long long dq2 = 2 * I.dq;
+
+  // boundary tracker at half level h = 2 n0 + 1 (the first E' of this launch)
+  BoundaryTrack tr;
+  const long long off0 = I.dq * (2 * n0 + 1) - ((long long)k0 << 32);
+  tr.bnext = count_at_or_left(zq, nb, I.dq * (2 * n0 + 1), k0);
+  tr.dprev = track_d(zq, tr.bnext - 1, nb, off0);
+  tr.dnext = track_d(zq, tr.bnext, nb, off0);
+  R vL = __ldg(tv + tr.bnext).x;
+  R vR = __ldg(tv + min(tr.bnext + 1, nb)).x;
+
+  unsigned smask = 0, pmask = 0;
+  if (A.src_amp) {
+    for (int q = 0; q < I.nsrc && q < 32; ++q) {
+      const int node = A.srcs[I.src0 + q].node;
+      if (node >= base && node < base + 32 * C) smask |= 1u << q;
+    }
+  }
+  if (A.record) {
+    for (int q = 0; q < I.nprb && q < 32; ++q) {
+      const int node = A.prbs[I.prb0 + q].node;
+      if (node >= x0 && node < x0 + W && node < I.nz) pmask |= 1u << q;
+    }
+  }
+
+  for (int s = 0; s < A.nsteps; ++s) {
+    // ---- material at level n-1/2 for this lane's cells: c >= c1 lies beyond the next boundary
+    const int c1 = (int)((tr.dnext + 0xFFFFFFFFLL) >> 32);
+#pragma unroll
+    for (int c = 0; c < C; ++c) P[c] = (c >= c1 ? vR : vL) * D[c];
+
+    // ---- B^n
+    {
+      const R pr = __shfl_down_sync(FULL, P[0], 1);
+      if (POS) {
+        const R bl1 = __shfl_up_sync(FULL, B[C - 1], 1);
+        const R bl2 = __shfl_up_sync(FULL, B[C - 2], 1);
+#pragma unroll
+        for (int c = C - 1; c >= 0; --c) {
+          const R b1 = c >= 1 ? B[c - 1] : bl1;
+          const R b2 = c >= 2 ? B[c - 2] : (c == 1 ? bl1 : bl2);
+          const R pn = c + 1 < C ? P[c + 1] : pr;
+          B[c] = bB0 * B[c] + (cc * b1 + (-cb * b2 + (P[c] - pn)));
+        }
+      } else {
+        const R br1 = __shfl_down_sync(FULL, B[0], 1);
+        const R br2 = __shfl_down_sync(FULL, B[1], 1);
+#pragma unroll
+        for (int c = 0; c < C; ++c) {
+          const R b1 = c + 1 < C ? B[c + 1] : br1;
+          const R b2 = c + 2 < C ? B[c + 2] : (c + 2 == C ? br1 : br2);
+          const R pn = c + 1 < C ? P[c + 1] : pr;
+          B[c] = bB0 * B[c] + (cc * b1 + (cb * b2 + (P[c] - pn)));
+        }
+      }
+    }
+
+    // ---- D^{n+1/2} (both D neighbours are read at level n-1/2: write a fresh array)
+    {
+      const R dl = __shfl_up_sync(FULL, D[C - 1], 1);
+      const R dr = __shfl_down_sync(FULL, D[0], 1);
+      const R bnl = __shfl_up_sync(FULL, B[C - 1], 1);
+      R Dn[C];
+#pragma unroll
+      for (int c = 0; c < C; ++c) {
+        const R left = c >= 1 ? D[c - 1] : dl;
+        const R right = c + 1 < C ? D[c + 1] : dr;
+        const R du = POS ? left : right;     // upwind neighbour
+        const R dd = POS ? right : left;     // downwind neighbour
+        const R bm = c >= 1 ? B[c - 1] : bnl;
+        Dn[c] = a * D[c] + (bD1 * du + (bD2 * dd + sm * (bm - B[c])));
+      }
+#pragma unroll
+      for (int c = 0; c < C; ++c) D[c] = Dn[c];
+    }
+
+    // ---- soft sources at t_{n+1/2}
+    for (unsigned m = smask; m; m &= m - 1) {
+      const int q = __ffs(m) - 1;
+      const int rel = A.srcs[I.src0 + q].node - base;
+      const R amp = (R)A.src_amp[(long long)(I.src0 + q) * A.chunk_stride + A.s0 + s];
+      if (lane == rel / C) {
+        const int cs = rel % C;
+#pragma unroll
+        for (int c = 0; c < C; ++c) D[c] += (c == cs) ? amp : (R)0;
+      }
+    }
+
+    // ---- advance the boundary tracker to level n+1/2
+    tr.dprev += dq2;
+    tr.dnext += dq2;
+    if (tr.dprev > 0) {            // the previous boundary moved past k0 (v > 0)
+      tr.dnext = tr.dprev;
+      tr.bnext -= 1;
+      const long long offn = I.dq * (2 * (n0 + s + 1) + 1) - ((long long)k0 << 32);
+      tr.dprev = track_d(zq, tr.bnext - 1, nb, offn);
+      vL = __ldg(tv + tr.bnext).x;
+      vR = __ldg(tv + min(tr.bnext + 1, nb)).x;
+    } else if (tr.dnext <= 0) {    // the next boundary moved to or behind k0 (v < 0)
+      tr.dprev = tr.dnext;
+      tr.bnext += 1;
+      const long long offn = I.dq * (2 * (n0 + s + 1) + 1) - ((long long)k0 << 32);
+      tr.dnext = track_d(zq, tr.bnext, nb, offn);
+      vL = __ldg(tv + tr.bnext).x;
+      vR = __ldg(tv + min(tr.bnext + 1, nb)).x;
+    }
+
+    // ---- probes: E = D / eps at level n+1/2
+    for (unsigned m = pmask; m; m &= m - 1) {
+      const int q = __ffs(m) - 1;
+      const int node = A.prbs[I.prb0 + q].node;
+      const int rel = node - base;
+      if (lane == rel / C) {
+        R sep, cbp;
+        node_coef<false, true>(I, A.tb, I.dq * (2 * (n0 + s + 1) + 1), node, sep, cbp);
+        A.samples[(long long)(I.prb0 + q) * A.chunk_stride + A.s0 + s] =
+            (double)(pick(D, rel % C) * sep * (R)I.inv_S);
+      }
+    }
+  }
+
+  const int hi = min(x0 + W, I.nz_pad);
+  store_cells<T, R, C>(A.Bout + I.off, k0, x0, hi, B);
+  store_cells<T, R, C>(A.Dout + I.off, k0, x0, hi, D);
+}
+
 // Tile width (output cells) of a tile shape for one sign of v.
 __host__ __device__ constexpr int tile_width(int C, int TB, bool pos) {
   return 32 * C - (pos ? 4 * TB : 3 * TB);
 }
 
-template <int C, int TB, bool MATTER, typename T>
+template <int C, int TB, bool MATTER, typename T, bool KAHAN = false>
 __global__ void __launch_bounds__(128) block_kernel(const BlockArgs<T> A) {
   const int warps_per_block = blockDim.x >> 5;
   const int gw = blockIdx.x * warps_per_block + (threadIdx.x >> 5);
@@ -455,27 +658,60 @@ __global__ void __launch_bounds__(128) block_kernel(const BlockArgs<T> A) {
     if (I.flags & F_POS) {
       constexpr int W = tile_width(C, TB, true);
       const int base = x0 - 3 * TB;
-      if (base < 0 || base + 32 * C > I.nz) run_tile<C, TB, true, MATTER, true>(A, I, x0, W, n0);
-      else run_tile<C, TB, true, MATTER, false>(A, I, x0, W, n0);
+      if (base < 0 || base + 32 * C > I.nz) run_tile<C, TB, true, MATTER, true, T, KAHAN>(A, I, x0, W, n0);
+      else run_tile<C, TB, true, MATTER, false, T, KAHAN>(A, I, x0, W, n0);
     } else {
       constexpr int W = tile_width(C, TB, false);
       const int base = x0 - TB;
-      if (base < 0 || base + 32 * C > I.nz) run_tile<C, TB, false, MATTER, true>(A, I, x0, W, n0);
-      else run_tile<C, TB, false, MATTER, false>(A, I, x0, W, n0);
+      if (base < 0 || base + 32 * C > I.nz) run_tile<C, TB, false, MATTER, true, T, KAHAN>(A, I, x0, W, n0);
+      else run_tile<C, TB, false, MATTER, false, T, KAHAN>(A, I, x0, W, n0);
     }
   }
 }
 
-template <int C, int TB, bool MATTER, typename T>
-int launch_block_shape(const void* args, int grid, int block, cudaStream_t st) {
-  block_kernel<C, TB, MATTER, T><<<grid, block, 0, st>>>(*static_cast<const BlockArgs<T>*>(args));
+// Interior tiles of moving-perturbation instances with uniform mu and wide
+// (or no) layers; the host sorts such tiles into their own list.
+template <int C, int TB, typename T, int MB>
+__global__ void __launch_bounds__(128, MB) fast_kernel(const BlockArgs<T> A) {
+  const int warps_per_block = blockDim.x >> 5;
+  const int gw = blockIdx.x * warps_per_block + (threadIdx.x >> 5);
+  const int nw = gridDim.x * warps_per_block;
+  const long long n0 = *A.n_done + A.s0;
+  for (int t = gw; t < A.n_tiles; t += nw) {
+    const int2 tl = A.tiles[t];
+    const InstDev I = A.inst[tl.x];
+    if (I.flags & F_POS) run_tile_fast<C, TB, true>(A, I, tl.y, tile_width(C, TB, true), n0);
+    else run_tile_fast<C, TB, false>(A, I, tl.y, tile_width(C, TB, false), n0);
+  }
+}
+
+// variant: 0 general moving perturbation, 1 general moving matter, 2 fast tiles
+// MB: blocks of 128 threads per SM the fast kernel is register-limited to.
+template <int C, int TB, typename T, bool KAHAN = false, int MB = 4>
+int launch_block_shape(int variant, const void* args, int grid, int block, cudaStream_t st) {
+  const BlockArgs<T>& a = *static_cast<const BlockArgs<T>*>(args);
+  if (variant == 2 && !KAHAN) fast_kernel<C, TB, T, MB><<<grid, block, 0, st>>>(a);
+  else if (variant == 1) block_kernel<C, TB, true, T, KAHAN><<<grid, block, 0, st>>>(a);
+  else if (variant == 0) block_kernel<C, TB, false, T, KAHAN><<<grid, block, 0, st>>>(a);
+  else return (int)cudaErrorInvalidValue;
   return (int)cudaGetLastError();
 }
 
-template <int C, int TB, bool MATTER, typename T>
-int occupancy_block_shape(int block, int* nb) {
-  return (int)cudaOccupancyMaxActiveBlocksPerMultiprocessor(nb, block_kernel<C, TB, MATTER, T>,
+template <int C, int TB, typename T, bool KAHAN = false, int MB = 4>
+int occupancy_block_shape(int variant, int block, int* nb) {
+  if (variant == 2 && !KAHAN)
+    return (int)cudaOccupancyMaxActiveBlocksPerMultiprocessor(nb, fast_kernel<C, TB, T, MB>, block, 0);
+  if (variant == 1)
+    return (int)cudaOccupancyMaxActiveBlocksPerMultiprocessor(nb, block_kernel<C, TB, true, T, KAHAN>,
+                                                              block, 0);
+  return (int)cudaOccupancyMaxActiveBlocksPerMultiprocessor(nb, block_kernel<C, TB, false, T, KAHAN>,
                                                             block, 0);
+}
+
+// Whether an instance's interior tiles can take the fast path for C cells per lane.
+__host__ __device__ inline bool fast_eligible(const InstDev& I, int C) {
+  return !(I.flags & F_MATTER) && (I.flags & F_MU_CONST) && !(I.flags & F_LINEAR) &&
+         ((I.flags & F_EPS_CONST) || I.minw > C);
 }
 
 }  // namespace gfdtd

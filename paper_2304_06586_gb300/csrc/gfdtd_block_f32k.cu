@@ -1,0 +1,37 @@
+// gfdtd_block_f32k.cu -- instantiations of the batched time-block kernels for
+// FP32 storage with Kahan-compensated B and D updates (the F32_KAHAN tier).  One translation unit per precision so they compile in parallel.
+// A shape is (cells per lane, steps per time block, blocks per SM that the
+// fast kernel's registers are limited to).
+#include "gfdtd_block.cuh"
+
+namespace gfdtd {
+
+#define GFDTD_SHAPES(X) X(16,16,4) X(8,16,4)
+
+int block_launch_f32k(int variant, int C, int TB, int MB, const void* a, int grid, int block,
+                        cudaStream_t st) {
+#define X(c, tb, mb) \
+  if (C == c && TB == tb && MB == mb) \
+    return launch_block_shape<c, tb, float, true, mb>(variant, a, grid, block, st);
+  GFDTD_SHAPES(X)
+#undef X
+  return (int)cudaErrorInvalidValue;
+}
+
+int block_occupancy_f32k(int variant, int C, int TB, int MB, int block, int* nb) {
+#define X(c, tb, mb) \
+  if (C == c && TB == tb && MB == mb) return occupancy_block_shape<c, tb, float, true, mb>(variant, block, nb);
+  GFDTD_SHAPES(X)
+#undef X
+  return (int)cudaErrorInvalidValue;
+}
+
+int block_shapes_f32k(int* C, int* TB, int* MB, int max) {
+  int n = 0;
+#define X(c, tb, mb) if (n < max) { C[n] = c; TB[n] = tb; MB[n] = mb; ++n; }
+  GFDTD_SHAPES(X)
+#undef X
+  return n;
+}
+
+}  // namespace gfdtd

@@ -26,6 +26,7 @@ struct InstDev {
   int nz_pad;        // nz rounded up to a multiple of 32
   int flags;
   int n;             // layers (LAYERS) or knots (LINEAR)
+  int minw;          // LAYERS: smallest interior layer width in whole cells (node spacing of boundaries)
   int tab;           // first entry of this instance in the profile tables
   int src0, nsrc;    // sources: global indices [src0, src0 + nsrc)
   int prb0, nprb;    // probes: global indices [prb0, prb0 + nprb)
@@ -46,6 +47,19 @@ struct Tables {
   const long long* zq;
   const double2* tabE;
   const double2* tabH;
+  const float2* tabE32;    // the same tables rounded to FP32 (for FP32 arithmetic)
+  const float2* tabH32;
+};
+
+// Table access in the arithmetic type R (float or double).
+template <typename R> struct TabOf;
+template <> struct TabOf<float> {
+  using V = float2;
+  __device__ static const float2* get(const Tables& t, bool eside) { return eside ? t.tabE32 : t.tabH32; }
+};
+template <> struct TabOf<double> {
+  using V = double2;
+  __device__ static const double2* get(const Tables& t, bool eside) { return eside ? t.tabE : t.tabH; }
 };
 
 struct SrcDev {
@@ -77,6 +91,10 @@ struct BlockArgs {
   const T* Din;
   T* Bout;
   T* Dout;
+  const T* cBin;              // Kahan compensation of B and D (F32_KAHAN only)
+  const T* cDin;
+  T* cBout;
+  T* cDout;
   const long long* n_done;    // steps completed at the start of the chunk (device)
   int s0;                     // first step of this launch within the chunk
   int nsteps;                 // steps in this launch (<= time block)
@@ -117,10 +135,13 @@ struct FoldArgs {
 };
 
 // Kernel launchers (gfdtd_kernels.cu).
-int block_launch(int prec, int matter, int C, int TB, const void* args, int grid, int block,
+// variant: 0 general moving perturbation, 1 general moving matter, 2 fast interior tiles
+// A tile shape is (C cells per lane, TB steps per time block, MB blocks per SM
+// the fast kernel is register-limited to).
+int block_launch(int prec, int variant, int C, int TB, int MB, const void* args, int grid, int block,
                  cudaStream_t st);
-int block_occupancy(int prec, int matter, int C, int TB, int block, int* blocks_per_sm);
-int block_shapes(int prec, int* C, int* TB, int max);   // tile shapes built for a precision
+int block_occupancy(int prec, int variant, int C, int TB, int MB, int block, int* blocks_per_sm);
+int block_shapes(int prec, int* C, int* TB, int* MB, int max);   // tile shapes built for a precision
 int plain_launch(int prec, const void* args, int nz, cudaStream_t st);
 int src_amp_launch(const SrcDev* srcs, int nsrc, double* amp, int stride, int nsteps,
                    const long long* n_done, double S, cudaStream_t st);

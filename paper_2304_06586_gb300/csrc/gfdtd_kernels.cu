@@ -4,47 +4,53 @@
 
 namespace gfdtd {
 
-int block_launch_f32(int, int, int, const void*, int, int, cudaStream_t);
-int block_launch_bf16(int, int, int, const void*, int, int, cudaStream_t);
-int block_launch_f16(int, int, int, const void*, int, int, cudaStream_t);
-int block_launch_f64(int, int, int, const void*, int, int, cudaStream_t);
-int block_occupancy_f32(int, int, int, int, int*);
-int block_occupancy_bf16(int, int, int, int, int*);
-int block_occupancy_f16(int, int, int, int, int*);
-int block_occupancy_f64(int, int, int, int, int*);
-int block_shapes_f32(int*, int*, int);
-int block_shapes_bf16(int*, int*, int);
-int block_shapes_f16(int*, int*, int);
-int block_shapes_f64(int*, int*, int);
+int block_launch_f32(int, int, int, int, const void*, int, int, cudaStream_t);
+int block_launch_bf16(int, int, int, int, const void*, int, int, cudaStream_t);
+int block_launch_f16(int, int, int, int, const void*, int, int, cudaStream_t);
+int block_launch_f64(int, int, int, int, const void*, int, int, cudaStream_t);
+int block_launch_f32k(int, int, int, int, const void*, int, int, cudaStream_t);
+int block_occupancy_f32(int, int, int, int, int, int*);
+int block_occupancy_bf16(int, int, int, int, int, int*);
+int block_occupancy_f16(int, int, int, int, int, int*);
+int block_occupancy_f64(int, int, int, int, int, int*);
+int block_occupancy_f32k(int, int, int, int, int, int*);
+int block_shapes_f32(int*, int*, int*, int);
+int block_shapes_bf16(int*, int*, int*, int);
+int block_shapes_f16(int*, int*, int*, int);
+int block_shapes_f64(int*, int*, int*, int);
+int block_shapes_f32k(int*, int*, int*, int);
 
-// prec takes the values of gfdtd_prec: 0 F32, 2 BF16, 3 F16, 4 F64.
-int block_launch(int prec, int matter, int C, int TB, const void* args, int grid, int block,
+// prec takes the values of gfdtd_prec: 0 F32, 1 F32_KAHAN, 2 BF16, 3 F16, 4 F64.
+int block_launch(int prec, int variant, int C, int TB, int MB, const void* args, int grid, int block,
                  cudaStream_t st) {
   switch (prec) {
-    case 0: return block_launch_f32(matter, C, TB, args, grid, block, st);
-    case 2: return block_launch_bf16(matter, C, TB, args, grid, block, st);
-    case 3: return block_launch_f16(matter, C, TB, args, grid, block, st);
-    case 4: return block_launch_f64(matter, C, TB, args, grid, block, st);
+    case 0: return block_launch_f32(variant, C, TB, MB, args, grid, block, st);
+    case 1: return block_launch_f32k(variant, C, TB, MB, args, grid, block, st);
+    case 2: return block_launch_bf16(variant, C, TB, MB, args, grid, block, st);
+    case 3: return block_launch_f16(variant, C, TB, MB, args, grid, block, st);
+    case 4: return block_launch_f64(variant, C, TB, MB, args, grid, block, st);
   }
   return (int)cudaErrorInvalidValue;
 }
 
-int block_occupancy(int prec, int matter, int C, int TB, int block, int* nb) {
+int block_occupancy(int prec, int variant, int C, int TB, int MB, int block, int* nb) {
   switch (prec) {
-    case 0: return block_occupancy_f32(matter, C, TB, block, nb);
-    case 2: return block_occupancy_bf16(matter, C, TB, block, nb);
-    case 3: return block_occupancy_f16(matter, C, TB, block, nb);
-    case 4: return block_occupancy_f64(matter, C, TB, block, nb);
+    case 0: return block_occupancy_f32(variant, C, TB, MB, block, nb);
+    case 1: return block_occupancy_f32k(variant, C, TB, MB, block, nb);
+    case 2: return block_occupancy_bf16(variant, C, TB, MB, block, nb);
+    case 3: return block_occupancy_f16(variant, C, TB, MB, block, nb);
+    case 4: return block_occupancy_f64(variant, C, TB, MB, block, nb);
   }
   return (int)cudaErrorInvalidValue;
 }
 
-int block_shapes(int prec, int* C, int* TB, int max) {
+int block_shapes(int prec, int* C, int* TB, int* MB, int max) {
   switch (prec) {
-    case 0: return block_shapes_f32(C, TB, max);
-    case 2: return block_shapes_bf16(C, TB, max);
-    case 3: return block_shapes_f16(C, TB, max);
-    case 4: return block_shapes_f64(C, TB, max);
+    case 0: return block_shapes_f32(C, TB, MB, max);
+    case 1: return block_shapes_f32k(C, TB, MB, max);
+    case 2: return block_shapes_bf16(C, TB, MB, max);
+    case 3: return block_shapes_f16(C, TB, MB, max);
+    case 4: return block_shapes_f64(C, TB, MB, max);
   }
   return 0;
 }
@@ -230,7 +236,7 @@ static int convert_t(int to_double, const void* src, void* dst, long long n, cud
 
 int convert_launch(int prec, int to_double, const void* src, void* dst, long long n, cudaStream_t st) {
   switch (prec) {
-    case 0: return convert_t<float>(to_double, src, dst, n, st);
+    case 0: case 1: return convert_t<float>(to_double, src, dst, n, st);
     case 2: return convert_t<__nv_bfloat16>(to_double, src, dst, n, st);
     case 3: return convert_t<__half>(to_double, src, dst, n, st);
     case 4: return convert_t<double>(to_double, src, dst, n, st);
@@ -282,7 +288,7 @@ static int derived_t(int which, const InstDev* inst, int i, Tables tb, const voi
 int derived_launch(int prec, int which, const InstDev* inst, int i, Tables tb, const void* B,
                    const void* D, double* out, int nz, long long n, cudaStream_t st) {
   switch (prec) {
-    case 0: return derived_t<float>(which, inst, i, tb, B, D, out, nz, n, st);
+    case 0: case 1: return derived_t<float>(which, inst, i, tb, B, D, out, nz, n, st);
     case 2: return derived_t<__nv_bfloat16>(which, inst, i, tb, B, D, out, nz, n, st);
     case 3: return derived_t<__half>(which, inst, i, tb, B, D, out, nz, n, st);
     case 4: return derived_t<double>(which, inst, i, tb, B, D, out, nz, n, st);
