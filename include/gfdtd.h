@@ -75,7 +75,8 @@ typedef enum {
     GFDTD_E_OOM = -2,          /* device or host allocation failed */
     GFDTD_E_CUDA = -3,         /* a CUDA runtime call failed; see gfdtd_last_error */
     GFDTD_E_UNSTABLE = -4,     /* medium outside the scheme's stability region (n|beta| > 1) */
-    GFDTD_E_TIMEOUT = -5,      /* reserved: a bounded device wait gave up */
+    GFDTD_E_TIMEOUT = -5,      /* a kernel's bounded wait (for its own tile copy) gave up; the
+                                  context stays usable, the affected steps are not valid */
     GFDTD_E_STATE = -6,        /* call not valid in the context's current state */
     GFDTD_E_UNSUPPORTED = -7   /* option not built into this library */
 } gfdtd_status;
@@ -210,7 +211,9 @@ typedef struct {
 
 gfdtd_status gfdtd_get_stats(const gfdtd_ctx* ctx, gfdtd_stats* out);
 
-/* Wait for all work queued on the context's stream. */
+/* Wait for all work queued on the context's stream; returns E_TIMEOUT (once)
+ * if a kernel reported that a bounded wait gave up since the last check.
+ * gfdtd_read_fields and gfdtd_read_spectrum report it the same way. */
 gfdtd_status gfdtd_synchronize(gfdtd_ctx* ctx);
 
 /* Text of the last error on this context (or of the last failed create when

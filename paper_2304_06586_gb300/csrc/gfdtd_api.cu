@@ -452,6 +452,7 @@ static gfdtd_status enqueue_block(gfdtd_ctx* c, cudaStream_t st, int from, int s
     a.cBout = (float*)c->cB[1 - from].p;
     a.cDout = (float*)c->cD[1 - from].p;
     a.n_done = (const long long*)c->d_ndone.p;
+    a.err = (int*)((char*)c->d_ndone.p + 8);
     a.s0 = s0;
     a.nsteps = nsteps;
     a.record = record ? 1 : 0;
@@ -562,6 +563,18 @@ static gfdtd_status autotune(gfdtd_ctx* c) {
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   return set_tiles(c, Cs[bi], TBs[bi], MBs[bi]);
+}
+
+// Reads (after the stream is synchronised) the device status word that kernels
+// set when a bounded wait gave up, and clears it.
+static gfdtd_status device_status(gfdtd_ctx* c) {
+  int err = 0;
+  CK(c, cudaMemcpy(&err, (char*)c->d_ndone.p + 8, sizeof(int), cudaMemcpyDeviceToHost));
+  if (err) {
+    CK(c, cudaMemset((char*)c->d_ndone.p + 8, 0, sizeof(int)));
+    return fail(c, GFDTD_E_TIMEOUT, "a kernel's bounded wait for its tile copy gave up (status %d)", err);
+  }
+  return GFDTD_OK;
 }
 
 static gfdtd_status check_inst(gfdtd_ctx* c, int inst) {
@@ -812,7 +825,7 @@ gfdtd_status gfdtd_read_fields(gfdtd_ctx* c, int inst, gfdtd_field which, double
   }
   CK(c, cudaMemcpyAsync(dst, c->d_tmp.p, (size_t)n * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
   CK(c, cudaStreamSynchronize(c->stream));
-  return GFDTD_OK;
+  return device_status(c);
 }
 
 gfdtd_status gfdtd_write_fields(gfdtd_ctx* c, int inst, gfdtd_field which, const double* src, int64_t n) {
@@ -873,7 +886,7 @@ gfdtd_status gfdtd_read_spectrum(gfdtd_ctx* c, int inst, int probe_id, double* r
   CK(c, cudaMemcpyAsync(re, (double*)c->d_acc_re.p + b0, nb * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
   CK(c, cudaMemcpyAsync(im, (double*)c->d_acc_im.p + b0, nb * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
   CK(c, cudaStreamSynchronize(c->stream));
-  return GFDTD_OK;
+  return device_status(c);
 }
 
 gfdtd_status gfdtd_steps_done(const gfdtd_ctx* c, int64_t* n) {
@@ -932,7 +945,7 @@ gfdtd_status gfdtd_get_stats(const gfdtd_ctx* c, gfdtd_stats* out) {
 gfdtd_status gfdtd_synchronize(gfdtd_ctx* c) {
   if (!c) return GFDTD_E_ARG;
   CK(c, cudaStreamSynchronize(c->stream));
-  return GFDTD_OK;
+  return device_status(c);
 }
 
 const char* gfdtd_last_error(const gfdtd_ctx* c) {

@@ -464,6 +464,52 @@ __device__ __forceinline__ void run_tile(const BlockArgs<T>& A, const InstDev& I
   store_cells<T, R, C>(A.Dout + I.off, k0, x0, hi, D);
 }
 
+// ------------------------------------------------ TMA bulk copies + mbarrier
+
+constexpr long long kWaitLimit = 1LL << 22;   // try_wait polls before a wait is declared failed
+constexpr int kErrTimeout = 1;
+
+__device__ __forceinline__ unsigned smem_u32(const void* p) {
+  return static_cast<unsigned>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ void mbar_init(unsigned long long* bar, unsigned count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void fence_mbar_init() {
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ __forceinline__ void fence_proxy_async() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(unsigned long long* bar, unsigned bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+               : "memory");
+}
+// 1-D bulk copy global -> shared through the TMA unit; completion counts on `bar`.
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, unsigned bytes,
+                                         unsigned long long* bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+          smem_u32(dst)),
+      "l"(src), "r"(bytes), "r"(smem_u32(bar))
+      : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(unsigned long long* bar, unsigned phase) {
+  unsigned ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(phase)
+      : "memory");
+  return ok != 0;
+}
+// Wait for phase `phase` of `bar`, giving up after kWaitLimit polls.
+__device__ __forceinline__ bool mbar_wait_bounded(unsigned long long* bar, unsigned phase) {
+  for (long long it = 0; it < kWaitLimit; ++it)
+    if (mbar_try_wait(bar, phase)) return true;
+  return false;
+}
+
 // ------------------------------------------------ fast tile (common case)
 //
 // Moving perturbation, uniform mu, layered eps whose layers are wider than a
@@ -492,9 +538,10 @@ __device__ __forceinline__ long long track_d(const long long* __restrict__ zq, i
   return __ldg(zq + b) + off;
 }
 
+// sB, sD: the tile's 32 C cells of B and D, already in shared memory.
 template <int C, int TB, bool POS, typename T>
 __device__ __forceinline__ void run_tile_fast(const BlockArgs<T>& A, const InstDev& I, int x0, int W,
-                                              long long n0) {
+                                              long long n0, const T* sB, const T* sD) {
   using R = typename Real<T>::type;
   using V2 = typename TabOf<R>::V;
   const int lane = threadIdx.x & 31;
@@ -503,8 +550,15 @@ __device__ __forceinline__ void run_tile_fast(const BlockArgs<T>& A, const InstD
   const int k0 = base + lane * C;
 
   R B[C], D[C], P[C];
-  load_cells<T, R, C>(A.Bin + I.off, k0, I.nz_pad, B);
-  load_cells<T, R, C>(A.Din + I.off, k0, I.nz_pad, D);
+  {
+    constexpr int V = 16 / sizeof(T);
+#pragma unroll
+    for (int j = 0; j < C / V; ++j) {
+      unpack(*reinterpret_cast<const uint4*>(sB + lane * C + j * V), &B[j * V], T());
+      unpack(*reinterpret_cast<const uint4*>(sD + lane * C + j * V), &D[j * V], T());
+    }
+  }
+  __syncwarp();   // every lane has its cells: the buffer may be refilled
 
   const R a = (R)I.a, cc = (R)I.c, cb = (R)I.cb;
   const R bB0 = POS ? a + cb : a - cb;            // weight of B_j
@@ -673,19 +727,60 @@ __global__ void __launch_bounds__(128) block_kernel(const BlockArgs<T> A) {
 // (or no) layers; the host sorts such tiles into their own list.
 template <int C, int TB, typename T, int MB>
 __global__ void __launch_bounds__(128, MB) fast_kernel(const BlockArgs<T> A) {
-  const int warps_per_block = blockDim.x >> 5;
-  const int gw = blockIdx.x * warps_per_block + (threadIdx.x >> 5);
-  const int nw = gridDim.x * warps_per_block;
+  constexpr int WPB = 4;                    // warps per block (blockDim.x == 128)
+  constexpr int CELLS = 32 * C;
+  constexpr unsigned BYTES = CELLS * sizeof(T);
+  __shared__ __align__(128) T sbuf[WPB][2][2][CELLS];      // [warp][buffer][B, D][cell]
+  __shared__ __align__(8) unsigned long long sbar[WPB][2];
+  const int wib = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int gw = blockIdx.x * WPB + wib;
+  const int nw = gridDim.x * WPB;
   const long long n0 = *A.n_done + A.s0;
-  for (int t = gw; t < A.n_tiles; t += nw) {
+  if (lane == 0) {
+    mbar_init(&sbar[wib][0], 1);
+    mbar_init(&sbar[wib][1], 1);
+    fence_mbar_init();
+  }
+  __syncwarp();
+
+  // lane 0 starts the bulk copies of tile t's input cells into buffer b
+  auto prefetch = [&](int t, int b) {
+    if (lane == 0) {
+      const int2 tl = A.tiles[t];
+      const long long off = A.inst[tl.x].off;
+      const int pos = A.inst[tl.x].flags & F_POS;
+      const long long e = off + tl.y - (pos ? 3 * TB : TB);
+      fence_proxy_async();
+      mbar_expect_tx(&sbar[wib][b], 2 * BYTES);
+      bulk_g2s(&sbuf[wib][b][0][0], A.Bin + e, BYTES, &sbar[wib][b]);
+      bulk_g2s(&sbuf[wib][b][1][0], A.Din + e, BYTES, &sbar[wib][b]);
+    }
+  };
+
+  unsigned phase[2] = {0u, 0u};
+  int t = gw, b = 0;
+  if (t < A.n_tiles) prefetch(t, 0);
+  for (; t < A.n_tiles; t += nw, b ^= 1) {
+    const int tn = t + nw;
+    if (tn < A.n_tiles) prefetch(tn, b ^ 1);
+    const bool ok = __all_sync(FULL, mbar_wait_bounded(&sbar[wib][b], phase[b]));
+    if (!ok) {
+      // give up: report, wait (bounded) for this warp's copies still in flight, leave
+      if (lane == 0) atomicOr(A.err, kErrTimeout);
+      mbar_wait_bounded(&sbar[wib][b], phase[b]);
+      if (tn < A.n_tiles) mbar_wait_bounded(&sbar[wib][b ^ 1], phase[b ^ 1]);
+      return;
+    }
+    phase[b] ^= 1u;
     const int2 tl = A.tiles[t];
     const InstDev I = A.inst[tl.x];
-    if (I.flags & F_POS) run_tile_fast<C, TB, true>(A, I, tl.y, tile_width(C, TB, true), n0);
-    else run_tile_fast<C, TB, false>(A, I, tl.y, tile_width(C, TB, false), n0);
+    const T* sB = &sbuf[wib][b][0][0];
+    const T* sD = &sbuf[wib][b][1][0];
+    if (I.flags & F_POS) run_tile_fast<C, TB, true>(A, I, tl.y, tile_width(C, TB, true), n0, sB, sD);
+    else run_tile_fast<C, TB, false>(A, I, tl.y, tile_width(C, TB, false), n0, sB, sD);
   }
 }
 
-// variant: 0 general moving perturbation, 1 general moving matter, 2 fast tiles
 // MB: blocks of 128 threads per SM the fast kernel is register-limited to.
 template <int C, int TB, typename T, bool KAHAN = false, int MB = 4>
 int launch_block_shape(int variant, const void* args, int grid, int block, cudaStream_t st) {

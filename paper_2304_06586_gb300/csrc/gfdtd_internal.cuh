@@ -99,6 +99,7 @@ struct BlockArgs {
   int s0;                     // first step of this launch within the chunk
   int nsteps;                 // steps in this launch (<= time block)
   int record;                 // nonzero: write probe samples
+  int* err;                   // device status word: bit 0 = a bounded wait gave up
 };
 
 // Arguments of the plain kernel (one instance, one step).
