@@ -187,6 +187,21 @@ gfdtd_status gfdtd_read_spectrum(gfdtd_ctx* ctx, int inst, int probe_id, double*
 /* Steps completed so far (the n of the state (B^n, D^{n+1/2})). */
 gfdtd_status gfdtd_steps_done(const gfdtd_ctx* ctx, int64_t* n);
 
+/* Gradient of probe power with respect to the permittivity profile, by the
+ * discrete adjoint (the transpose of every step of Sec. 4 / Table 1, applied
+ * in reverse time) with sqrt(n_steps) checkpointing.  From the current state,
+ * advances every instance by n_steps >= 1 steps exactly as gfdtd_step does
+ * (state, step count and DFT accumulators included), and returns, per instance
+ * i, loss[i] = L_i = sum_{f = bin_lo}^{bin_hi - 1} |X_f|^2 with X_f the DFT of
+ * its probe `probe_id` accumulated over these n_steps only, and in grad the
+ * derivatives dL_i / d eps_r[j] of every profile value j of instance i (LAYERS:
+ * layer values; LINEAR: knot values), instances concatenated in order.
+ * Moving-perturbation instances and FP32 / F32_KAHAN contexts only
+ * (E_UNSUPPORTED otherwise).  Every instance needs probe `probe_id` with at
+ * least bin_hi bins.  loss: n_inst doubles; grad: sum of n values doubles. */
+gfdtd_status gfdtd_adjoint(gfdtd_ctx* ctx, int64_t n_steps, int probe_id, int bin_lo, int bin_hi,
+                           double* loss, double* grad);
+
 /* Host-only von Neumann analysis (Sec. 5, App. A): max over kz dz in (0, pi]
  * of the modulus of the eigenvalues of the one-step amplification matrix of a
  * uniform medium (eps_r, mu_r) moving at beta with Courant number S. */

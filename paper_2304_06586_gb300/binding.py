@@ -56,6 +56,7 @@ SIGNATURES = {
     "gfdtd_read_spectrum": (C.c_int, [C.c_void_p, C.c_int, C.c_int, _dp, _dp]),
     "gfdtd_steps_done": (C.c_int, [C.c_void_p, _i64p]),
     "gfdtd_stability": (C.c_int, [C.c_double, C.c_double, C.c_double, C.c_double, C.c_int, _dp]),
+    "gfdtd_adjoint": (C.c_int, [C.c_void_p, C.c_int64, C.c_int, C.c_int, C.c_int, _dp, _dp]),
     "gfdtd_set_tuning": (C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_int]),
     "gfdtd_get_stats": (C.c_int, [C.c_void_p, C.POINTER(Stats)]),
     "gfdtd_synchronize": (C.c_int, [C.c_void_p]),
@@ -231,6 +232,18 @@ class Simulation:
         re, im = np.zeros(n_bins), np.zeros(n_bins)
         self._check(self._L.gfdtd_read_spectrum(self._h, inst, probe_id, _ptr(re), _ptr(im)), "read_spectrum")
         return re + 1j * im
+
+    def adjoint(self, n_steps, probe_id, bin_lo, bin_hi, n_values):
+        """gfdtd_adjoint: per-instance loss and d loss / d eps values (list of arrays)."""
+        loss = np.zeros(len(self.nz))
+        grad = np.zeros(int(sum(n_values)))
+        self._check(self._L.gfdtd_adjoint(self._h, int(n_steps), int(probe_id), int(bin_lo), int(bin_hi),
+                                          _ptr(loss), _ptr(grad)), "adjoint")
+        out, o = [], 0
+        for n in n_values:
+            out.append(grad[o:o + n])
+            o += n
+        return loss, out
 
     def steps_done(self):
         n = C.c_int64()

@@ -110,6 +110,11 @@ struct gfdtd_ctx {
   int grid[3] = {0, 0, 0};
   int num_sms = 0;
 
+  // adjoint work buffers (allocated on first use)
+  DevBuf d_ckB, d_ckD, d_dseg, d_wB[2], d_lB[2], d_lD[2], d_grad, d_gn, d_adjn, d_Xre, d_Xim,
+      d_bin0, d_pnode, d_acc0_re, d_acc0_im, d_adj_tiles;
+  int n_adj_tiles = 0;
+
   // graphs keyed by (chunk length, parity)
   std::map<std::pair<int, int>, cudaGraphExec_t> graphs;
   long long launches = 0;
@@ -583,6 +588,202 @@ static gfdtd_status check_inst(gfdtd_ctx* c, int inst) {
   return GFDTD_OK;
 }
 
+
+// One forward step of every instance with explicit buffers: reads (Bin, Din),
+// writes (Bout, Dout); the step taken is *n_done + s0 + 1.  Used by the
+// adjoint's segment recomputation (plain FP32 kernels, no probe samples).
+static gfdtd_status enqueue_one_step(gfdtd_ctx* c, const void* Bin, const void* Din, void* Bout,
+                                     void* Dout, const long long* n_done, int s0) {
+  const int prec = c->prec == GFDTD_F32_KAHAN ? GFDTD_F32 : c->prec;
+  for (int k = 0; k < 3; ++k) {
+    if (c->n_tiles[k] == 0) continue;
+    BlockArgs<float> a{};
+    a.inst = (const InstDev*)c->d_inst.p;
+    a.tiles = (const int2*)c->d_tiles[k].p;
+    a.n_tiles = c->n_tiles[k];
+    a.tb = tables_of(c);
+    a.srcs = (const SrcDev*)c->d_srcs.p;
+    a.src_amp = c->n_src > 0 ? (const double*)c->d_amp.p : nullptr;
+    a.prbs = (const PrbDev*)c->d_prbs.p;
+    a.samples = (double*)c->d_samples.p;
+    a.chunk_stride = kChunk;
+    a.Bin = (const float*)Bin;
+    a.Din = (const float*)Din;
+    a.Bout = (float*)Bout;
+    a.Dout = (float*)Dout;
+    a.n_done = n_done;
+    a.err = (int*)((char*)c->d_ndone.p + 8);
+    a.s0 = s0;
+    a.nsteps = 1;
+    a.record = 0;
+    CKI(c, block_launch(prec, k, c->C, c->TB, c->MB, &a, c->grid[k], kBlock, c->stream));
+    ++c->launches;
+  }
+  return GFDTD_OK;
+}
+
+extern "C" gfdtd_status gfdtd_adjoint(gfdtd_ctx* c, int64_t n_steps, int probe_id, int bin_lo,
+                                      int bin_hi, double* loss, double* grad) {
+  if (!c) return GFDTD_E_ARG;
+  if (n_steps < 1 || !loss || !grad || bin_lo < 0 || bin_hi <= bin_lo)
+    return fail(c, GFDTD_E_ARG, "need n_steps >= 1, 0 <= bin_lo < bin_hi, loss and grad");
+  if (c->prec != GFDTD_F32 && c->prec != GFDTD_F32_KAHAN)
+    return fail(c, GFDTD_E_UNSUPPORTED, "the adjoint is built for FP32 fields");
+  for (int i = 0; i < c->n_inst; ++i) {
+    if (c->media[i].kind != GFDTD_PERTURBATION)
+      return fail(c, GFDTD_E_UNSUPPORTED, "the adjoint is built for moving perturbation");
+    if (probe_id < 0 || probe_id >= (int)c->inst_probes[i].size())
+      return fail(c, GFDTD_E_ARG, "instance %d has no probe %d", i, probe_id);
+    if ((int)c->probes[c->inst_probes[i][probe_id]].omega.size() < bin_hi)
+      return fail(c, GFDTD_E_ARG, "instance %d: probe has fewer than %d bins", i, bin_hi);
+  }
+  gfdtd_status s = finalize(c);
+  if (s) return s;
+  if (c->C == 0 && (s = autotune(c))) return s;
+  cudaStream_t st = c->stream;
+  const long long N = n_steps;
+  const long long K = (long long)std::ceil(std::sqrt((double)N));
+  const long long nseg = (N + K - 1) / K;
+  const size_t fb = (size_t)c->total * c->eb;          // bytes of one field buffer
+  const size_t lb = (size_t)c->total * sizeof(float);
+  const int ntab = (int)(c->d_tabE.bytes / sizeof(double2));
+  if ((s = dalloc(c, c->d_ckB, fb * nseg)) || (s = dalloc(c, c->d_ckD, fb * nseg)) ||
+      (s = dalloc(c, c->d_dseg, fb * (K + 1))) || (s = dalloc(c, c->d_wB[0], fb)) ||
+      (s = dalloc(c, c->d_wB[1], fb)) || (s = dalloc(c, c->d_lB[0], lb)) ||
+      (s = dalloc(c, c->d_lB[1], lb)) || (s = dalloc(c, c->d_lD[0], lb)) ||
+      (s = dalloc(c, c->d_lD[1], lb)) || (s = dalloc(c, c->d_grad, sizeof(double) * ntab)) ||
+      (s = dalloc(c, c->d_gn, sizeof(double) * K * c->n_inst)) || (s = dalloc(c, c->d_adjn, 16)) ||
+      (s = dalloc(c, c->d_acc0_re, sizeof(double) * std::max(1, c->n_bins))) ||
+      (s = dalloc(c, c->d_acc0_im, sizeof(double) * std::max(1, c->n_bins))))
+    return s;
+  // padding cells past nz are never written by the step kernels: keep them zero
+  CK(c, cudaMemsetAsync(c->d_dseg.p, 0, fb * (K + 1), st));
+  CK(c, cudaMemsetAsync(c->d_wB[0].p, 0, fb, st));
+  CK(c, cudaMemsetAsync(c->d_wB[1].p, 0, fb, st));
+  if (c->n_adj_tiles == 0) {
+    std::vector<int2> t;
+    for (int i = 0; i < c->n_inst; ++i)
+      for (long long x0 = 0; x0 < c->nz[i]; x0 += 256) t.push_back(make_int2(i, (int)x0));
+    if ((s = upload(c, c->d_adj_tiles, t))) return s;
+    c->n_adj_tiles = (int)t.size();
+  }
+  // ---- forward with checkpoints at every segment start
+  const long long n0 = c->n_done;
+  CK(c, cudaMemcpyAsync(c->d_acc0_re.p, c->d_acc_re.p, sizeof(double) * c->n_bins, cudaMemcpyDeviceToDevice, st));
+  CK(c, cudaMemcpyAsync(c->d_acc0_im.p, c->d_acc_im.p, sizeof(double) * c->n_bins, cudaMemcpyDeviceToDevice, st));
+  for (long long sg = 0; sg < nseg; ++sg) {
+    CK(c, cudaMemcpyAsync((char*)c->d_ckB.p + sg * fb, c->B[c->cur].p, fb, cudaMemcpyDeviceToDevice, st));
+    CK(c, cudaMemcpyAsync((char*)c->d_ckD.p + sg * fb, c->D[c->cur].p, fb, cudaMemcpyDeviceToDevice, st));
+    long long left = std::min(K, N - sg * K);
+    while (left > 0) {
+      const int ch = (int)std::min<long long>(left, kChunk);
+      if ((s = run_chunk(c, ch))) return s;
+      left -= ch;
+    }
+  }
+  // ---- loss: L_i = sum over the band of |X_f|^2, X accumulated over these steps
+  std::vector<double> re(c->n_bins), im(c->n_bins), re0(c->n_bins), im0(c->n_bins);
+  CK(c, cudaMemcpyAsync(re.data(), c->d_acc_re.p, sizeof(double) * c->n_bins, cudaMemcpyDeviceToHost, st));
+  CK(c, cudaMemcpyAsync(im.data(), c->d_acc_im.p, sizeof(double) * c->n_bins, cudaMemcpyDeviceToHost, st));
+  CK(c, cudaMemcpyAsync(re0.data(), c->d_acc0_re.p, sizeof(double) * c->n_bins, cudaMemcpyDeviceToHost, st));
+  CK(c, cudaMemcpyAsync(im0.data(), c->d_acc0_im.p, sizeof(double) * c->n_bins, cudaMemcpyDeviceToHost, st));
+  CK(c, cudaStreamSynchronize(st));
+  if ((s = device_status(c))) return s;
+  std::vector<double> Xre(c->n_bins, 0.0), Xim(c->n_bins, 0.0);
+  std::vector<int> bin0(c->n_inst), pnode(c->n_inst);
+  for (int i = 0; i < c->n_inst; ++i) {
+    const int p = c->inst_probes[i][probe_id];
+    const int b0 = c->prb_bin0[c->prb_global[p]] + bin_lo;
+    bin0[i] = b0;
+    pnode[i] = (int)c->probes[p].node;
+    double L = 0.0;
+    for (int f = 0; f < bin_hi - bin_lo; ++f) {
+      Xre[b0 + f] = re[b0 + f] - re0[b0 + f];
+      Xim[b0 + f] = im[b0 + f] - im0[b0 + f];
+      L += Xre[b0 + f] * Xre[b0 + f] + Xim[b0 + f] * Xim[b0 + f];
+    }
+    loss[i] = L;
+  }
+  if ((s = upload(c, c->d_Xre, Xre)) || (s = upload(c, c->d_Xim, Xim)) || (s = upload(c, c->d_bin0, bin0)) ||
+      (s = upload(c, c->d_pnode, pnode)))
+    return s;
+  // ---- reverse sweep, segment by segment
+  CK(c, cudaMemsetAsync(c->d_lB[0].p, 0, lb, st));
+  CK(c, cudaMemsetAsync(c->d_lD[0].p, 0, lb, st));
+  CK(c, cudaMemsetAsync(c->d_grad.p, 0, sizeof(double) * ntab, st));
+  int lc = 0;
+  long long host_n = 0;
+  for (long long sg = nseg - 1; sg >= 0; --sg) {
+    const long long ns = n0 + sg * K;                 // steps done at the segment start
+    const int Ks = (int)std::min(K, N - sg * K);
+    host_n = ns;
+    CK(c, cudaMemcpyAsync(c->d_adjn.p, &host_n, sizeof(long long), cudaMemcpyHostToDevice, st));
+    CK(c, cudaMemcpyAsync(c->d_wB[0].p, (char*)c->d_ckB.p + sg * fb, fb, cudaMemcpyDeviceToDevice, st));
+    CK(c, cudaMemcpyAsync(c->d_dseg.p, (char*)c->d_ckD.p + sg * fb, fb, cudaMemcpyDeviceToDevice, st));
+    if (c->n_src > 0)
+      CKI(c, src_amp_launch((const SrcDev*)c->d_srcs.p, c->n_src, (double*)c->d_amp.p, kChunk, Ks,
+                            (const long long*)c->d_adjn.p, c->S, st));
+    for (int m = 1; m <= Ks; ++m) {
+      if ((s = enqueue_one_step(c, c->d_wB[(m - 1) & 1].p, (char*)c->d_dseg.p + (m - 1) * fb,
+                                c->d_wB[m & 1].p, (char*)c->d_dseg.p + m * fb,
+                                (const long long*)c->d_adjn.p, m - 1)))
+        return s;
+    }
+    SourceAdjArgs sa;
+    sa.n_inst = c->n_inst;
+    sa.bin0 = (const int*)c->d_bin0.p;
+    sa.nb = bin_hi - bin_lo;
+    sa.omega = (const double*)c->d_omega.p;
+    sa.Xre = (const double*)c->d_Xre.p;
+    sa.Xim = (const double*)c->d_Xim.p;
+    sa.n_first = ns + 1;
+    sa.steps = Ks;
+    sa.S = c->S;
+    sa.gn = (double*)c->d_gn.p;
+    CKI(c, loss_source_launch(sa, st));
+    for (int m = Ks; m >= 1; --m) {
+      const long long n = ns + m;
+      ProbeAdjArgs pa;
+      pa.inst = (const InstDev*)c->d_inst.p;
+      pa.n_inst = c->n_inst;
+      pa.tb = tables_of(c);
+      pa.probe_node = (const int*)c->d_pnode.p;
+      pa.gn = (const double*)c->d_gn.p + (long long)(m - 1) * c->n_inst;
+      pa.lD = (float*)c->d_lD[lc].p;
+      pa.Dnew = (const float*)((char*)c->d_dseg.p + m * fb);
+      pa.n = n;
+      pa.grad = (double*)c->d_grad.p;
+      CKI(c, probe_adjoint_launch(pa, st));
+      AdjArgs aa;
+      aa.inst = (const InstDev*)c->d_inst.p;
+      aa.tiles = (const int2*)c->d_adj_tiles.p;
+      aa.n_tiles = c->n_adj_tiles;
+      aa.tb = tables_of(c);
+      aa.lBn = (const float*)c->d_lB[lc].p;
+      aa.lDn = (const float*)c->d_lD[lc].p;
+      aa.lB = (float*)c->d_lB[1 - lc].p;
+      aa.lD = (float*)c->d_lD[1 - lc].p;
+      aa.Dold = (const float*)((char*)c->d_dseg.p + (m - 1) * fb);
+      aa.n = n;
+      aa.grad = (double*)c->d_grad.p;
+      CKI(c, adjoint_step_launch(aa, st));
+      c->launches += 2;
+      lc = 1 - lc;
+    }
+    CK(c, cudaStreamSynchronize(st));   // host_n is reused by the next segment's copy
+  }
+  std::vector<double> g(ntab);
+  CK(c, cudaMemcpyAsync(g.data(), c->d_grad.p, sizeof(double) * ntab, cudaMemcpyDeviceToHost, st));
+  CK(c, cudaStreamSynchronize(st));
+  size_t o = 0;
+  for (int i = 0; i < c->n_inst; ++i) {
+    const int nv = (int)c->media[i].eps.size();
+    for (int j = 0; j < nv; ++j) grad[o + j] = g[c->h_inst[i].tab + j];
+    o += nv;
+  }
+  return device_status(c);
+}
+
 // ================================================================== the ABI
 
 extern "C" {
@@ -960,7 +1161,11 @@ void gfdtd_destroy(gfdtd_ctx* c) {
                     &c->cD[1], &c->d_ndone, &c->d_inst, &c->d_zq,
                     &c->d_tabE, &c->d_tabH, &c->d_srcs, &c->d_prbs, &c->d_amp, &c->d_samples,
                     &c->d_omega, &c->d_binprb, &c->d_acc_re, &c->d_acc_im, &c->d_tiles[0],
-                    &c->d_tiles[1], &c->d_tiles[2], &c->d_tmp, &c->d_tabE32, &c->d_tabH32};
+                    &c->d_tiles[1], &c->d_tiles[2], &c->d_tmp, &c->d_tabE32, &c->d_tabH32,
+                    &c->d_ckB, &c->d_ckD, &c->d_dseg, &c->d_wB[0], &c->d_wB[1], &c->d_lB[0],
+                    &c->d_lB[1], &c->d_lD[0], &c->d_lD[1], &c->d_grad, &c->d_gn, &c->d_adjn,
+                    &c->d_Xre, &c->d_Xim, &c->d_bin0, &c->d_pnode, &c->d_acc0_re, &c->d_acc0_im,
+                    &c->d_adj_tiles};
   for (DevBuf* b : bufs) dfree(c, *b);
   if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
   delete c;

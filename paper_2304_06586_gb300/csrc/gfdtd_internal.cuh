@@ -135,6 +135,49 @@ struct FoldArgs {
   double S;
 };
 
+// Adjoint (gfdtd_adjoint.cu).
+struct AdjArgs {
+  const InstDev* inst;
+  const int2* tiles;          // (instance, first cell) of 256-cell blocks
+  int n_tiles;
+  Tables tb;
+  const float* lBn;           // adjoint of B^n, D^{n+1/2}
+  const float* lDn;
+  float* lB;                  // adjoint of B^{n-1}, D^{n-1/2}
+  float* lD;
+  const float* Dold;          // D^{n-1/2}
+  long long n;                // the forward step being transposed
+  double* grad;               // dL/d(profile value), indexed by the instance's table offset
+};
+
+struct ProbeAdjArgs {
+  const InstDev* inst;
+  int n_inst;
+  Tables tb;
+  const int* probe_node;      // per instance
+  const double* gn;           // per instance: dL/dF_n
+  float* lD;
+  const float* Dnew;          // D^{n+1/2}
+  long long n;
+  double* grad;
+};
+
+struct SourceAdjArgs {
+  int n_inst;
+  const int* bin0;            // per instance: first bin of the loss band in the arrays below
+  int nb;                     // bins per instance in the band
+  const double* omega;        // all bins (global bin index)
+  const double* Xre;          // loss-band DFT per global bin
+  const double* Xim;
+  long long n_first;          // first step of the segment
+  int steps;
+  double S;
+  double* gn;                 // [step][inst]
+};
+int adjoint_step_launch(const AdjArgs& a, cudaStream_t st);
+int probe_adjoint_launch(const ProbeAdjArgs& a, cudaStream_t st);
+int loss_source_launch(const SourceAdjArgs& a, cudaStream_t st);
+
 // Kernel launchers (gfdtd_kernels.cu).
 // variant: 0 general moving perturbation, 1 general moving matter, 2 fast interior tiles
 // A tile shape is (C cells per lane, TB steps per time block, MB blocks per SM

@@ -274,3 +274,56 @@ def test_kahan_reduces_accumulated_rounding():
     print("accumulated rounding: F32 %.3e, F32_KAHAN %.3e" % (errs[gb.F32], errs[gb.F32_KAHAN]))
     assert errs[gb.F32_KAHAN] <= TOL32
     assert errs[gb.F32_KAHAN] < 0.5 * errs[gb.F32]
+
+
+def _adjoint_workload(n_inst=3, seed=31):
+    """Config-5 shape at reduced size: PWL eps over a moving region, transmitted probe."""
+    base = w.config5(n_inst=n_inst, nz=1 << 11, n_steps=3400, n_ctrl=48, seed=seed)
+    out = []
+    for k, I in enumerate(base.instances):
+        beta = (0.4, -0.3, 0.25)[k % 3]
+        out.append(w.InstanceSpec(nz=I.nz, beta=beta, interp=w.LINEAR, z=I.z - 2046.0 + 600.0,
+                                  eps=I.eps, mu=I.mu, sources=[w.gaussian_source(200, 40.0, 3.0)],
+                                  probes=[(1300 if beta > 0 else 300, I.probes[0][1])]))
+    return w.Workload("adjoint_small", base.S, base.n_steps, out)
+
+
+def test_adjoint_matches_oracle_adjoint():
+    """GPU adjoint (checkpointed, FP32 fields, FP64 gradients) vs the oracle's FP64 adjoint."""
+    wl = _adjoint_workload()
+    sim = make_sim(wl, allow_unstable=False)
+    nv = [len(I.eps) for I in wl.instances]
+    loss, grads = sim.adjoint(wl.n_steps, 0, 0, 16, nv)
+    assert sim.steps_done() == wl.n_steps
+    for k, o in enumerate(make_oracle(wl)):
+        L, g = o.adjoint(0, range(16), wl.n_steps)
+        assert abs(loss[k] - L) <= 1e-4 * L, (k, loss[k], L)
+        assert rel_l2(grads[k], g) <= 1e-3, (k, rel_l2(grads[k], g))
+        # the 48 interior controls on their own (the end knots dominate the vector)
+        assert rel_l2(grads[k][1:-1], g[1:-1]) <= 1e-3, (k, rel_l2(grads[k][1:-1], g[1:-1]))
+
+
+def test_adjoint_matches_finite_differences():
+    """dL/d(control eps) from the GPU adjoint vs central differences of the FP64
+    oracle's loss (h = 1e-4) on a few control points."""
+    wl = _adjoint_workload(n_inst=1)
+    sim = make_sim(wl, allow_unstable=False)
+    loss, grads = sim.adjoint(wl.n_steps, 0, 0, 16, [len(wl.instances[0].eps)])
+    I = wl.instances[0]
+    import oracle
+
+    def L_of(eps):
+        o = oracle.Instance(I.nz, wl.S, I.beta, interp=1, z=I.z, eps=eps, mu=I.mu)
+        o.add_source(*I.sources[0])
+        o.add_probe(I.probes[0][0], I.probes[0][1])
+        o.run(wl.n_steps)
+        return float(np.sum(np.abs(o.spectrum(0)) ** 2))
+
+    g = grads[0]
+    h = 1e-4
+    for j in (3, 17, 30, 44):
+        ep, em = I.eps.copy(), I.eps.copy()
+        ep[j] += h
+        em[j] -= h
+        fd = (L_of(ep) - L_of(em)) / (2 * h)
+        assert abs(g[j] - fd) <= 1e-3 * np.abs(g).max(), (j, g[j], fd)
