@@ -235,6 +235,28 @@ gfdtd_status gfdtd_synchronize(gfdtd_ctx* ctx);
  * ctx is NULL).  Valid until the next call on the context. */
 const char* gfdtd_last_error(const gfdtd_ctx* ctx);
 
+/* Allocation-free stepping (the paper has no counterpart: this is a service
+ * for callers that cannot allocate device memory -- code being recorded into
+ * a CUDA graph, where cudaMalloc cannot be captured; processes whose device
+ * memory belongs to another framework's pool; loops that must never block on
+ * an allocator).  Advances ONE instance held in caller-owned device buffers
+ * B and D (FP32, nz elements each, the state (B^n, D^{n+1/2}) with n =
+ * n_done) by n_steps steps, with the medium given as in gfdtd_set_medium, no
+ * sources and no probes, using the same kernels and tile shape (16 cells per
+ * lane, 16 steps per time block) as gfdtd_step.  Every working buffer lives
+ * in one statically allocated device array of about 4.4 MB that each GPU
+ * loading this library keeps until the process exits; no call allocates or
+ * frees memory.  Limits: 1 <= nz <= 2^18 and n <= 1024 profile values,
+ * otherwise E_ARG.  The first call on a device looks up the array's device
+ * address (cudaGetSymbolAddress); make that first call outside any stream
+ * capture.  All calls share the array: calls whose work overlaps on the GPU
+ * (other streams, other threads) race and corrupt each other.  The call
+ * returns when the work on `cuda_stream` has finished. */
+gfdtd_status gfdtd_step_noalloc(int64_t nz, double S, gfdtd_kind kind, double beta,
+                                gfdtd_interp interp, int n, const double* z, const double* eps_r,
+                                const double* mu_r, float* B, float* D, int64_t n_done,
+                                int64_t n_steps, void* cuda_stream);
+
 /* Release the context and all its device memory.  NULL is ignored. */
 void gfdtd_destroy(gfdtd_ctx* ctx);
 

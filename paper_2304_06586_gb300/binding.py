@@ -62,6 +62,8 @@ SIGNATURES = {
     "gfdtd_synchronize": (C.c_int, [C.c_void_p]),
     "gfdtd_last_error": (C.c_char_p, [C.c_void_p]),
     "gfdtd_destroy": (None, [C.c_void_p]),
+    "gfdtd_step_noalloc": (C.c_int, [C.c_int64, C.c_double, C.c_int, C.c_double, C.c_int, C.c_int, _dp,
+                                     _dp, _dp, C.c_void_p, C.c_void_p, C.c_int64, C.c_int64, C.c_void_p]),
 }
 
 _lib = None
@@ -135,6 +137,20 @@ def stability(S, beta, eps_r, mu_r=1.0, kind=PERTURBATION):
     if rc != OK:
         raise GfdtdError(rc, "gfdtd_stability")
     return out.value
+
+
+def step_noalloc(B_ptr, D_ptr, nz, S, kind=PERTURBATION, beta=0.0, interp=LAYERS, z=(), eps=(1.0,),
+                 mu=None, n_done=0, n_steps=1, stream=0):
+    """gfdtd_step_noalloc: advance one instance held in caller-owned device buffers
+    (FP32 device pointers B_ptr, D_ptr of nz elements) without allocating."""
+    eps = _f64(eps)
+    mu = _f64(np.ones_like(eps) if mu is None else mu)
+    z = _f64(z) if len(z) else np.zeros(1)
+    rc = load().gfdtd_step_noalloc(int(nz), float(S), kind, float(beta), interp, len(eps), _ptr(z),
+                                   _ptr(eps), _ptr(mu), C.c_void_p(B_ptr), C.c_void_p(D_ptr),
+                                   int(n_done), int(n_steps), C.c_void_p(stream))
+    if rc != OK:
+        raise GfdtdError(rc, "gfdtd_step_noalloc")
 
 
 class Simulation:
