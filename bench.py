@@ -54,6 +54,23 @@ def dist_setup():
     return rank, world, local
 
 
+def rank_workload(rank, n_inst, time_steps):
+    """The batch a rank runs: instances are independent, so every rank steps its
+    own seeded batch of the crystal workload (weak scaling, no data exchange)."""
+    from paper_2304_06586_gb300 import workloads as w
+    return w.config3(n_inst=n_inst, n_steps=time_steps, seed=w.SEED0 + 3 + 1000 * rank)
+
+
+def max_over_ranks(value, dist=None, device="cpu"):
+    """The job's time is the slowest rank's (all_reduce MAX); identity on one rank."""
+    if dist is None:
+        return float(value)
+    import torch
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 class Clocks:
     """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
 
@@ -158,8 +175,7 @@ def run_reference(args, wl, rank):
 def main():
     args = parse()
     rank, world, local = dist_setup()
-    from paper_2304_06586_gb300 import workloads as w
-    wl = w.config3(n_inst=args.instances, n_steps=args.time_steps, seed=w.SEED0 + 3 + 1000 * rank)
+    wl = rank_workload(rank, args.instances, args.time_steps)
     if args.impl == "reference":
         return run_reference(args, wl, rank)
 
@@ -199,13 +215,9 @@ def main():
                 sim.step(T)
             e1.record(stream)
             barrier()
-        ms = e0.elapsed_time(e1)
+        ms = max_over_ranks(e0.elapsed_time(e1), pg, "cuda")
         st = sim.stats()
         launches = st["kernel_launches"] - l0
-        if pg:
-            t = torch.tensor([ms], device="cuda")
-            pg.all_reduce(t, op=pg.ReduceOp.MAX)
-            ms = float(t.item())
         cells = st["cells"]
         cu = cells * T * args.steps
         value = cu * world / (ms / 1e3) / 1e9
@@ -242,11 +254,7 @@ def main():
                 sim.read_state(gb.FIELD_D, hD.data_ptr(), nbytes)
                 sim.synchronize()
             barrier()
-            dt = time.perf_counter() - t0
-            if pg:
-                t = torch.tensor([dt], device="cuda")
-                pg.all_reduce(t, op=pg.ReduceOp.MAX)
-                dt = float(t.item())
+            dt = max_over_ranks(time.perf_counter() - t0, pg, "cuda")
             e2e = {"value": cu * world / dt / 1e9, "unit": "Gcell-updates/s",
                    "h2d_bytes_per_step": 2 * nbytes, "d2h_bytes_per_step": 2 * nbytes}
 

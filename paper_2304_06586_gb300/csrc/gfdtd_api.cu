@@ -96,7 +96,7 @@ struct gfdtd_ctx {
   // device tables (rebuilt by finalize)
   bool dirty = true;
   DevBuf d_inst, d_zq, d_tabE, d_tabH, d_srcs, d_prbs, d_amp, d_samples, d_omega, d_binprb,
-      d_acc_re, d_acc_im, d_tiles[3], d_tmp, d_tabE32, d_tabH32;
+      d_acc_re, d_acc_im, d_tiles[3], d_tmp, d_tabE32, d_tabH32, d_hint;
   std::vector<InstDev> h_inst;
   std::vector<int> prb_global;          // probe creation index -> global (instance-sorted) index
   std::vector<int> prb_bin0;
@@ -271,6 +271,9 @@ static gfdtd_status set_tiles(gfdtd_ctx* c, int C, int TB, int MB) {
   std::vector<int2> t[3];
   gfdtd_status s = build_tiles(c, C, TB, t);
   if (s) return s;
+  // per fast tile and lane: the lane's next layer boundary, kept between launches
+  if ((s = dalloc(c, c->d_hint, std::max<size_t>(16, t[2].size() * 32 * sizeof(int))))) return s;
+  CK(c, cudaMemsetAsync(c->d_hint.p, 0xff, std::max<size_t>(16, t[2].size() * 32 * sizeof(int)), c->stream));
   for (int k = 0; k < 3; ++k) {
     s = upload(c, c->d_tiles[k], t[k]);
     if (s) return s;
@@ -458,6 +461,7 @@ static gfdtd_status enqueue_block(gfdtd_ctx* c, cudaStream_t st, int from, int s
     a.cDout = (float*)c->cD[1 - from].p;
     a.n_done = (const long long*)c->d_ndone.p;
     a.err = (int*)((char*)c->d_ndone.p + 8);
+    a.hint = (k == 2 && record) ? (int*)c->d_hint.p : nullptr;   // tuning trials leave it alone
     a.s0 = s0;
     a.nsteps = nsteps;
     a.record = record ? 1 : 0;
@@ -1161,7 +1165,7 @@ void gfdtd_destroy(gfdtd_ctx* c) {
                     &c->cD[1], &c->d_ndone, &c->d_inst, &c->d_zq,
                     &c->d_tabE, &c->d_tabH, &c->d_srcs, &c->d_prbs, &c->d_amp, &c->d_samples,
                     &c->d_omega, &c->d_binprb, &c->d_acc_re, &c->d_acc_im, &c->d_tiles[0],
-                    &c->d_tiles[1], &c->d_tiles[2], &c->d_tmp, &c->d_tabE32, &c->d_tabH32,
+                    &c->d_tiles[1], &c->d_tiles[2], &c->d_tmp, &c->d_tabE32, &c->d_tabH32, &c->d_hint,
                     &c->d_ckB, &c->d_ckD, &c->d_dseg, &c->d_wB[0], &c->d_wB[1], &c->d_lB[0],
                     &c->d_lB[1], &c->d_lD[0], &c->d_lD[1], &c->d_grad, &c->d_gn, &c->d_adjn,
                     &c->d_Xre, &c->d_Xim, &c->d_bin0, &c->d_pnode, &c->d_acc0_re, &c->d_acc0_im,

@@ -541,7 +541,7 @@ __device__ __forceinline__ long long track_d(const long long* __restrict__ zq, i
 // sB, sD: the tile's 32 C cells of B and D, already in shared memory.
 template <int C, int TB, bool POS, typename T>
 __device__ __forceinline__ void run_tile_fast(const BlockArgs<T>& A, const InstDev& I, int x0, int W,
-                                              long long n0, const T* sB, const T* sD) {
+                                              long long n0, const T* sB, const T* sD, int t) {
   using R = typename Real<T>::type;
   using V2 = typename TabOf<R>::V;
   const int lane = threadIdx.x & 31;
@@ -570,10 +570,22 @@ __device__ __forceinline__ void run_tile_fast(const BlockArgs<T>& A, const InstD
   const int nb = I.n - 1;
   const long long dq2 = 2 * I.dq;
 
-  // boundary tracker at half level h = 2 n0 + 1 (the first E' of this launch)
+  // boundary tracker at half level h = 2 n0 + 1 (the first E' of this launch).
+  // The lane's next boundary is kept per tile between launches; it moves by at
+  // most one boundary per launch, so checking the stored index is enough.
   BoundaryTrack tr;
-  const long long off0 = I.dq * (2 * n0 + 1) - ((long long)k0 << 32);
-  tr.bnext = count_at_or_left(zq, nb, I.dq * (2 * n0 + 1), k0);
+  const long long offh = I.dq * (2 * n0 + 1);
+  const long long off0 = offh - ((long long)k0 << 32);
+  {
+    int b = A.hint ? A.hint[(long long)t * 32 + lane] : -1;
+    if (b < 0 || b > nb) {
+      b = count_at_or_left(zq, nb, offh, k0);
+    } else {
+      while (b < nb && node_of(__ldg(zq + b), offh) <= k0) ++b;
+      while (b > 0 && node_of(__ldg(zq + b - 1), offh) > k0) --b;
+    }
+    tr.bnext = b;
+  }
   tr.dprev = track_d(zq, tr.bnext - 1, nb, off0);
   tr.dnext = track_d(zq, tr.bnext, nb, off0);
   R vL = __ldg(tv + tr.bnext).x;
@@ -689,6 +701,7 @@ __device__ __forceinline__ void run_tile_fast(const BlockArgs<T>& A, const InstD
     }
   }
 
+  if (A.hint) A.hint[(long long)t * 32 + lane] = tr.bnext;
   const int hi = min(x0 + W, I.nz_pad);
   store_cells<T, R, C>(A.Bout + I.off, k0, x0, hi, B);
   store_cells<T, R, C>(A.Dout + I.off, k0, x0, hi, D);
@@ -776,8 +789,8 @@ __global__ void __launch_bounds__(128, MB) fast_kernel(const BlockArgs<T> A) {
     const InstDev I = A.inst[tl.x];
     const T* sB = &sbuf[wib][b][0][0];
     const T* sD = &sbuf[wib][b][1][0];
-    if (I.flags & F_POS) run_tile_fast<C, TB, true>(A, I, tl.y, tile_width(C, TB, true), n0, sB, sD);
-    else run_tile_fast<C, TB, false>(A, I, tl.y, tile_width(C, TB, false), n0, sB, sD);
+    if (I.flags & F_POS) run_tile_fast<C, TB, true>(A, I, tl.y, tile_width(C, TB, true), n0, sB, sD, t);
+    else run_tile_fast<C, TB, false>(A, I, tl.y, tile_width(C, TB, false), n0, sB, sD, t);
   }
 }
 

@@ -100,6 +100,8 @@ struct BlockArgs {
   int nsteps;                 // steps in this launch (<= time block)
   int record;                 // nonzero: write probe samples
   int* err;                   // device status word: bit 0 = a bounded wait gave up
+  int* hint;                  // fast tiles: per tile and lane, the lane's next layer boundary
+                              // at the end of the last launch (-1: unknown); NULL: not kept
 };
 
 // Arguments of the plain kernel (one instance, one step).

@@ -17,7 +17,7 @@ from paper_2304_06586_gb300 import workloads as w
 pytestmark = pytest.mark.gpu
 
 TOL32 = 1e-4
-SHAPES = [(16, 8), (16, 16), (16, 32), (8, 16)]
+SHAPES = [(16, 8), (16, 16), (16, 32), (8, 16), (16, 16, 5)]
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -204,10 +204,11 @@ def test_precision_tiers(prec, tol):
     print("precision tier", prec, "worst relative L2", worst)
 
 
-def test_crystal_small_matches_oracle():
+@pytest.mark.parametrize("tuning", [None, (16, 16, 5)])
+def test_crystal_small_matches_oracle(tuning):
     """Config-3 shape at reduced size (stable velocities), from rest, sources and probes."""
     wl = w.config3(n_inst=48, nz_lo=1 << 10, nz_hi=1 << 13, n_steps=600, stable_only=True)
-    sim = make_sim(wl, allow_unstable=False)
+    sim = make_sim(wl, allow_unstable=False, tuning=tuning)
     orcs = make_oracle(wl)
     sim.step(wl.n_steps)
     import oracle
