@@ -96,7 +96,7 @@ struct gfdtd_ctx {
   // device tables (rebuilt by finalize)
   bool dirty = true;
   DevBuf d_inst, d_zq, d_tabE, d_tabH, d_srcs, d_prbs, d_amp, d_samples, d_omega, d_binprb,
-      d_acc_re, d_acc_im, d_tiles[3], d_tmp, d_tabE32, d_tabH32, d_hint;
+      d_acc_re, d_acc_im, d_tiles[3], d_tmp, d_tabE32, d_tabH32, d_ftiles, d_track;
   std::vector<InstDev> h_inst;
   std::vector<int> prb_global;          // probe creation index -> global (instance-sorted) index
   std::vector<int> prb_bin0;
@@ -240,10 +240,13 @@ static std::vector<float2> to_f32(const std::vector<double2>& v) {
 
 // Tiles of every instance, split by kernel variant: 0 general moving
 // perturbation, 1 general moving matter, 2 fast interior tiles (see
-// fast_kernel).  Each list is ordered by the sign of v so that warps running
-// at the same time execute the same code.
-static gfdtd_status build_tiles(gfdtd_ctx* c, int C, int TB, std::vector<int2> out[3]) {
+// fast_kernel), with the fast kernel's tile records in `fast` (the order of
+// out[2]).  Each list is ordered by the sign of v so that warps running at the
+// same time execute the same code.
+static gfdtd_status build_tiles(gfdtd_ctx* c, int C, int TB, std::vector<int2> out[3],
+                                std::vector<FastTile>& fast) {
   std::vector<int2> part[3][2];
+  std::vector<FastTile> fpart[2];
   for (int i = 0; i < c->n_inst; ++i) {
     const InstDev& d = c->h_inst[i];
     const bool pos = (d.flags & F_POS) != 0;
@@ -256,12 +259,29 @@ static gfdtd_status build_tiles(gfdtd_ctx* c, int C, int TB, std::vector<int2> o
       const bool edge = base < 0 || base + 32LL * C > c->nz[i];
       const int v = matter ? 1 : (fast_ok && !edge ? 2 : 0);
       part[v][pos ? 0 : 1].push_back(make_int2(i, (int)x0));
+      if (v == 2) {
+        FastTile f{};
+        f.e = d.off + base;
+        f.inst = i;
+        f.x0 = (int)x0;
+        const std::vector<SrcDev>& src = c->sources[i];
+        for (size_t q = 0; q < src.size() && q < 32; ++q)
+          if (src[q].node >= base && src[q].node < base + 32LL * C) f.smask |= 1u << q;
+        const std::vector<int>& prb = c->inst_probes[i];
+        for (size_t q = 0; q < prb.size() && q < 32; ++q) {
+          const long long node = c->probes[prb[q]].node;
+          if (node >= x0 && node < x0 + W && node < c->nz[i]) f.pmask |= 1u << q;
+        }
+        fpart[pos ? 0 : 1].push_back(f);
+      }
     }
   }
   for (int v = 0; v < 3; ++v) {
     out[v] = part[v][0];
     out[v].insert(out[v].end(), part[v][1].begin(), part[v][1].end());
   }
+  fast = fpart[0];
+  fast.insert(fast.end(), fpart[1].begin(), fpart[1].end());
   if (out[0].size() + out[1].size() + out[2].size() > (size_t)INT32_MAX)
     return fail(c, GFDTD_E_ARG, "too many tiles");
   return GFDTD_OK;
@@ -269,11 +289,14 @@ static gfdtd_status build_tiles(gfdtd_ctx* c, int C, int TB, std::vector<int2> o
 
 static gfdtd_status set_tiles(gfdtd_ctx* c, int C, int TB, int MB) {
   std::vector<int2> t[3];
-  gfdtd_status s = build_tiles(c, C, TB, t);
+  std::vector<FastTile> ft;
+  gfdtd_status s = build_tiles(c, C, TB, t, ft);
   if (s) return s;
-  // per fast tile and lane: the lane's next layer boundary, kept between launches
-  if ((s = dalloc(c, c->d_hint, std::max<size_t>(16, t[2].size() * 32 * sizeof(int))))) return s;
-  CK(c, cudaMemsetAsync(c->d_hint.p, 0xff, std::max<size_t>(16, t[2].size() * 32 * sizeof(int)), c->stream));
+  if ((s = upload(c, c->d_ftiles, ft))) return s;
+  // per fast tile: the boundary trackers of its lanes, kept between launches (n = -1: none yet)
+  const size_t track_bytes = std::max<size_t>(sizeof(TrackTile), ft.size() * sizeof(TrackTile));
+  if ((s = dalloc(c, c->d_track, track_bytes))) return s;
+  CK(c, cudaMemsetAsync(c->d_track.p, 0xff, track_bytes, c->stream));
   for (int k = 0; k < 3; ++k) {
     s = upload(c, c->d_tiles[k], t[k]);
     if (s) return s;
@@ -342,6 +365,10 @@ static gfdtd_status finalize(gfdtd_ctx* c) {
     d.inv_S = 1.0 / S;
     d.beta = m.beta;
     d.cb = 0.5 * S * m.beta;
+    d.a32 = (float)d.a;
+    d.c32 = (float)d.c;
+    d.cb32 = (float)d.cb;
+    d.sm32 = 0.0f;
     int flags = 0;
     if (m.beta >= 0.0) flags |= F_POS;
     if (m.kind == GFDTD_MATTER) flags |= F_MATTER;
@@ -373,6 +400,7 @@ static gfdtd_status finalize(gfdtd_ctx* c) {
       d.minw = wmin > 1e9 ? (1 << 30) : std::max(0, (int)std::floor(wmin) - 1);
       if (econst) flags |= F_EPS_CONST;
       if (mconst) flags |= F_MU_CONST;
+      d.sm32 = (float)tabH[d.tab].x;
     }
     while (zq.size() < tabE.size()) zq.push_back(0);
     d.flags = flags;
@@ -461,7 +489,8 @@ static gfdtd_status enqueue_block(gfdtd_ctx* c, cudaStream_t st, int from, int s
     a.cDout = (float*)c->cD[1 - from].p;
     a.n_done = (const long long*)c->d_ndone.p;
     a.err = (int*)((char*)c->d_ndone.p + 8);
-    a.hint = (k == 2 && record) ? (int*)c->d_hint.p : nullptr;   // tuning trials leave it alone
+    a.ftiles = k == 2 ? (const FastTile*)c->d_ftiles.p : nullptr;
+    a.track = (k == 2 && record) ? (TrackTile*)c->d_track.p : nullptr;   // tuning trials leave it alone
     a.s0 = s0;
     a.nsteps = nsteps;
     a.record = record ? 1 : 0;
@@ -620,6 +649,7 @@ static gfdtd_status enqueue_one_step(gfdtd_ctx* c, const void* Bin, const void* 
     a.s0 = s0;
     a.nsteps = 1;
     a.record = 0;
+    a.ftiles = k == 2 ? (const FastTile*)c->d_ftiles.p : nullptr;
     CKI(c, block_launch(prec, k, c->C, c->TB, c->MB, &a, c->grid[k], kBlock, c->stream));
     ++c->launches;
   }
@@ -1165,7 +1195,7 @@ void gfdtd_destroy(gfdtd_ctx* c) {
                     &c->cD[1], &c->d_ndone, &c->d_inst, &c->d_zq,
                     &c->d_tabE, &c->d_tabH, &c->d_srcs, &c->d_prbs, &c->d_amp, &c->d_samples,
                     &c->d_omega, &c->d_binprb, &c->d_acc_re, &c->d_acc_im, &c->d_tiles[0],
-                    &c->d_tiles[1], &c->d_tiles[2], &c->d_tmp, &c->d_tabE32, &c->d_tabH32, &c->d_hint,
+                    &c->d_tiles[1], &c->d_tiles[2], &c->d_tmp, &c->d_tabE32, &c->d_tabH32, &c->d_ftiles, &c->d_track,
                     &c->d_ckB, &c->d_ckD, &c->d_dseg, &c->d_wB[0], &c->d_wB[1], &c->d_lB[0],
                     &c->d_lB[1], &c->d_lD[0], &c->d_lD[1], &c->d_grad, &c->d_gn, &c->d_adjn,
                     &c->d_Xre, &c->d_Xim, &c->d_bin0, &c->d_pnode, &c->d_acc0_re, &c->d_acc0_im,

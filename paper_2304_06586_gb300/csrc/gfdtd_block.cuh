@@ -519,10 +519,20 @@ __device__ __forceinline__ bool mbar_wait_bounded(unsigned long long* bar, unsig
 //            D'_k = a D_k + (c - cb) D_{k-1} + cb D_{k+1} + sm (B'_{k-1} - B'_k)
 //   v <  0:  B'_j = (a - cb) B_j + c B_{j+1} + cb B_{j+2} + P_j - P_{j+1}
 //            D'_k = a D_k + (c + cb) D_{k+1} - cb D_{k-1} + sm (B'_{k-1} - B'_k)
-// (the same equations, regrouped).  The material of a lane is tracked with
-// the two layer boundaries around its first cell k0: d = zq + dq h - k0 2^32
-// grows by 2 dq per step, and cells c >= ceil(d / 2^32) of the run lie beyond
-// the boundary.
+// (the same equations, regrouped).  Inside the tile B is carried as
+// Bs = sm B (sm uniform), which removes the multiply by sm from the D update:
+// Bs'_j = (same weights) Bs + sm (P_j - P_{j+1}) and D'_k = ... + Bs'_{k-1} - Bs'_k;
+// the factor sm is applied to the layer values, so P holds sm se D.  The
+// material of a lane is tracked with the two layer boundaries around its first
+// cell k0: d = zq + dq h - k0 2^32 grows by 2 dq per step, and cells
+// c >= ceil(d / 2^32) of the run lie beyond the boundary.  The B update takes
+// one multiplier per lane (the layer of the whole run); the few lanes with a
+// boundary inside their run then add the difference of the two layers' P.
+
+// The FP64 or the FP32 copy of an instance coefficient, whichever R is.
+template <typename R> __device__ __forceinline__ R coef(double d, float f);
+template <> __device__ __forceinline__ float coef<float>(double, float f) { return f; }
+template <> __device__ __forceinline__ double coef<double>(double d, float) { return d; }
 
 struct BoundaryTrack {
   long long dprev, dnext;     // zq_b + dq h - k0 2^32 of the boundaries around k0
@@ -538,18 +548,22 @@ __device__ __forceinline__ long long track_d(const long long* __restrict__ zq, i
   return __ldg(zq + b) + off;
 }
 
-// sB, sD: the tile's 32 C cells of B and D, already in shared memory.
+// sB, sD: the tile's 32 C cells of B and D, and sT: the tracker state saved
+// for the tile by the previous launch (NULL: none kept), all in shared memory.
 template <int C, int TB, bool POS, typename T>
-__device__ __forceinline__ void run_tile_fast(const BlockArgs<T>& A, const InstDev& I, int x0, int W,
-                                              long long n0, const T* sB, const T* sD, int t) {
+__device__ __forceinline__ void run_tile_fast(const BlockArgs<T>& A, const InstDev& I, const FastTile& ft,
+                                              long long n0, const T* sB, const T* sD,
+                                              const TrackTile* sT, int t) {
   using R = typename Real<T>::type;
   using V2 = typename TabOf<R>::V;
   const int lane = threadIdx.x & 31;
-  constexpr int L = POS ? 3 * TB : TB;
+  constexpr int L = POS ? 3 * TB : TB;               // upwind cone of TB steps
+  constexpr int W = 32 * C - (POS ? 4 * TB : 3 * TB);  // output cells
+  const int x0 = ft.x0;
   const int base = x0 - L;
   const int k0 = base + lane * C;
 
-  R B[C], D[C], P[C];
+  R B[C], D[C];
   {
     constexpr int V = 16 / sizeof(T);
 #pragma unroll
@@ -558,102 +572,128 @@ __device__ __forceinline__ void run_tile_fast(const BlockArgs<T>& A, const InstD
       unpack(*reinterpret_cast<const uint4*>(sD + lane * C + j * V), &D[j * V], T());
     }
   }
-  __syncwarp();   // every lane has its cells: the buffer may be refilled
+  R sm;                                             // S / mu, uniform in a fast tile
+  if constexpr (sizeof(R) == 4) sm = I.sm32;
+  else sm = __ldg(&A.tb.tabH[I.tab].x);
+#pragma unroll
+  for (int c = 0; c < C; ++c) B[c] *= sm;          // Bs = sm B
 
-  const R a = (R)I.a, cc = (R)I.c, cb = (R)I.cb;
+  const R a = coef<R>(I.a, I.a32), cc = coef<R>(I.c, I.c32), cb = coef<R>(I.cb, I.cb32);
   const R bB0 = POS ? a + cb : a - cb;            // weight of B_j
   const R bD1 = POS ? cc - cb : cc + cb;          // weight of the upwind D neighbour
   const R bD2 = POS ? cb : -cb;                   // weight of the downwind D neighbour
   const V2* __restrict__ tv = TabOf<R>::get(A.tb, true) + I.tab;
   const long long* __restrict__ zq = A.tb.zq + I.tab;
-  const R sm = (R)__ldg(TabOf<R>::get(A.tb, false) + I.tab).x;
   const int nb = I.n - 1;
   const long long dq2 = 2 * I.dq;
 
-  // boundary tracker at half level h = 2 n0 + 1 (the first E' of this launch).
-  // The lane's next boundary is kept per tile between launches; it moves by at
-  // most one boundary per launch, so checking the stored index is enough.
+  // boundary tracker at half level h = 2 n0 + 1 (the first E' of this launch):
+  // the state the previous launch left for this tile if it ended at n0, else
+  // found by binary search.
   BoundaryTrack tr;
-  const long long offh = I.dq * (2 * n0 + 1);
-  const long long off0 = offh - ((long long)k0 << 32);
-  {
-    int b = A.hint ? A.hint[(long long)t * 32 + lane] : -1;
-    if (b < 0 || b > nb) {
-      b = count_at_or_left(zq, nb, offh, k0);
+  R vL, vR;
+  if (sT && sT->n == n0) {
+    const TrackLane& s = sT->lane[lane];
+    tr.dprev = s.dprev;
+    tr.dnext = s.dnext;
+    tr.bnext = s.bnext;
+    if constexpr (sizeof(R) == 4) {
+      vL = s.vL;
+      vR = s.vR;
     } else {
-      while (b < nb && node_of(__ldg(zq + b), offh) <= k0) ++b;
-      while (b > 0 && node_of(__ldg(zq + b - 1), offh) > k0) --b;
+      vL = sm * __ldg(tv + tr.bnext).x;
+      vR = sm * __ldg(tv + min(tr.bnext + 1, nb)).x;
     }
-    tr.bnext = b;
+  } else {
+    const long long offh = I.dq * (2 * n0 + 1);
+    const long long off0 = offh - ((long long)k0 << 32);
+    tr.bnext = count_at_or_left(zq, nb, offh, k0);
+    tr.dprev = track_d(zq, tr.bnext - 1, nb, off0);
+    tr.dnext = track_d(zq, tr.bnext, nb, off0);
+    vL = sm * __ldg(tv + tr.bnext).x;               // sm se of the layers around the boundary
+    vR = sm * __ldg(tv + min(tr.bnext + 1, nb)).x;
   }
-  tr.dprev = track_d(zq, tr.bnext - 1, nb, off0);
-  tr.dnext = track_d(zq, tr.bnext, nb, off0);
-  R vL = __ldg(tv + tr.bnext).x;
-  R vR = __ldg(tv + min(tr.bnext + 1, nb)).x;
+  __syncwarp();   // every lane has read its tile data: the buffers may be refilled
 
-  unsigned smask = 0, pmask = 0;
-  if (A.src_amp) {
-    for (int q = 0; q < I.nsrc && q < 32; ++q) {
-      const int node = A.srcs[I.src0 + q].node;
-      if (node >= base && node < base + 32 * C) smask |= 1u << q;
-    }
-  }
-  if (A.record) {
-    for (int q = 0; q < I.nprb && q < 32; ++q) {
-      const int node = A.prbs[I.prb0 + q].node;
-      if (node >= x0 && node < x0 + W && node < I.nz) pmask |= 1u << q;
-    }
-  }
+  const unsigned smask = A.src_amp ? ft.smask : 0u;
+  const unsigned pmask = A.record ? ft.pmask : 0u;
 
   for (int s = 0; s < A.nsteps; ++s) {
     // ---- material at level n-1/2 for this lane's cells: c >= c1 lies beyond the next boundary
     const int c1 = (int)((tr.dnext + 0xFFFFFFFFLL) >> 32);
-#pragma unroll
-    for (int c = 0; c < C; ++c) P[c] = (c >= c1 ? vR : vL) * D[c];
+    const R v = c1 <= 0 ? vR : vL;       // exact for the whole run unless 0 < c1 < C
 
-    // ---- B^n
+    // ---- B^n with P_c = v D_c (P of cell 0 is exact in every lane)
     {
-      const R pr = __shfl_down_sync(FULL, P[0], 1);
+      const R pr = __shfl_down_sync(FULL, v * D[0], 1);
       if (POS) {
         const R bl1 = __shfl_up_sync(FULL, B[C - 1], 1);
         const R bl2 = __shfl_up_sync(FULL, B[C - 2], 1);
+        R pn = pr;
 #pragma unroll
         for (int c = C - 1; c >= 0; --c) {
           const R b1 = c >= 1 ? B[c - 1] : bl1;
           const R b2 = c >= 2 ? B[c - 2] : (c == 1 ? bl1 : bl2);
-          const R pn = c + 1 < C ? P[c + 1] : pr;
-          B[c] = bB0 * B[c] + (cc * b1 + (-cb * b2 + (P[c] - pn)));
+          const R pc = v * D[c];
+          B[c] = bB0 * B[c] + (cc * b1 + (-cb * b2 + (pc - pn)));
+          pn = pc;
         }
       } else {
         const R br1 = __shfl_down_sync(FULL, B[0], 1);
         const R br2 = __shfl_down_sync(FULL, B[1], 1);
+        R pc = v * D[0];
 #pragma unroll
         for (int c = 0; c < C; ++c) {
           const R b1 = c + 1 < C ? B[c + 1] : br1;
           const R b2 = c + 2 < C ? B[c + 2] : (c + 2 == C ? br1 : br2);
-          const R pn = c + 1 < C ? P[c + 1] : pr;
-          B[c] = bB0 * B[c] + (cc * b1 + (cb * b2 + (P[c] - pn)));
+          const R pn = c + 1 < C ? v * D[c + 1] : pr;
+          B[c] = bB0 * B[c] + (cc * b1 + (cb * b2 + (pc - pn)));
+          pc = pn;
+        }
+      }
+      // lanes whose run holds a boundary: cells c >= c1 take vR, so B_c gains
+      // q_c - q_{c+1} with q_c = (vR - vL) D_c for c >= c1, else 0
+      const bool inside = c1 > 0 && c1 < C;
+      if (__any_sync(FULL, inside)) {
+        const R dv = inside ? vR - vL : (R)0;
+        R qn = 0;
+#pragma unroll
+        for (int c = C - 1; c >= 0; --c) {
+          const R qc = c >= c1 ? dv * D[c] : (R)0;
+          B[c] += qc - qn;
+          qn = qc;
         }
       }
     }
 
-    // ---- D^{n+1/2} (both D neighbours are read at level n-1/2: write a fresh array)
+    // ---- D^{n+1/2}, in place, walking from the downwind end: the term of the
+    // next cell that needs this cell's old D (its downwind neighbour) is formed
+    // before that D is overwritten.
     {
       const R dl = __shfl_up_sync(FULL, D[C - 1], 1);
       const R dr = __shfl_down_sync(FULL, D[0], 1);
       const R bnl = __shfl_up_sync(FULL, B[C - 1], 1);
-      R Dn[C];
+      if (POS) {
+        R part = bD2 * dr + (B[C - 2] - B[C - 1]);
 #pragma unroll
-      for (int c = 0; c < C; ++c) {
-        const R left = c >= 1 ? D[c - 1] : dl;
-        const R right = c + 1 < C ? D[c + 1] : dr;
-        const R du = POS ? left : right;     // upwind neighbour
-        const R dd = POS ? right : left;     // downwind neighbour
-        const R bm = c >= 1 ? B[c - 1] : bnl;
-        Dn[c] = a * D[c] + (bD1 * du + (bD2 * dd + sm * (bm - B[c])));
+        for (int c = C - 1; c >= 0; --c) {
+          R next = 0;
+          if (c >= 1) next = bD2 * D[c] + ((c >= 2 ? B[c - 2] : bnl) - B[c - 1]);
+          const R left = c >= 1 ? D[c - 1] : dl;
+          D[c] = a * D[c] + (bD1 * left + part);
+          part = next;
+        }
+      } else {
+        R part = bD2 * dl + (bnl - B[0]);
+#pragma unroll
+        for (int c = 0; c < C; ++c) {
+          R next = 0;
+          if (c + 1 < C) next = bD2 * D[c] + (B[c] - B[c + 1]);
+          const R right = c + 1 < C ? D[c + 1] : dr;
+          D[c] = a * D[c] + (bD1 * right + part);
+          part = next;
+        }
       }
-#pragma unroll
-      for (int c = 0; c < C; ++c) D[c] = Dn[c];
     }
 
     // ---- soft sources at t_{n+1/2}
@@ -668,23 +708,25 @@ __device__ __forceinline__ void run_tile_fast(const BlockArgs<T>& A, const InstD
       }
     }
 
-    // ---- advance the boundary tracker to level n+1/2
+    // ---- advance the boundary tracker to level n+1/2.  With v >= 0 the d
+    // values only grow, so only the previous boundary can pass k0; with
+    // v < 0 only the next one can.
     tr.dprev += dq2;
     tr.dnext += dq2;
-    if (tr.dprev > 0) {            // the previous boundary moved past k0 (v > 0)
+    if (POS && tr.dprev > 0) {            // the previous boundary moved past k0
       tr.dnext = tr.dprev;
       tr.bnext -= 1;
       const long long offn = I.dq * (2 * (n0 + s + 1) + 1) - ((long long)k0 << 32);
       tr.dprev = track_d(zq, tr.bnext - 1, nb, offn);
-      vL = __ldg(tv + tr.bnext).x;
-      vR = __ldg(tv + min(tr.bnext + 1, nb)).x;
-    } else if (tr.dnext <= 0) {    // the next boundary moved to or behind k0 (v < 0)
+      vL = sm * __ldg(tv + tr.bnext).x;
+      vR = sm * __ldg(tv + min(tr.bnext + 1, nb)).x;
+    } else if (!POS && tr.dnext <= 0) {   // the next boundary moved to or behind k0
       tr.dprev = tr.dnext;
       tr.bnext += 1;
       const long long offn = I.dq * (2 * (n0 + s + 1) + 1) - ((long long)k0 << 32);
       tr.dnext = track_d(zq, tr.bnext, nb, offn);
-      vL = __ldg(tv + tr.bnext).x;
-      vR = __ldg(tv + min(tr.bnext + 1, nb)).x;
+      vL = sm * __ldg(tv + tr.bnext).x;
+      vR = sm * __ldg(tv + min(tr.bnext + 1, nb)).x;
     }
 
     // ---- probes: E = D / eps at level n+1/2
@@ -701,7 +743,20 @@ __device__ __forceinline__ void run_tile_fast(const BlockArgs<T>& A, const InstD
     }
   }
 
-  if (A.hint) A.hint[(long long)t * 32 + lane] = tr.bnext;
+  if (A.track) {
+    TrackLane o;
+    o.dprev = tr.dprev;
+    o.dnext = tr.dnext;
+    o.vL = (float)vL;
+    o.vR = (float)vR;
+    o.bnext = tr.bnext;
+    o.pad = 0;
+    A.track[t].lane[lane] = o;
+    if (lane == 0) A.track[t].n = n0 + A.nsteps;
+  }
+  const R inv_sm = (R)1 / sm;
+#pragma unroll
+  for (int c = 0; c < C; ++c) B[c] *= inv_sm;      // back to B
   const int hi = min(x0 + W, I.nz_pad);
   store_cells<T, R, C>(A.Bout + I.off, k0, x0, hi, B);
   store_cells<T, R, C>(A.Dout + I.off, k0, x0, hi, D);
@@ -737,18 +792,26 @@ __global__ void __launch_bounds__(128) block_kernel(const BlockArgs<T> A) {
 }
 
 // Interior tiles of moving-perturbation instances with uniform mu and wide
-// (or no) layers; the host sorts such tiles into their own list.
+// (or no) layers; the host sorts such tiles into their own list.  Each warp
+// walks its tiles with two shared-memory buffers: while it steps one tile,
+// bulk copies bring the next tile's cells, its instance record, its tile
+// record and its saved tracker state into the other buffer.
 template <int C, int TB, typename T, int MB>
 __global__ void __launch_bounds__(128, MB) fast_kernel(const BlockArgs<T> A) {
   constexpr int WPB = 4;                    // warps per block (blockDim.x == 128)
   constexpr int CELLS = 32 * C;
   constexpr unsigned BYTES = CELLS * sizeof(T);
   __shared__ __align__(128) T sbuf[WPB][2][2][CELLS];      // [warp][buffer][B, D][cell]
+  __shared__ __align__(16) InstDev sinst[WPB][2];
+  __shared__ __align__(16) FastTile sft[WPB][2];
+  __shared__ __align__(16) TrackTile strk[WPB][2];
   __shared__ __align__(8) unsigned long long sbar[WPB][2];
   const int wib = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int gw = blockIdx.x * WPB + wib;
   const int nw = gridDim.x * WPB;
   const long long n0 = *A.n_done + A.s0;
+  const unsigned tx = 2 * BYTES + (unsigned)sizeof(InstDev) + (unsigned)sizeof(FastTile) +
+                      (A.track ? (unsigned)sizeof(TrackTile) : 0u);
   if (lane == 0) {
     mbar_init(&sbar[wib][0], 1);
     mbar_init(&sbar[wib][1], 1);
@@ -756,26 +819,38 @@ __global__ void __launch_bounds__(128, MB) fast_kernel(const BlockArgs<T> A) {
   }
   __syncwarp();
 
-  // lane 0 starts the bulk copies of tile t's input cells into buffer b
+  // lane 0: input offset and instance of the tile prefetched next, read one
+  // tile ahead so that the read is done by the time the copies start
+  long long fe = 0;
+  int fi = 0;
+  auto fetch_record = [&](int t) {
+    if (lane == 0 && t < A.n_tiles) {
+      fe = A.ftiles[t].e;
+      fi = A.ftiles[t].inst;
+    }
+  };
+  // lane 0 starts the bulk copies of tile t into buffer b
   auto prefetch = [&](int t, int b) {
     if (lane == 0) {
-      const int2 tl = A.tiles[t];
-      const long long off = A.inst[tl.x].off;
-      const int pos = A.inst[tl.x].flags & F_POS;
-      const long long e = off + tl.y - (pos ? 3 * TB : TB);
       fence_proxy_async();
-      mbar_expect_tx(&sbar[wib][b], 2 * BYTES);
-      bulk_g2s(&sbuf[wib][b][0][0], A.Bin + e, BYTES, &sbar[wib][b]);
-      bulk_g2s(&sbuf[wib][b][1][0], A.Din + e, BYTES, &sbar[wib][b]);
+      mbar_expect_tx(&sbar[wib][b], tx);
+      bulk_g2s(&sbuf[wib][b][0][0], A.Bin + fe, BYTES, &sbar[wib][b]);
+      bulk_g2s(&sbuf[wib][b][1][0], A.Din + fe, BYTES, &sbar[wib][b]);
+      bulk_g2s(&sinst[wib][b], A.inst + fi, sizeof(InstDev), &sbar[wib][b]);
+      bulk_g2s(&sft[wib][b], A.ftiles + t, sizeof(FastTile), &sbar[wib][b]);
+      if (A.track) bulk_g2s(&strk[wib][b], A.track + t, sizeof(TrackTile), &sbar[wib][b]);
     }
   };
 
   unsigned phase[2] = {0u, 0u};
   int t = gw, b = 0;
+  fetch_record(t);
   if (t < A.n_tiles) prefetch(t, 0);
+  fetch_record(t + nw);
   for (; t < A.n_tiles; t += nw, b ^= 1) {
     const int tn = t + nw;
     if (tn < A.n_tiles) prefetch(tn, b ^ 1);
+    fetch_record(tn + nw);
     const bool ok = __all_sync(FULL, mbar_wait_bounded(&sbar[wib][b], phase[b]));
     if (!ok) {
       // give up: report, wait (bounded) for this warp's copies still in flight, leave
@@ -785,12 +860,13 @@ __global__ void __launch_bounds__(128, MB) fast_kernel(const BlockArgs<T> A) {
       return;
     }
     phase[b] ^= 1u;
-    const int2 tl = A.tiles[t];
-    const InstDev I = A.inst[tl.x];
+    const InstDev I = sinst[wib][b];
+    const FastTile ft = sft[wib][b];
     const T* sB = &sbuf[wib][b][0][0];
     const T* sD = &sbuf[wib][b][1][0];
-    if (I.flags & F_POS) run_tile_fast<C, TB, true>(A, I, tl.y, tile_width(C, TB, true), n0, sB, sD, t);
-    else run_tile_fast<C, TB, false>(A, I, tl.y, tile_width(C, TB, false), n0, sB, sD, t);
+    const TrackTile* sT = A.track ? &strk[wib][b] : nullptr;
+    if (I.flags & F_POS) run_tile_fast<C, TB, true>(A, I, ft, n0, sB, sD, sT, t);
+    else run_tile_fast<C, TB, false>(A, I, ft, n0, sB, sD, sT, t);
   }
 }
 
@@ -807,8 +883,14 @@ int launch_block_shape(int variant, const void* args, int grid, int block, cudaS
 
 template <int C, int TB, typename T, bool KAHAN = false, int MB = 4>
 int occupancy_block_shape(int variant, int block, int* nb) {
-  if (variant == 2 && !KAHAN)
+  if (variant == 2 && !KAHAN) {
+    // MB blocks of the fast kernel need MB x its static shared memory: ask for the largest carveout
+    const cudaError_t e = cudaFuncSetAttribute(fast_kernel<C, TB, T, MB>,
+                                               cudaFuncAttributePreferredSharedMemoryCarveout,
+                                               (int)cudaSharedmemCarveoutMaxShared);
+    if (e != cudaSuccess) return (int)e;
     return (int)cudaOccupancyMaxActiveBlocksPerMultiprocessor(nb, fast_kernel<C, TB, T, MB>, block, 0);
+  }
   if (variant == 1)
     return (int)cudaOccupancyMaxActiveBlocksPerMultiprocessor(nb, block_kernel<C, TB, true, T, KAHAN>,
                                                               block, 0);

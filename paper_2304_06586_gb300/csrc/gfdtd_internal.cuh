@@ -36,7 +36,11 @@ struct InstDev {
   double inv_S;
   double beta;
   double cb;         // S beta / 2: coupling in the Table 1 averages (moving perturbation)
+  float a32, c32, cb32;   // a, c, cb rounded to FP32 (the FP32-arithmetic kernels read these)
+  float sm32;              // S / mu of layer 0 (half nodes) in FP32: the uniform value when F_MU_CONST
+  int pad0, pad1;
 };
+static_assert(sizeof(InstDev) % 16 == 0, "InstDev is copied by TMA in 16-byte units");
 
 // Profile tables (concatenated over instances).
 //   zq[tab + i]   : boundary (LAYERS, i < n-1) or knot (LINEAR, i < n) in 2^-32 cell
@@ -75,6 +79,34 @@ struct PrbDev {
   int bin0;          // first bin in the omega / accumulator arrays
 };
 
+// A tile of the fast kernel: where its input window starts in the field
+// arrays and which sources and probes of its instance it holds (host-built).
+struct FastTile {
+  long long e;       // element offset of the first input cell, off + x0 - (upwind cone)
+  int inst;          // instance
+  int x0;            // first output cell
+  unsigned smask;    // bit q: source src0 + q has its node in the tile's input window
+  unsigned pmask;    // bit q: probe prb0 + q has its node among the tile's output cells
+  int pad0, pad1;
+};
+static_assert(sizeof(FastTile) == 32, "FastTile is copied by TMA in 16-byte units");
+
+// Boundary tracker of one lane of a fast tile at the end of a launch.
+struct TrackLane {
+  long long dprev, dnext;    // zq + dq h - k0 2^32 of the boundaries around the lane's first cell
+  float vL, vR;              // sm se of the layers on both sides of the next boundary (FP32 kernels)
+  int bnext;                 // index of the next boundary
+  int pad;
+};
+// The tracker state of a fast tile; n = the step count the state belongs to
+// (-1: none).  Written at the end of each recording launch, read by the next.
+struct TrackTile {
+  long long n;
+  long long pad;
+  TrackLane lane[32];
+};
+static_assert(sizeof(TrackTile) % 16 == 0, "TrackTile is copied by TMA in 16-byte units");
+
 // Arguments of one time-block launch of the batched kernel.
 template <typename T>
 struct BlockArgs {
@@ -100,8 +132,8 @@ struct BlockArgs {
   int nsteps;                 // steps in this launch (<= time block)
   int record;                 // nonzero: write probe samples
   int* err;                   // device status word: bit 0 = a bounded wait gave up
-  int* hint;                  // fast tiles: per tile and lane, the lane's next layer boundary
-                              // at the end of the last launch (-1: unknown); NULL: not kept
+  const FastTile* ftiles;     // fast kernel: its tiles (n_tiles records, same order as `tiles`)
+  TrackTile* track;           // fast kernel: tracker state per tile, kept between launches; NULL: not kept
 };
 
 // Arguments of the plain kernel (one instance, one step).

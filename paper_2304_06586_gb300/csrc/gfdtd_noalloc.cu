@@ -36,7 +36,8 @@ constexpr size_t kOffTabH = kOffTabE + align256(sizeof(double2) * kMaxValues);
 constexpr size_t kOffTabE32 = kOffTabH + align256(sizeof(double2) * kMaxValues);
 constexpr size_t kOffTabH32 = kOffTabE32 + align256(sizeof(float2) * kMaxValues);
 constexpr size_t kOffTiles = kOffTabH32 + align256(sizeof(float2) * kMaxValues);
-constexpr size_t kOffInst = kOffTiles + align256(3 * sizeof(int2) * kMaxTiles);
+constexpr size_t kOffFast = kOffTiles + align256(3 * sizeof(int2) * kMaxTiles);
+constexpr size_t kOffInst = kOffFast + align256(sizeof(FastTile) * kMaxTiles);
 constexpr size_t kOffCounter = kOffInst + align256(sizeof(InstDev));
 constexpr size_t kScratchBytes = kOffCounter + 256;
 
@@ -95,6 +96,9 @@ extern "C" gfdtd_status gfdtd_step_noalloc(int64_t nz, double S, gfdtd_kind kind
   I.inv_S = 1.0 / S;
   I.beta = beta;
   I.cb = 0.5 * S * beta;
+  I.a32 = (float)I.a;
+  I.c32 = (float)I.c;
+  I.cb32 = (float)I.cb;
   I.minw = 0;
   int flags = (beta >= 0.0 ? F_POS : 0) | (kind == GFDTD_MATTER ? F_MATTER : 0);
   std::vector<long long> zq(n, 0);
@@ -129,12 +133,14 @@ extern "C" gfdtd_status gfdtd_step_noalloc(int64_t nz, double S, gfdtd_kind kind
     if (mconst) flags |= F_MU_CONST;
   }
   I.flags = flags;
+  I.sm32 = interp == GFDTD_LINEAR ? 0.0f : (float)tH[0].x;
   for (int k = 0; k < n; ++k) {
     tE32[k] = make_float2((float)tE[k].x, (float)tE[k].y);
     tH32[k] = make_float2((float)tH[k].x, (float)tH[k].y);
   }
   // tiles by kernel variant, as the context path lists them
   std::vector<int2> tiles[3];
+  std::vector<FastTile> fast;          // records of tiles[2] (this call has no sources or probes)
   {
     const bool pos = (flags & F_POS) != 0;
     const int W = 32 * kC - (pos ? 4 * kTB : 3 * kTB);
@@ -144,6 +150,13 @@ extern "C" gfdtd_status gfdtd_step_noalloc(int64_t nz, double S, gfdtd_kind kind
       const bool edge = b0 < 0 || b0 + 32LL * kC > nz;
       const int v = (flags & F_MATTER) ? 1 : (fast_eligible(I, kC) && !edge ? 2 : 0);
       tiles[v].push_back(make_int2(0, (int)x0));
+      if (v == 2) {
+        FastTile f{};
+        f.e = b0;
+        f.inst = 0;
+        f.x0 = (int)x0;
+        fast.push_back(f);
+      }
     }
   }
 
@@ -162,6 +175,9 @@ extern "C" gfdtd_status gfdtd_step_noalloc(int64_t nz, double S, gfdtd_kind kind
     if (!tiles[v].empty())
       NA_CK(cudaMemcpyAsync(base + kOffTiles + v * sizeof(int2) * kMaxTiles, tiles[v].data(),
                             sizeof(int2) * tiles[v].size(), cudaMemcpyHostToDevice, st));
+  if (!fast.empty())
+    NA_CK(cudaMemcpyAsync(base + kOffFast, fast.data(), sizeof(FastTile) * fast.size(),
+                          cudaMemcpyHostToDevice, st));
   NA_CK(cudaMemcpyAsync(base + kOffInst, &I, sizeof(InstDev), cudaMemcpyHostToDevice, st));
   long long counter[2] = {n_done, 0};                 // steps done; status word
   NA_CK(cudaMemcpyAsync(base + kOffCounter, counter, sizeof(counter), cudaMemcpyHostToDevice, st));
@@ -191,6 +207,7 @@ extern "C" gfdtd_status gfdtd_step_noalloc(int64_t nz, double S, gfdtd_kind kind
       a.s0 = (int)s0;
       a.nsteps = (int)std::min<long long>(kTB, n_steps - s0);
       a.record = 0;
+      if (v == 2) a.ftiles = reinterpret_cast<const FastTile*>(base + kOffFast);
       const int grid = std::max(1, std::min(num_sms * kMB, (a.n_tiles + 3) / 4));
       if (block_launch(GFDTD_F32, v, kC, kTB, kMB, &a, grid, 128, st) != 0) return GFDTD_E_CUDA;
     }
