@@ -548,6 +548,69 @@ __device__ __forceinline__ long long track_d(const long long* __restrict__ zq, i
   return __ldg(zq + b) + off;
 }
 
+// B^n of a fast tile with P_c = v D_c (level n-1/2) for every cell of the
+// lane; P of the next lane's cell 0 comes by shuffle.
+template <int C, bool POS, typename R>
+__device__ __forceinline__ void fast_b_update(R (&B)[C], const R (&D)[C], R v, R bB0, R cc, R cb) {
+  const R pr = __shfl_down_sync(FULL, v * D[0], 1);
+  if (POS) {
+    const R bl1 = __shfl_up_sync(FULL, B[C - 1], 1);
+    const R bl2 = __shfl_up_sync(FULL, B[C - 2], 1);
+    R pn = pr;
+#pragma unroll
+    for (int c = C - 1; c >= 0; --c) {
+      const R b1 = c >= 1 ? B[c - 1] : bl1;
+      const R b2 = c >= 2 ? B[c - 2] : (c == 1 ? bl1 : bl2);
+      const R pc = v * D[c];
+      B[c] = bB0 * B[c] + (cc * b1 + (-cb * b2 + (pc - pn)));
+      pn = pc;
+    }
+  } else {
+    const R br1 = __shfl_down_sync(FULL, B[0], 1);
+    const R br2 = __shfl_down_sync(FULL, B[1], 1);
+    R pc = v * D[0];
+#pragma unroll
+    for (int c = 0; c < C; ++c) {
+      const R b1 = c + 1 < C ? B[c + 1] : br1;
+      const R b2 = c + 2 < C ? B[c + 2] : (c + 2 == C ? br1 : br2);
+      const R pn = c + 1 < C ? v * D[c + 1] : pr;
+      B[c] = bB0 * B[c] + (cc * b1 + (cb * b2 + (pc - pn)));
+      pc = pn;
+    }
+  }
+}
+
+// D^{n+1/2} of a fast tile, in place, walking from the downwind end: the term
+// of the next cell that needs this cell's old D (its downwind neighbour) is
+// formed before that D is overwritten.  B is (S/mu) B^n.
+template <int C, bool POS, typename R>
+__device__ __forceinline__ void fast_d_update(const R (&B)[C], R (&D)[C], R a, R bD1, R bD2) {
+  const R dl = __shfl_up_sync(FULL, D[C - 1], 1);
+  const R dr = __shfl_down_sync(FULL, D[0], 1);
+  const R bnl = __shfl_up_sync(FULL, B[C - 1], 1);
+  if (POS) {
+    R part = bD2 * dr + (B[C - 2] - B[C - 1]);
+#pragma unroll
+    for (int c = C - 1; c >= 0; --c) {
+      R next = 0;
+      if (c >= 1) next = bD2 * D[c] + ((c >= 2 ? B[c - 2] : bnl) - B[c - 1]);
+      const R left = c >= 1 ? D[c - 1] : dl;
+      D[c] = a * D[c] + (bD1 * left + part);
+      part = next;
+    }
+  } else {
+    R part = bD2 * dl + (bnl - B[0]);
+#pragma unroll
+    for (int c = 0; c < C; ++c) {
+      R next = 0;
+      if (c + 1 < C) next = bD2 * D[c] + (B[c] - B[c + 1]);
+      const R right = c + 1 < C ? D[c + 1] : dr;
+      D[c] = a * D[c] + (bD1 * right + part);
+      part = next;
+    }
+  }
+}
+
 // sB, sD: the tile's 32 C cells of B and D, and sT: the tracker state saved
 // for the tile by the previous launch (NULL: none kept), all in shared memory.
 template <int C, int TB, bool POS, typename T>
@@ -618,41 +681,38 @@ __device__ __forceinline__ void run_tile_fast(const BlockArgs<T>& A, const InstD
   const unsigned smask = A.src_amp ? ft.smask : 0u;
   const unsigned pmask = A.record ? ft.pmask : 0u;
 
+  // A quiet tile has no source or probe, and in no lane does a boundary pass
+  // the lane's first cell or lie inside its run during this launch: every lane
+  // then keeps one multiplier and only the stencil arithmetic remains.
+  bool quiet;
+  {
+    const long long span = (long long)(A.nsteps - 1) * dq2;   // dnext moves by this over the launch
+    const int c1a = (int)((tr.dnext + 0xFFFFFFFFLL) >> 32);          // first step
+    const int c1b = (int)((tr.dnext + span + 0xFFFFFFFFLL) >> 32);   // last step
+    const bool no_event = POS ? tr.dprev + span + dq2 <= 0 : tr.dnext + span + dq2 > 0;
+    const bool one_side = POS ? (c1a >= C || c1b <= 0) : (c1a <= 0 || c1b >= C);
+    quiet = __all_sync(FULL, (smask | pmask) == 0u && no_event && one_side);
+  }
+  if (quiet) {
+    const int c1 = (int)((tr.dnext + 0xFFFFFFFFLL) >> 32);
+    const R v = c1 <= 0 ? vR : vL;
+    for (int s = 0; s < A.nsteps; ++s) {
+      fast_b_update<C, POS>(B, D, v, bB0, cc, cb);
+      fast_d_update<C, POS>(B, D, a, bD1, bD2);
+    }
+    tr.dprev += (long long)A.nsteps * dq2;
+    tr.dnext += (long long)A.nsteps * dq2;
+  } else {
   for (int s = 0; s < A.nsteps; ++s) {
     // ---- material at level n-1/2 for this lane's cells: c >= c1 lies beyond the next boundary
     const int c1 = (int)((tr.dnext + 0xFFFFFFFFLL) >> 32);
     const R v = c1 <= 0 ? vR : vL;       // exact for the whole run unless 0 < c1 < C
 
     // ---- B^n with P_c = v D_c (P of cell 0 is exact in every lane)
+    fast_b_update<C, POS>(B, D, v, bB0, cc, cb);
+    // lanes whose run holds a boundary: cells c >= c1 take vR, so B_c gains
+    // q_c - q_{c+1} with q_c = (vR - vL) D_c for c >= c1, else 0
     {
-      const R pr = __shfl_down_sync(FULL, v * D[0], 1);
-      if (POS) {
-        const R bl1 = __shfl_up_sync(FULL, B[C - 1], 1);
-        const R bl2 = __shfl_up_sync(FULL, B[C - 2], 1);
-        R pn = pr;
-#pragma unroll
-        for (int c = C - 1; c >= 0; --c) {
-          const R b1 = c >= 1 ? B[c - 1] : bl1;
-          const R b2 = c >= 2 ? B[c - 2] : (c == 1 ? bl1 : bl2);
-          const R pc = v * D[c];
-          B[c] = bB0 * B[c] + (cc * b1 + (-cb * b2 + (pc - pn)));
-          pn = pc;
-        }
-      } else {
-        const R br1 = __shfl_down_sync(FULL, B[0], 1);
-        const R br2 = __shfl_down_sync(FULL, B[1], 1);
-        R pc = v * D[0];
-#pragma unroll
-        for (int c = 0; c < C; ++c) {
-          const R b1 = c + 1 < C ? B[c + 1] : br1;
-          const R b2 = c + 2 < C ? B[c + 2] : (c + 2 == C ? br1 : br2);
-          const R pn = c + 1 < C ? v * D[c + 1] : pr;
-          B[c] = bB0 * B[c] + (cc * b1 + (cb * b2 + (pc - pn)));
-          pc = pn;
-        }
-      }
-      // lanes whose run holds a boundary: cells c >= c1 take vR, so B_c gains
-      // q_c - q_{c+1} with q_c = (vR - vL) D_c for c >= c1, else 0
       const bool inside = c1 > 0 && c1 < C;
       if (__any_sync(FULL, inside)) {
         const R dv = inside ? vR - vL : (R)0;
@@ -666,35 +726,8 @@ __device__ __forceinline__ void run_tile_fast(const BlockArgs<T>& A, const InstD
       }
     }
 
-    // ---- D^{n+1/2}, in place, walking from the downwind end: the term of the
-    // next cell that needs this cell's old D (its downwind neighbour) is formed
-    // before that D is overwritten.
-    {
-      const R dl = __shfl_up_sync(FULL, D[C - 1], 1);
-      const R dr = __shfl_down_sync(FULL, D[0], 1);
-      const R bnl = __shfl_up_sync(FULL, B[C - 1], 1);
-      if (POS) {
-        R part = bD2 * dr + (B[C - 2] - B[C - 1]);
-#pragma unroll
-        for (int c = C - 1; c >= 0; --c) {
-          R next = 0;
-          if (c >= 1) next = bD2 * D[c] + ((c >= 2 ? B[c - 2] : bnl) - B[c - 1]);
-          const R left = c >= 1 ? D[c - 1] : dl;
-          D[c] = a * D[c] + (bD1 * left + part);
-          part = next;
-        }
-      } else {
-        R part = bD2 * dl + (bnl - B[0]);
-#pragma unroll
-        for (int c = 0; c < C; ++c) {
-          R next = 0;
-          if (c + 1 < C) next = bD2 * D[c] + (B[c] - B[c + 1]);
-          const R right = c + 1 < C ? D[c + 1] : dr;
-          D[c] = a * D[c] + (bD1 * right + part);
-          part = next;
-        }
-      }
-    }
+    // ---- D^{n+1/2}
+    fast_d_update<C, POS>(B, D, a, bD1, bD2);
 
     // ---- soft sources at t_{n+1/2}
     for (unsigned m = smask; m; m &= m - 1) {
@@ -741,6 +774,7 @@ __device__ __forceinline__ void run_tile_fast(const BlockArgs<T>& A, const InstD
             (double)(pick(D, rel % C) * sep * (R)I.inv_S);
       }
     }
+  }
   }
 
   if (A.track) {
