@@ -250,8 +250,8 @@ static gfdtd_status build_tiles(gfdtd_ctx* c, int C, int TB, std::vector<int2> o
   for (int i = 0; i < c->n_inst; ++i) {
     const InstDev& d = c->h_inst[i];
     const bool pos = (d.flags & F_POS) != 0;
-    const int W = 32 * C - (pos ? 4 * TB : 3 * TB);
-    const int L = pos ? 3 * TB : TB;
+    const int W = tile_width(C, TB, pos, 16 / c->eb);
+    const int L = tile_margin(TB, pos, 16 / c->eb);
     const bool matter = (d.flags & F_MATTER) != 0;
     const bool fast_ok = fast_eligible(d, C) && c->prec != GFDTD_F32_KAHAN;
     for (long long x0 = 0; x0 < c->nz[i]; x0 += W) {

@@ -272,7 +272,7 @@ __device__ __forceinline__ void run_tile(const BlockArgs<T>& A, const InstDev& I
                                          long long n0) {
   using R = typename Real<T>::type;
   const int lane = threadIdx.x & 31;
-  constexpr int L = POS ? 3 * TB : TB;   // upwind margin of the dependency cone
+  constexpr int L = tile_margin(TB, POS, 16 / sizeof(T));   // x0 - base
   const int base = x0 - L;
   const int k0 = base + lane * C;
   const int nz = I.nz;
@@ -620,8 +620,8 @@ __device__ __forceinline__ void run_tile_fast(const BlockArgs<T>& A, const InstD
   using R = typename Real<T>::type;
   using V2 = typename TabOf<R>::V;
   const int lane = threadIdx.x & 31;
-  constexpr int L = POS ? 3 * TB : TB;               // upwind cone of TB steps
-  constexpr int W = 32 * C - (POS ? 4 * TB : 3 * TB);  // output cells
+  constexpr int L = tile_margin(TB, POS, 16 / sizeof(T));     // x0 - base
+  constexpr int W = tile_width(C, TB, POS, 16 / sizeof(T));   // output cells
   const int x0 = ft.x0;
   const int base = x0 - L;
   const int k0 = base + lane * C;
@@ -796,11 +796,6 @@ __device__ __forceinline__ void run_tile_fast(const BlockArgs<T>& A, const InstD
   store_cells<T, R, C>(A.Dout + I.off, k0, x0, hi, D);
 }
 
-// Tile width (output cells) of a tile shape for one sign of v.
-__host__ __device__ constexpr int tile_width(int C, int TB, bool pos) {
-  return 32 * C - (pos ? 4 * TB : 3 * TB);
-}
-
 template <int C, int TB, bool MATTER, typename T, bool KAHAN = false>
 __global__ void __launch_bounds__(128) block_kernel(const BlockArgs<T> A) {
   const int warps_per_block = blockDim.x >> 5;
@@ -811,14 +806,15 @@ __global__ void __launch_bounds__(128) block_kernel(const BlockArgs<T> A) {
     const int2 tl = A.tiles[t];
     const InstDev I = A.inst[tl.x];
     const int x0 = tl.y;
+    constexpr int V = 16 / sizeof(T);
     if (I.flags & F_POS) {
-      constexpr int W = tile_width(C, TB, true);
-      const int base = x0 - 3 * TB;
+      constexpr int W = tile_width(C, TB, true, V);
+      const int base = x0 - tile_margin(TB, true, V);
       if (base < 0 || base + 32 * C > I.nz) run_tile<C, TB, true, MATTER, true, T, KAHAN>(A, I, x0, W, n0);
       else run_tile<C, TB, true, MATTER, false, T, KAHAN>(A, I, x0, W, n0);
     } else {
-      constexpr int W = tile_width(C, TB, false);
-      const int base = x0 - TB;
+      constexpr int W = tile_width(C, TB, false, V);
+      const int base = x0 - tile_margin(TB, false, V);
       if (base < 0 || base + 32 * C > I.nz) run_tile<C, TB, false, MATTER, true, T, KAHAN>(A, I, x0, W, n0);
       else run_tile<C, TB, false, MATTER, false, T, KAHAN>(A, I, x0, W, n0);
     }

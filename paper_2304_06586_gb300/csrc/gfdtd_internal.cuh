@@ -79,6 +79,20 @@ struct PrbDev {
   int bin0;          // first bin in the omega / accumulator arrays
 };
 
+// Tile geometry of the batched kernels.  A warp holds the window
+// [base, base + 32 C) of an instance and advances it TB steps.  B'_j reads
+// B_{j-2..j} and D_{j..j+1}, and D'_k reads D_{k-1..k+1} and B'_{k-1..k}
+// (v >= 0; mirrored for v < 0), so after TB steps the cells still exact are
+// [base + 2 TB + 1, base + 32 C - TB) for v >= 0 and [base + TB, base + 32 C - 2 TB)
+// for v < 0.  The margin x0 - base and the output width are whole 16-byte
+// vectors of V cells, so every copy of a tile is 16-byte aligned.
+__host__ __device__ constexpr int tile_margin(int TB, bool pos, int V) {
+  return ((pos ? 2 * TB + 1 : TB) + V - 1) / V * V;
+}
+__host__ __device__ constexpr int tile_width(int C, int TB, bool pos, int V) {
+  return (32 * C - tile_margin(TB, pos, V) - (pos ? TB : 2 * TB)) / V * V;
+}
+
 // A tile of the fast kernel: where its input window starts in the field
 // arrays and which sources and probes of its instance it holds (host-built).
 struct FastTile {

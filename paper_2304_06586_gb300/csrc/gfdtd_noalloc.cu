@@ -24,7 +24,7 @@ namespace {
 constexpr int kMaxCells = 1 << 18;                 // largest nz accepted
 constexpr int kMaxValues = 1024;                   // largest number of profile values
 constexpr int kC = 16, kTB = 16, kMB = 4;          // tile shape of the kernels used
-constexpr int kMaxTiles = kMaxCells / (32 * kC - 4 * kTB) + 2;
+constexpr int kMaxTiles = kMaxCells / tile_width(kC, kTB, true, 4) + 2;   // the narrower sign
 
 // Byte layout of the scratch array (each region 256-byte aligned).
 constexpr size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
@@ -143,8 +143,8 @@ extern "C" gfdtd_status gfdtd_step_noalloc(int64_t nz, double S, gfdtd_kind kind
   std::vector<FastTile> fast;          // records of tiles[2] (this call has no sources or probes)
   {
     const bool pos = (flags & F_POS) != 0;
-    const int W = 32 * kC - (pos ? 4 * kTB : 3 * kTB);
-    const int L = pos ? 3 * kTB : kTB;
+    const int W = tile_width(kC, kTB, pos, 4);
+    const int L = tile_margin(kTB, pos, 4);
     for (long long x0 = 0; x0 < nz; x0 += W) {
       const long long b0 = x0 - L;
       const bool edge = b0 < 0 || b0 + 32LL * kC > nz;

@@ -17,7 +17,7 @@ from paper_2304_06586_gb300 import workloads as w
 pytestmark = pytest.mark.gpu
 
 TOL32 = 1e-4
-SHAPES = [(16, 8), (16, 16), (16, 32), (8, 16), (16, 16, 5)]
+SHAPES = [(16, 8), (16, 16), (16, 24), (16, 32), (8, 16), (16, 16, 5)]
 
 
 @pytest.fixture(scope="module", autouse=True)
