@@ -32,6 +32,61 @@ FLOPS_PER_CELL_UPDATE = 20        # FP32 operations of one B and D update (E*, B
 SM_COUNT, FP32_LANES_PER_SM, SM_MAX_MHZ = 152, 128, 2070.0
 
 
+KERNEL_SOURCES = ("gfdtd_block.cuh", "gfdtd_internal.cuh", "gfdtd_block_f32.cu")
+
+
+def kernel_source_hash():
+    """sha256 over the sources the FP32 fast kernel is compiled from."""
+    import hashlib
+    h = hashlib.sha256()
+    for name in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, "paper_2304_06586_gb300", "csrc", name), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()
+
+
+def measured_traffic():
+    """DRAM bytes per cell-update of the fast kernel from the committed ncu
+    summary, if it was taken on the kernel as it is now (else None)."""
+    path = os.path.join(ROOT, "profiles", "fast_kernel_crystal256x64steps.md")
+    if not os.path.exists(path):
+        return None
+    fields = {}
+    with open(path) as f:
+        for line in f:
+            if ":" in line and line.startswith("- "):
+                k, v = line[2:].split(":", 1)
+                fields[k.strip()] = v.strip().strip("`")
+    try:
+        if fields.get("kernel source sha256") != kernel_source_hash():
+            return None
+        return float(fields["dram bytes per cell-update"])
+    except (KeyError, ValueError):
+        return None
+
+
+def roofline_of(kt):
+    """FP32-pipe roofline of the fast kernel from per-launch CUDA-event times."""
+    fast = kt["fast"]
+    if fast["launches"] == 0:
+        return None
+    launch_ms = fast["ms"] / fast["launches"]
+    cu_per_launch = fast["cell_updates"] / fast["launches"]
+    achieved = FLOPS_PER_CELL_UPDATE * cu_per_launch / (launch_ms / 1e3) / 1e12
+    peak = 2 * FP32_LANES_PER_SM * SM_COUNT * SM_MAX_MHZ * 1e6 / 1e12
+    bpc = measured_traffic()
+    total_ms = sum(v["ms"] for v in kt.values())
+    return {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+            "frac": achieved / peak,
+            "traffic": None if bpc is None else bpc * cu_per_launch,
+            "kernel": "fast_kernel", "launch_ms": launch_ms, "cell_updates_per_launch": cu_per_launch,
+            "share_of_batched_time": fast["ms"] / total_ms if total_ms > 0 else None,
+            "note": "FP32 pipe: %d flops per cell-update (algorithmic), peak = 2 x 128 lanes x 152 SMs x "
+                    "2070 MHz (derived); launch time from CUDA events around each fast_kernel launch; "
+                    "traffic = ncu DRAM bytes per cell-update x cell-updates per launch"
+                    % FLOPS_PER_CELL_UPDATE}
+
+
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -222,17 +277,10 @@ def main():
         cu = cells * T * args.steps
         value = cu * world / (ms / 1e3) / 1e9
 
-        # batched kernel launches per bench step: one per time block per instance kind
-        blocks_per_step = int(np.ceil(T / st["time_block"]))
-        launch_ms = ms / (args.steps * blocks_per_step)           # includes the small per-chunk kernels
-        cu_per_launch = cells * st["time_block"]
-        achieved = FLOPS_PER_CELL_UPDATE * cu_per_launch / (launch_ms / 1e3) / 1e12
-        peak = 2 * FP32_LANES_PER_SM * SM_COUNT * SM_MAX_MHZ * 1e6 / 1e12
-        roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                    "frac": achieved / peak, "traffic": None,
-                    "note": "FP32 pipe: %d flops per cell-update, peak = 2 x 128 lanes x 152 SMs x "
-                            "2070 MHz; launch time = timed region / batched launches"
-                            % FLOPS_PER_CELL_UPDATE}
+        # roofline of the dominant kernel: the same step, each batched launch
+        # bracketed by CUDA events on the simulation's stream
+        kt = sim.profile_kernels(T)
+        roofline = roofline_of(kt)
 
         # end to end through the C ABI with pinned host buffers
         e2e = None

@@ -226,6 +226,23 @@ typedef struct {
 
 gfdtd_status gfdtd_get_stats(const gfdtd_ctx* ctx, gfdtd_stats* out);
 
+/* Measurement hook (no counterpart in the paper).  Advances every instance by
+ * n_steps exactly as gfdtd_step does (same kernels, same results), but
+ * launches them one by one outside CUDA graphs, brackets each batched-kernel
+ * launch with CUDA events on the context's stream and waits for the stream
+ * at the end.  Index 0 of each array is the general moving-perturbation
+ * kernel, 1 the general moving-matter kernel, 2 the fast interior kernel:
+ * launches, their summed device time in ms, and the cell-updates they
+ * produced (exact output cells of their tiles x steps).  out is written on
+ * success only.  Errors as gfdtd_step; E_ARG for a NULL out. */
+typedef struct {
+    int64_t launches[3];
+    double ms[3];
+    int64_t cell_updates[3];
+} gfdtd_kernel_times;
+
+gfdtd_status gfdtd_profile_kernels(gfdtd_ctx* ctx, int64_t n_steps, gfdtd_kernel_times* out);
+
 /* Wait for all work queued on the context's stream; returns E_TIMEOUT (once)
  * if a kernel reported that a bounded wait gave up since the last check.
  * gfdtd_read_fields and gfdtd_read_spectrum report it the same way. */

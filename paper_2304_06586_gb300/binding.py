@@ -37,6 +37,13 @@ class Stats(C.Structure):
                 ("kernel_launches", C.c_int64), ("cells", C.c_int64)]
 
 
+class KernelTimes(C.Structure):
+    _fields_ = [("launches", C.c_int64 * 3), ("ms", C.c_double * 3), ("cell_updates", C.c_int64 * 3)]
+
+
+KERNEL_VARIANTS = ("general_perturbation", "general_matter", "fast")
+
+
 # every symbol of include/gfdtd.h with its (restype, argtypes)
 SIGNATURES = {
     "gfdtd_set_allocator": (C.c_int, [ALLOC_FN, FREE_FN, C.c_void_p]),
@@ -59,6 +66,7 @@ SIGNATURES = {
     "gfdtd_adjoint": (C.c_int, [C.c_void_p, C.c_int64, C.c_int, C.c_int, C.c_int, _dp, _dp]),
     "gfdtd_set_tuning": (C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_int]),
     "gfdtd_get_stats": (C.c_int, [C.c_void_p, C.POINTER(Stats)]),
+    "gfdtd_profile_kernels": (C.c_int, [C.c_void_p, C.c_int64, C.POINTER(KernelTimes)]),
     "gfdtd_synchronize": (C.c_int, [C.c_void_p]),
     "gfdtd_last_error": (C.c_char_p, [C.c_void_p]),
     "gfdtd_destroy": (None, [C.c_void_p]),
@@ -274,6 +282,14 @@ class Simulation:
         s = Stats()
         self._check(self._L.gfdtd_get_stats(self._h, C.byref(s)), "get_stats")
         return {k: getattr(s, k) for k, _ in Stats._fields_}
+
+    def profile_kernels(self, n):
+        """Advance n steps like step(), timing each batched-kernel launch with
+        CUDA events; per kernel variant: launches, total ms, cell-updates."""
+        t = KernelTimes()
+        self._check(self._L.gfdtd_profile_kernels(self._h, int(n), C.byref(t)), "profile_kernels")
+        return {name: {"launches": t.launches[i], "ms": t.ms[i], "cell_updates": t.cell_updates[i]}
+                for i, name in enumerate(KERNEL_VARIANTS)}
 
     def synchronize(self):
         self._check(self._L.gfdtd_synchronize(self._h), "synchronize")

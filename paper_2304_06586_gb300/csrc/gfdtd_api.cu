@@ -107,6 +107,7 @@ struct gfdtd_ctx {
   int C = 0, TB = 0, MB = 0;            // chosen tile shape (0 = autotune)
   bool tuned = false;
   int n_tiles[3] = {0, 0, 0};           // [general perturbation, general matter, fast interior]
+  long long valid_cells[3] = {0, 0, 0}; // exact output cells of each list's tiles per step
   int grid[3] = {0, 0, 0};
   int num_sms = 0;
 
@@ -247,6 +248,7 @@ static gfdtd_status build_tiles(gfdtd_ctx* c, int C, int TB, std::vector<int2> o
                                 std::vector<FastTile>& fast) {
   std::vector<int2> part[3][2];
   std::vector<FastTile> fpart[2];
+  for (int v = 0; v < 3; ++v) c->valid_cells[v] = 0;
   for (int i = 0; i < c->n_inst; ++i) {
     const InstDev& d = c->h_inst[i];
     const bool pos = (d.flags & F_POS) != 0;
@@ -259,6 +261,7 @@ static gfdtd_status build_tiles(gfdtd_ctx* c, int C, int TB, std::vector<int2> o
       const bool edge = base < 0 || base + 32LL * C > c->nz[i];
       const int v = matter ? 1 : (fast_ok && !edge ? 2 : 0);
       part[v][pos ? 0 : 1].push_back(make_int2(i, (int)x0));
+      c->valid_cells[v] += std::min<long long>(W, c->nz[i] - x0);
       if (v == 2) {
         FastTile f{};
         f.e = d.off + base;
@@ -465,9 +468,9 @@ static Tables tables_of(gfdtd_ctx* c) {
 
 // Enqueue one time-block launch (both kinds) reading buffer `from`.
 static gfdtd_status enqueue_block(gfdtd_ctx* c, cudaStream_t st, int from, int s0, int nsteps,
-                                  bool record, bool sources) {
+                                  bool record, bool sources, int only = -1) {
   for (int k = 0; k < 3; ++k) {
-    if (c->n_tiles[k] == 0) continue;
+    if (c->n_tiles[k] == 0 || (only >= 0 && k != only)) continue;
     // BlockArgs<T> has the same layout for every T (pointers), so fill the float version
     BlockArgs<float> a;
     a.inst = (const InstDev*)c->d_inst.p;
@@ -998,6 +1001,81 @@ gfdtd_status gfdtd_step(gfdtd_ctx* c, int64_t n_steps) {
     n_steps -= ch;
   }
   return GFDTD_OK;
+}
+
+gfdtd_status gfdtd_profile_kernels(gfdtd_ctx* c, int64_t n_steps, gfdtd_kernel_times* out) {
+  if (!c) return GFDTD_E_ARG;
+  if (!out) return fail(c, GFDTD_E_ARG, "out is NULL");
+  if (n_steps < 0) return fail(c, GFDTD_E_ARG, "n_steps < 0");
+  gfdtd_status s = finalize(c);
+  if (s) return s;
+  if (c->C == 0) {
+    s = autotune(c);
+    if (s) return s;
+  }
+  struct Mark { int k; int nsteps; cudaEvent_t e0, e1; };
+  std::vector<Mark> marks;
+  auto release = [&]() {
+    for (Mark& m : marks) { cudaEventDestroy(m.e0); cudaEventDestroy(m.e1); }
+    marks.clear();
+  };
+  gfdtd_kernel_times r;
+  std::memset(&r, 0, sizeof r);
+  while (n_steps > 0 && s == GFDTD_OK) {
+    const int ch = (int)std::min<int64_t>(n_steps, kChunk);
+    if (c->n_src > 0) {
+      if (src_amp_launch((const SrcDev*)c->d_srcs.p, c->n_src, (double*)c->d_amp.p, kChunk, ch,
+                         (const long long*)c->d_ndone.p, c->S, c->stream) != 0) {
+        s = fail(c, GFDTD_E_CUDA, "source amplitude launch failed");
+        break;
+      }
+      ++c->launches;
+    }
+    int b = c->cur, m = 0;
+    for (int s0 = 0; s0 < ch && s == GFDTD_OK; s0 += c->TB) {
+      const int nsteps = std::min(c->TB, ch - s0);
+      for (int k = 0; k < 3 && s == GFDTD_OK; ++k) {
+        if (c->n_tiles[k] == 0) continue;
+        Mark mk{k, nsteps, nullptr, nullptr};
+        if (cudaEventCreate(&mk.e0) != cudaSuccess || cudaEventCreate(&mk.e1) != cudaSuccess) {
+          if (mk.e0) cudaEventDestroy(mk.e0);
+          s = fail(c, GFDTD_E_CUDA, "cudaEventCreate failed");
+          break;
+        }
+        marks.push_back(mk);
+        if (cudaEventRecord(mk.e0, c->stream) != cudaSuccess) { s = fail(c, GFDTD_E_CUDA, "event record failed"); break; }
+        s = enqueue_block(c, c->stream, b, s0, nsteps, true, true, k);
+        if (s) break;
+        if (cudaEventRecord(mk.e1, c->stream) != cudaSuccess) { s = fail(c, GFDTD_E_CUDA, "event record failed"); break; }
+      }
+      b = 1 - b;
+      ++m;
+    }
+    if (s) break;
+    s = enqueue_fold_advance(c, c->stream, ch);
+    if (s) break;
+    if (m & 1) c->cur = 1 - c->cur;
+    c->n_done += ch;
+    n_steps -= ch;
+  }
+  if (s == GFDTD_OK && cudaStreamSynchronize(c->stream) != cudaSuccess)
+    s = fail(c, GFDTD_E_CUDA, "%s", cudaGetErrorString(cudaGetLastError()));
+  if (s == GFDTD_OK) {
+    for (const Mark& mk : marks) {
+      float ms = 0.0f;
+      if (cudaEventElapsedTime(&ms, mk.e0, mk.e1) != cudaSuccess) {
+        s = fail(c, GFDTD_E_CUDA, "cudaEventElapsedTime failed");
+        break;
+      }
+      r.launches[mk.k] += 1;
+      r.ms[mk.k] += ms;
+      r.cell_updates[mk.k] += c->valid_cells[mk.k] * mk.nsteps;
+    }
+  }
+  release();
+  if (s == GFDTD_OK) s = device_status(c);
+  if (s == GFDTD_OK) *out = r;
+  return s;
 }
 
 gfdtd_status gfdtd_step_plain(gfdtd_ctx* c, int64_t n_steps) {

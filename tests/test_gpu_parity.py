@@ -328,3 +328,22 @@ def test_adjoint_matches_finite_differences():
         em[j] -= h
         fd = (L_of(ep) - L_of(em)) / (2 * h)
         assert abs(g[j] - fd) <= 1e-3 * np.abs(g).max(), (j, g[j], fd)
+
+
+def test_profile_kernels_matches_step_and_covers_every_cell():
+    """The measurement entry point runs the same launches as step(): identical
+    fields and spectra, and its per-kernel cell-updates add up to every cell
+    of every instance once per step."""
+    wl = w.config3(n_inst=24, nz_lo=1 << 10, nz_hi=1 << 13, n_steps=0, stable_only=True)
+    a = make_sim(wl, allow_unstable=False, tuning=(16, 16, 5))
+    b = make_sim(wl, allow_unstable=False, tuning=(16, 16, 5))
+    n = 1100                       # more than one chunk, ragged last time block
+    a.step(n)
+    t = b.profile_kernels(n)
+    cells = sum(i.nz for i in wl.instances)
+    assert sum(v["cell_updates"] for v in t.values()) == cells * n
+    assert t["fast"]["launches"] > 0 and t["fast"]["ms"] > 0.0
+    for k, inst in enumerate(wl.instances):
+        for f in (gb.FIELD_B, gb.FIELD_D):
+            assert np.array_equal(a.read_fields(k, f), b.read_fields(k, f))
+    assert a.steps_done() == b.steps_done() == n
