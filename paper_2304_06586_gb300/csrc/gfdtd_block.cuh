@@ -548,11 +548,11 @@ __device__ __forceinline__ long long track_d(const long long* __restrict__ zq, i
   return __ldg(zq + b) + off;
 }
 
-// B^n of a fast tile with P_c = v D_c (level n-1/2) for every cell of the
-// lane; P of the next lane's cell 0 comes by shuffle.
-template <int C, bool POS, typename R>
-__device__ __forceinline__ void fast_b_update(R (&B)[C], const R (&D)[C], R v, R bB0, R cc, R cb) {
-  const R pr = __shfl_down_sync(FULL, v * D[0], 1);
+// B^n of a fast tile with P_c = vc(c) D_c (level n-1/2) for cell c of the
+// lane's run; P of the next lane's cell 0 comes by shuffle.
+template <int C, bool POS, typename R, typename VC>
+__device__ __forceinline__ void fast_b_update_cells(R (&B)[C], const R (&D)[C], VC vc, R bB0, R cc, R cb) {
+  const R pr = __shfl_down_sync(FULL, vc(0) * D[0], 1);
   if (POS) {
     const R bl1 = __shfl_up_sync(FULL, B[C - 1], 1);
     const R bl2 = __shfl_up_sync(FULL, B[C - 2], 1);
@@ -561,23 +561,29 @@ __device__ __forceinline__ void fast_b_update(R (&B)[C], const R (&D)[C], R v, R
     for (int c = C - 1; c >= 0; --c) {
       const R b1 = c >= 1 ? B[c - 1] : bl1;
       const R b2 = c >= 2 ? B[c - 2] : (c == 1 ? bl1 : bl2);
-      const R pc = v * D[c];
+      const R pc = vc(c) * D[c];
       B[c] = bB0 * B[c] + (cc * b1 + (-cb * b2 + (pc - pn)));
       pn = pc;
     }
   } else {
     const R br1 = __shfl_down_sync(FULL, B[0], 1);
     const R br2 = __shfl_down_sync(FULL, B[1], 1);
-    R pc = v * D[0];
+    R pc = vc(0) * D[0];
 #pragma unroll
     for (int c = 0; c < C; ++c) {
       const R b1 = c + 1 < C ? B[c + 1] : br1;
       const R b2 = c + 2 < C ? B[c + 2] : (c + 2 == C ? br1 : br2);
-      const R pn = c + 1 < C ? v * D[c + 1] : pr;
+      const R pn = c + 1 < C ? vc(c + 1) * D[c + 1] : pr;
       B[c] = bB0 * B[c] + (cc * b1 + (cb * b2 + (pc - pn)));
       pc = pn;
     }
   }
+}
+
+// The same with one multiplier v for the whole run.
+template <int C, bool POS, typename R>
+__device__ __forceinline__ void fast_b_update(R (&B)[C], const R (&D)[C], R v, R bB0, R cc, R cb) {
+  fast_b_update_cells<C, POS>(B, D, [v](int) { return v; }, bB0, cc, cb);
 }
 
 // D^{n+1/2} of a fast tile, in place, walking from the downwind end: the term
@@ -613,10 +619,11 @@ __device__ __forceinline__ void fast_d_update(const R (&B)[C], R (&D)[C], R a, R
 
 // sB, sD: the tile's 32 C cells of B and D, and sT: the tracker state saved
 // for the tile by the previous launch (NULL: none kept), all in shared memory.
-template <int C, int TB, bool POS, typename T>
+// refill() is called once every lane has read them: it may overwrite them.
+template <int C, int TB, bool POS, typename T, typename Refill>
 __device__ __forceinline__ void run_tile_fast(const BlockArgs<T>& A, const InstDev& I, const FastTile& ft,
                                               long long n0, const T* sB, const T* sD,
-                                              const TrackTile* sT, int t) {
+                                              const TrackTile* sT, int t, Refill&& refill) {
   using R = typename Real<T>::type;
   using V2 = typename TabOf<R>::V;
   const int lane = threadIdx.x & 31;
@@ -676,7 +683,8 @@ __device__ __forceinline__ void run_tile_fast(const BlockArgs<T>& A, const InstD
     vL = sm * __ldg(tv + tr.bnext).x;               // sm se of the layers around the boundary
     vR = sm * __ldg(tv + min(tr.bnext + 1, nb)).x;
   }
-  __syncwarp();   // every lane has read its tile data: the buffers may be refilled
+  __syncwarp();   // every lane has read its tile data: the buffer may be refilled
+  refill();
 
   const unsigned smask = A.src_amp ? ft.smask : 0u;
   const unsigned pmask = A.record ? ft.pmask : 0u;
@@ -708,23 +716,12 @@ __device__ __forceinline__ void run_tile_fast(const BlockArgs<T>& A, const InstD
     const int c1 = (int)((tr.dnext + 0xFFFFFFFFLL) >> 32);
     const R v = c1 <= 0 ? vR : vL;       // exact for the whole run unless 0 < c1 < C
 
-    // ---- B^n with P_c = v D_c (P of cell 0 is exact in every lane)
-    fast_b_update<C, POS>(B, D, v, bB0, cc, cb);
-    // lanes whose run holds a boundary: cells c >= c1 take vR, so B_c gains
-    // q_c - q_{c+1} with q_c = (vR - vL) D_c for c >= c1, else 0
-    {
-      const bool inside = c1 > 0 && c1 < C;
-      if (__any_sync(FULL, inside)) {
-        const R dv = inside ? vR - vL : (R)0;
-        R qn = 0;
-#pragma unroll
-        for (int c = C - 1; c >= 0; --c) {
-          const R qc = c >= c1 ? dv * D[c] : (R)0;
-          B[c] += qc - qn;
-          qn = qc;
-        }
-      }
-    }
+    // ---- B^n with P_c = v_c D_c: one multiplier per lane unless a lane of the
+    // warp holds a boundary inside its run (cells c >= c1 take vR)
+    if (__any_sync(FULL, c1 > 0 && c1 < C))
+      fast_b_update_cells<C, POS>(B, D, [&](int c) { return c >= c1 ? vR : vL; }, bB0, cc, cb);
+    else
+      fast_b_update<C, POS>(B, D, v, bB0, cc, cb);
 
     // ---- D^{n+1/2}
     fast_d_update<C, POS>(B, D, a, bD1, bD2);
@@ -823,19 +820,20 @@ __global__ void __launch_bounds__(128) block_kernel(const BlockArgs<T> A) {
 
 // Interior tiles of moving-perturbation instances with uniform mu and wide
 // (or no) layers; the host sorts such tiles into their own list.  Each warp
-// walks its tiles with two shared-memory buffers: while it steps one tile,
-// bulk copies bring the next tile's cells, its instance record, its tile
-// record and its saved tracker state into the other buffer.
+// walks its tiles with one shared-memory buffer: as soon as the lanes hold a
+// tile's cells in registers, bulk copies start bringing the next tile's
+// cells, instance record, tile record and saved tracker state into it, and
+// they land while the warp steps the current tile.
 template <int C, int TB, typename T, int MB>
 __global__ void __launch_bounds__(128, MB) fast_kernel(const BlockArgs<T> A) {
   constexpr int WPB = 4;                    // warps per block (blockDim.x == 128)
   constexpr int CELLS = 32 * C;
   constexpr unsigned BYTES = CELLS * sizeof(T);
-  __shared__ __align__(128) T sbuf[WPB][2][2][CELLS];      // [warp][buffer][B, D][cell]
-  __shared__ __align__(16) InstDev sinst[WPB][2];
-  __shared__ __align__(16) FastTile sft[WPB][2];
-  __shared__ __align__(16) TrackTile strk[WPB][2];
-  __shared__ __align__(8) unsigned long long sbar[WPB][2];
+  __shared__ __align__(128) T sbuf[WPB][2][CELLS];      // [warp][B, D][cell]
+  __shared__ __align__(16) InstDev sinst[WPB];
+  __shared__ __align__(16) FastTile sft[WPB];
+  __shared__ __align__(16) TrackTile strk[WPB];
+  __shared__ __align__(8) unsigned long long sbar[WPB];
   const int wib = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int gw = blockIdx.x * WPB + wib;
   const int nw = gridDim.x * WPB;
@@ -843,14 +841,13 @@ __global__ void __launch_bounds__(128, MB) fast_kernel(const BlockArgs<T> A) {
   const unsigned tx = 2 * BYTES + (unsigned)sizeof(InstDev) + (unsigned)sizeof(FastTile) +
                       (A.track ? (unsigned)sizeof(TrackTile) : 0u);
   if (lane == 0) {
-    mbar_init(&sbar[wib][0], 1);
-    mbar_init(&sbar[wib][1], 1);
+    mbar_init(&sbar[wib], 1);
     fence_mbar_init();
   }
   __syncwarp();
 
-  // lane 0: input offset and instance of the tile prefetched next, read one
-  // tile ahead so that the read is done by the time the copies start
+  // lane 0: input offset and instance of the tile to be prefetched next; the
+  // record is read one tile ahead so that it is in registers when needed
   long long fe = 0;
   int fi = 0;
   auto fetch_record = [&](int t) {
@@ -859,44 +856,42 @@ __global__ void __launch_bounds__(128, MB) fast_kernel(const BlockArgs<T> A) {
       fi = A.ftiles[t].inst;
     }
   };
-  // lane 0 starts the bulk copies of tile t into buffer b
-  auto prefetch = [&](int t, int b) {
-    if (lane == 0) {
+  // lane 0 starts the bulk copies of tile t into the warp's buffer
+  auto prefetch = [&](int t) {
+    if (lane == 0 && t < A.n_tiles) {
       fence_proxy_async();
-      mbar_expect_tx(&sbar[wib][b], tx);
-      bulk_g2s(&sbuf[wib][b][0][0], A.Bin + fe, BYTES, &sbar[wib][b]);
-      bulk_g2s(&sbuf[wib][b][1][0], A.Din + fe, BYTES, &sbar[wib][b]);
-      bulk_g2s(&sinst[wib][b], A.inst + fi, sizeof(InstDev), &sbar[wib][b]);
-      bulk_g2s(&sft[wib][b], A.ftiles + t, sizeof(FastTile), &sbar[wib][b]);
-      if (A.track) bulk_g2s(&strk[wib][b], A.track + t, sizeof(TrackTile), &sbar[wib][b]);
+      mbar_expect_tx(&sbar[wib], tx);
+      bulk_g2s(&sbuf[wib][0][0], A.Bin + fe, BYTES, &sbar[wib]);
+      bulk_g2s(&sbuf[wib][1][0], A.Din + fe, BYTES, &sbar[wib]);
+      bulk_g2s(&sinst[wib], A.inst + fi, sizeof(InstDev), &sbar[wib]);
+      bulk_g2s(&sft[wib], A.ftiles + t, sizeof(FastTile), &sbar[wib]);
+      if (A.track) bulk_g2s(&strk[wib], A.track + t, sizeof(TrackTile), &sbar[wib]);
     }
   };
 
-  unsigned phase[2] = {0u, 0u};
-  int t = gw, b = 0;
-  fetch_record(t);
-  if (t < A.n_tiles) prefetch(t, 0);
-  fetch_record(t + nw);
-  for (; t < A.n_tiles; t += nw, b ^= 1) {
+  unsigned phase = 0u;
+  fetch_record(gw);
+  prefetch(gw);
+  fetch_record(gw + nw);
+  for (int t = gw; t < A.n_tiles; t += nw) {
     const int tn = t + nw;
-    if (tn < A.n_tiles) prefetch(tn, b ^ 1);
-    fetch_record(tn + nw);
-    const bool ok = __all_sync(FULL, mbar_wait_bounded(&sbar[wib][b], phase[b]));
+    const bool ok = __all_sync(FULL, mbar_wait_bounded(&sbar[wib], phase));
     if (!ok) {
       // give up: report, wait (bounded) for this warp's copies still in flight, leave
       if (lane == 0) atomicOr(A.err, kErrTimeout);
-      mbar_wait_bounded(&sbar[wib][b], phase[b]);
-      if (tn < A.n_tiles) mbar_wait_bounded(&sbar[wib][b ^ 1], phase[b ^ 1]);
+      mbar_wait_bounded(&sbar[wib], phase);
       return;
     }
-    phase[b] ^= 1u;
-    const InstDev I = sinst[wib][b];
-    const FastTile ft = sft[wib][b];
-    const T* sB = &sbuf[wib][b][0][0];
-    const T* sD = &sbuf[wib][b][1][0];
-    const TrackTile* sT = A.track ? &strk[wib][b] : nullptr;
-    if (I.flags & F_POS) run_tile_fast<C, TB, true>(A, I, ft, n0, sB, sD, sT, t);
-    else run_tile_fast<C, TB, false>(A, I, ft, n0, sB, sD, sT, t);
+    phase ^= 1u;
+    const InstDev I = sinst[wib];
+    const FastTile ft = sft[wib];
+    const TrackTile* sT = A.track ? &strk[wib] : nullptr;
+    auto refill = [&]() {
+      prefetch(tn);
+      fetch_record(tn + nw);
+    };
+    if (I.flags & F_POS) run_tile_fast<C, TB, true>(A, I, ft, n0, sbuf[wib][0], sbuf[wib][1], sT, t, refill);
+    else run_tile_fast<C, TB, false>(A, I, ft, n0, sbuf[wib][0], sbuf[wib][1], sT, t, refill);
   }
 }
 
