@@ -536,8 +536,13 @@ template <> __device__ __forceinline__ double coef<double>(double d, float) { re
 
 struct BoundaryTrack {
   long long dprev, dnext;     // zq_b + dq h - k0 2^32 of the boundaries around k0
+  long long dnext2;           // the boundary after dnext (tracked when a run can hold two)
   int bnext;                  // index of the next boundary (first with d > 0)
 };
+
+// Boundaries a lane's run of C cells may hold in the fast kernel: the wider
+// runs track a second one, so layers need only be wider than C / 2.
+__host__ __device__ constexpr int fast_boundaries_per_run(int C) { return C > 16 ? 2 : 1; }
 
 constexpr long long FAR_AWAY = 1LL << 61;
 
@@ -660,19 +665,30 @@ __device__ __forceinline__ void run_tile_fast(const BlockArgs<T>& A, const InstD
   // boundary tracker at half level h = 2 n0 + 1 (the first E' of this launch):
   // the state the previous launch left for this tile if it ended at n0, else
   // found by binary search.
+  constexpr int NB = fast_boundaries_per_run(C);
   BoundaryTrack tr;
-  R vL, vR;
+  R vL, vM = 0, vR;      // sm se of the layers: k0's, past dnext (NB = 2: up to dnext2), past the last tracked
+  auto load_layers = [&]() {
+    vL = sm * __ldg(tv + tr.bnext).x;
+    if constexpr (NB == 2) {
+      vM = sm * __ldg(tv + min(tr.bnext + 1, nb)).x;
+      vR = sm * __ldg(tv + min(tr.bnext + 2, nb)).x;
+    } else {
+      vR = sm * __ldg(tv + min(tr.bnext + 1, nb)).x;
+    }
+  };
   if (sT && sT->n == n0) {
     const TrackLane& s = sT->lane[lane];
     tr.dprev = s.dprev;
     tr.dnext = s.dnext;
+    tr.dnext2 = s.dnext2;
     tr.bnext = s.bnext;
     if constexpr (sizeof(R) == 4) {
       vL = s.vL;
+      vM = s.vM;
       vR = s.vR;
     } else {
-      vL = sm * __ldg(tv + tr.bnext).x;
-      vR = sm * __ldg(tv + min(tr.bnext + 1, nb)).x;
+      load_layers();
     }
   } else {
     const long long offh = I.dq * (2 * n0 + 1);
@@ -680,8 +696,8 @@ __device__ __forceinline__ void run_tile_fast(const BlockArgs<T>& A, const InstD
     tr.bnext = count_at_or_left(zq, nb, offh, k0);
     tr.dprev = track_d(zq, tr.bnext - 1, nb, off0);
     tr.dnext = track_d(zq, tr.bnext, nb, off0);
-    vL = sm * __ldg(tv + tr.bnext).x;               // sm se of the layers around the boundary
-    vR = sm * __ldg(tv + min(tr.bnext + 1, nb)).x;
+    tr.dnext2 = NB == 2 ? track_d(zq, tr.bnext + 1, nb, off0) : FAR_AWAY;
+    load_layers();
   }
   __syncwarp();   // every lane has read its tile data: the buffer may be refilled
   refill();
@@ -710,6 +726,7 @@ __device__ __forceinline__ void run_tile_fast(const BlockArgs<T>& A, const InstD
     }
     tr.dprev += (long long)A.nsteps * dq2;
     tr.dnext += (long long)A.nsteps * dq2;
+    if constexpr (NB == 2) tr.dnext2 += (long long)A.nsteps * dq2;
   } else {
   for (int s = 0; s < A.nsteps; ++s) {
     // ---- material at level n-1/2 for this lane's cells: c >= c1 lies beyond the next boundary
@@ -718,9 +735,15 @@ __device__ __forceinline__ void run_tile_fast(const BlockArgs<T>& A, const InstD
 
     // ---- B^n with P_c = v_c D_c: one multiplier per lane unless a lane of the
     // warp holds a boundary inside its run (cells c >= c1 take vR)
-    if (__any_sync(FULL, c1 > 0 && c1 < C))
-      fast_b_update_cells<C, POS>(B, D, [&](int c) { return c >= c1 ? vR : vL; }, bB0, cc, cb);
-    else
+    if (__any_sync(FULL, c1 > 0 && c1 < C)) {
+      if constexpr (NB == 2) {
+        const int c2 = (int)((tr.dnext2 + 0xFFFFFFFFLL) >> 32);
+        fast_b_update_cells<C, POS>(B, D, [&](int c) { return c >= c2 ? vR : (c >= c1 ? vM : vL); },
+                                    bB0, cc, cb);
+      } else {
+        fast_b_update_cells<C, POS>(B, D, [&](int c) { return c >= c1 ? vR : vL; }, bB0, cc, cb);
+      }
+    } else
       fast_b_update<C, POS>(B, D, v, bB0, cc, cb);
 
     // ---- D^{n+1/2}
@@ -743,20 +766,25 @@ __device__ __forceinline__ void run_tile_fast(const BlockArgs<T>& A, const InstD
     // v < 0 only the next one can.
     tr.dprev += dq2;
     tr.dnext += dq2;
+    if constexpr (NB == 2) tr.dnext2 += dq2;
     if (POS && tr.dprev > 0) {            // the previous boundary moved past k0
+      if constexpr (NB == 2) tr.dnext2 = tr.dnext;
       tr.dnext = tr.dprev;
       tr.bnext -= 1;
       const long long offn = I.dq * (2 * (n0 + s + 1) + 1) - ((long long)k0 << 32);
       tr.dprev = track_d(zq, tr.bnext - 1, nb, offn);
-      vL = sm * __ldg(tv + tr.bnext).x;
-      vR = sm * __ldg(tv + min(tr.bnext + 1, nb)).x;
+      load_layers();
     } else if (!POS && tr.dnext <= 0) {   // the next boundary moved to or behind k0
       tr.dprev = tr.dnext;
       tr.bnext += 1;
       const long long offn = I.dq * (2 * (n0 + s + 1) + 1) - ((long long)k0 << 32);
-      tr.dnext = track_d(zq, tr.bnext, nb, offn);
-      vL = sm * __ldg(tv + tr.bnext).x;
-      vR = sm * __ldg(tv + min(tr.bnext + 1, nb)).x;
+      if constexpr (NB == 2) {
+        tr.dnext = tr.dnext2;
+        tr.dnext2 = track_d(zq, tr.bnext + 1, nb, offn);
+      } else {
+        tr.dnext = track_d(zq, tr.bnext, nb, offn);
+      }
+      load_layers();
     }
 
     // ---- probes: E = D / eps at level n+1/2
@@ -778,7 +806,9 @@ __device__ __forceinline__ void run_tile_fast(const BlockArgs<T>& A, const InstD
     TrackLane o;
     o.dprev = tr.dprev;
     o.dnext = tr.dnext;
+    o.dnext2 = tr.dnext2;
     o.vL = (float)vL;
+    o.vM = (float)vM;
     o.vR = (float)vR;
     o.bnext = tr.bnext;
     o.pad = 0;
@@ -925,8 +955,10 @@ int occupancy_block_shape(int variant, int block, int* nb) {
 
 // Whether an instance's interior tiles can take the fast path for C cells per lane.
 __host__ __device__ inline bool fast_eligible(const InstDev& I, int C) {
+  // layers wider than C cells (C / 2 when the kernel tracks two boundaries per run)
+  const bool wide = fast_boundaries_per_run(C) == 2 ? 2 * I.minw > C : I.minw > C;
   return !(I.flags & F_MATTER) && (I.flags & F_MU_CONST) && !(I.flags & F_LINEAR) &&
-         ((I.flags & F_EPS_CONST) || I.minw > C);
+         ((I.flags & F_EPS_CONST) || wide);
 }
 
 }  // namespace gfdtd

@@ -108,10 +108,12 @@ static_assert(sizeof(FastTile) == 32, "FastTile is copied by TMA in 16-byte unit
 // Boundary tracker of one lane of a fast tile at the end of a launch.
 struct TrackLane {
   long long dprev, dnext;    // zq + dq h - k0 2^32 of the boundaries around the lane's first cell
-  float vL, vR;              // sm se of the layers on both sides of the next boundary (FP32 kernels)
+  long long dnext2;          // the same of the boundary after dnext (kernels that track two)
+  float vL, vM, vR;          // sm se of the layers before, between and after dnext, dnext2 (FP32 kernels)
   int bnext;                 // index of the next boundary
-  int pad;
+  long long pad;
 };
+static_assert(sizeof(TrackLane) == 48, "TrackLane layout");
 // The tracker state of a fast tile; n = the step count the state belongs to
 // (-1: none).  Written at the end of each recording launch, read by the next.
 struct TrackTile {

@@ -17,7 +17,7 @@ from paper_2304_06586_gb300 import workloads as w
 pytestmark = pytest.mark.gpu
 
 TOL32 = 1e-4
-SHAPES = [(16, 8), (16, 16), (16, 24), (16, 32), (8, 16), (16, 16, 5)]
+SHAPES = [(16, 8), (16, 16), (16, 24), (16, 32), (8, 16), (16, 16, 5), (24, 16), (24, 24)]
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -204,7 +204,7 @@ def test_precision_tiers(prec, tol):
     print("precision tier", prec, "worst relative L2", worst)
 
 
-@pytest.mark.parametrize("tuning", [None, (16, 16, 5)])
+@pytest.mark.parametrize("tuning", [None, (16, 16, 5), (24, 24, 4)])
 def test_crystal_small_matches_oracle(tuning):
     """Config-3 shape at reduced size (stable velocities), from rest, sources and probes."""
     wl = w.config3(n_inst=48, nz_lo=1 << 10, nz_hi=1 << 13, n_steps=600, stable_only=True)
@@ -347,3 +347,29 @@ def test_profile_kernels_matches_step_and_covers_every_cell():
         for f in (gb.FIELD_B, gb.FIELD_D):
             assert np.array_equal(a.read_fields(k, f), b.read_fields(k, f))
     assert a.steps_done() == b.steps_done() == n
+
+
+@pytest.mark.parametrize("tuning", [(24, 24, 4), (24, 16, 4)])
+def test_two_boundaries_per_lane_run(tuning):
+    """Layers of 14-30 cells under 24-cell lane runs: runs hold two boundaries
+    at a time and boundaries pass lane starts in both directions, with sources
+    and probes inside the layered region."""
+    rng = np.random.default_rng(11)
+    out = []
+    for v in (0.45, -0.45, 0.2, -0.2, 0.05, -0.33):
+        nz = 6000
+        widths = rng.integers(14, 31, size=60)
+        z = 1500.0 + np.cumsum(widths) + rng.uniform(0, 1)
+        eps = np.where(np.arange(len(z) + 1) % 2 == 0, 1.0, rng.uniform(1.5, 3.0))
+        out.append(w.InstanceSpec(nz=nz, beta=v, z=z, eps=eps, mu=np.ones(len(eps)),
+                                  sources=[w.gaussian_source(1700, 20.0, 3.0)],
+                                  probes=[(2000, np.linspace(0.1, 0.5, 5)), (5800, np.linspace(0.2, 0.4, 3))]))
+    wl = w.Workload("two_boundaries", 0.5, 700, out)
+    sim = make_sim(wl, allow_unstable=False, tuning=tuning)
+    st = sim.stats()
+    assert (st["cells_per_lane"], st["time_block"]) == tuning[:2]
+    orcs = make_oracle(wl)
+    sim.step(wl.n_steps)
+    for o in orcs:
+        o.run(wl.n_steps)
+    _compare(wl, sim, orcs, TOL32)
