@@ -256,17 +256,37 @@ static gfdtd_status build_tiles(gfdtd_ctx* c, int C, int TB, std::vector<int2> o
     const int L = tile_margin(TB, pos, 16 / c->eb);
     const bool matter = (d.flags & F_MATTER) != 0;
     const bool fast_ok = fast_eligible(d, C) && c->prec != GFDTD_F32_KAHAN;
-    for (long long x0 = 0; x0 < c->nz[i]; x0 += W) {
-      const long long base = x0 - L;
-      const bool edge = base < 0 || base + 32LL * C > c->nz[i];
-      const int v = matter ? 1 : (fast_ok && !edge ? 2 : 0);
+    const long long nz = c->nz[i], V = 16 / c->eb, span = 32LL * C;
+    for (long long x0 = 0; x0 < nz; x0 += W) {
+      long long base = x0 - L;
+      const bool left = base < 0, right = base + span > nz;
+      // The fast kernel also takes a tile at one end of the domain: its window
+      // is moved inside [0, nz) (the zero fields beyond the end are exact, so
+      // no margin is needed on that side), rounded to whole vectors at the
+      // right end.  Tiles at both ends, or whose window would not cover the
+      // output range, stay with the general kernel.
+      int edge = 0;
+      bool fast_tile = fast_ok && !(left && right);
+      if (fast_tile && left) {
+        base = 0;
+        edge = 1;
+        if (span > nz) fast_tile = false;
+      } else if (fast_tile && right) {
+        base = (nz + V - 1) / V * V - span;
+        edge = 2 | (int)((base + span - nz) << 8);
+        // the two cells before nz must lie in the last lane's run (B_nz-1 + B_nz-2 term)
+        if (base < 0 || base + L > x0 || base + span - nz > C - 2) fast_tile = false;
+      }
+      const int v = matter ? 1 : (fast_tile ? 2 : 0);
       part[v][pos ? 0 : 1].push_back(make_int2(i, (int)x0));
-      c->valid_cells[v] += std::min<long long>(W, c->nz[i] - x0);
+      c->valid_cells[v] += std::min<long long>(W, nz - x0);
       if (v == 2) {
         FastTile f{};
         f.e = d.off + base;
         f.inst = i;
         f.x0 = (int)x0;
+        f.base = (int)base;
+        f.edge = edge;
         const std::vector<SrcDev>& src = c->sources[i];
         for (size_t q = 0; q < src.size() && q < 32; ++q)
           if (src[q].node >= base && src[q].node < base + 32LL * C) f.smask |= 1u << q;

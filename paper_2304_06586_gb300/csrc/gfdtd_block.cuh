@@ -555,12 +555,19 @@ __device__ __forceinline__ long long track_d(const long long* __restrict__ zq, i
 
 // B^n of a fast tile with P_c = vc(c) D_c (level n-1/2) for cell c of the
 // lane's run; P of the next lane's cell 0 comes by shuffle.
+// x, or zero when z (the argument is evaluated by every lane first).
+template <typename R>
+__device__ __forceinline__ R sel0(bool z, R x) { return z ? (R)0 : x; }
+
+// zl / zr: the cells left of the run / right of it are outside the domain (zero).
 template <int C, bool POS, typename R, typename VC>
-__device__ __forceinline__ void fast_b_update_cells(R (&B)[C], const R (&D)[C], VC vc, R bB0, R cc, R cb) {
-  const R pr = __shfl_down_sync(FULL, vc(0) * D[0], 1);
+__device__ __forceinline__ void fast_b_update_cells(R (&B)[C], const R (&D)[C], VC vc, R bB0, R cc, R cb,
+                                                    bool zl = false, bool zr = false) {
+  // every lane takes part in each shuffle; the ends of the domain are applied after
+  const R pr = sel0(zr, __shfl_down_sync(FULL, vc(0) * D[0], 1));
   if (POS) {
-    const R bl1 = __shfl_up_sync(FULL, B[C - 1], 1);
-    const R bl2 = __shfl_up_sync(FULL, B[C - 2], 1);
+    const R bl1 = sel0(zl, __shfl_up_sync(FULL, B[C - 1], 1));
+    const R bl2 = sel0(zl, __shfl_up_sync(FULL, B[C - 2], 1));
     R pn = pr;
 #pragma unroll
     for (int c = C - 1; c >= 0; --c) {
@@ -571,8 +578,8 @@ __device__ __forceinline__ void fast_b_update_cells(R (&B)[C], const R (&D)[C], 
       pn = pc;
     }
   } else {
-    const R br1 = __shfl_down_sync(FULL, B[0], 1);
-    const R br2 = __shfl_down_sync(FULL, B[1], 1);
+    const R br1 = sel0(zr, __shfl_down_sync(FULL, B[0], 1));
+    const R br2 = sel0(zr, __shfl_down_sync(FULL, B[1], 1));
     R pc = vc(0) * D[0];
 #pragma unroll
     for (int c = 0; c < C; ++c) {
@@ -595,10 +602,11 @@ __device__ __forceinline__ void fast_b_update(R (&B)[C], const R (&D)[C], R v, R
 // of the next cell that needs this cell's old D (its downwind neighbour) is
 // formed before that D is overwritten.  B is (S/mu) B^n.
 template <int C, bool POS, typename R>
-__device__ __forceinline__ void fast_d_update(const R (&B)[C], R (&D)[C], R a, R bD1, R bD2) {
-  const R dl = __shfl_up_sync(FULL, D[C - 1], 1);
-  const R dr = __shfl_down_sync(FULL, D[0], 1);
-  const R bnl = __shfl_up_sync(FULL, B[C - 1], 1);
+__device__ __forceinline__ void fast_d_update(const R (&B)[C], R (&D)[C], R a, R bD1, R bD2,
+                                              bool zl = false, bool zr = false) {
+  const R dl = sel0(zl, __shfl_up_sync(FULL, D[C - 1], 1));
+  const R dr = sel0(zr, __shfl_down_sync(FULL, D[0], 1));
+  const R bnl = sel0(zl, __shfl_up_sync(FULL, B[C - 1], 1));
   if (POS) {
     R part = bD2 * dr + (B[C - 2] - B[C - 1]);
 #pragma unroll
@@ -635,8 +643,9 @@ __device__ __forceinline__ void run_tile_fast(const BlockArgs<T>& A, const InstD
   constexpr int L = tile_margin(TB, POS, 16 / sizeof(T));     // x0 - base
   constexpr int W = tile_width(C, TB, POS, 16 / sizeof(T));   // output cells
   const int x0 = ft.x0;
-  const int base = x0 - L;
+  const int base = ft.base;                        // x0 - L, or moved inside the domain at its ends
   const int k0 = base + lane * C;
+  (void)L;
 
   R B[C], D[C];
   {
@@ -715,7 +724,7 @@ __device__ __forceinline__ void run_tile_fast(const BlockArgs<T>& A, const InstD
     const int c1b = (int)((tr.dnext + span + 0xFFFFFFFFLL) >> 32);   // last step
     const bool no_event = POS ? tr.dprev + span + dq2 <= 0 : tr.dnext + span + dq2 > 0;
     const bool one_side = POS ? (c1a >= C || c1b <= 0) : (c1a <= 0 || c1b >= C);
-    quiet = __all_sync(FULL, (smask | pmask) == 0u && no_event && one_side);
+    quiet = __all_sync(FULL, (smask | pmask) == 0u && ft.edge == 0 && no_event && one_side);
   }
   if (quiet) {
     const int c1 = (int)((tr.dnext + 0xFFFFFFFFLL) >> 32);
@@ -728,26 +737,64 @@ __device__ __forceinline__ void run_tile_fast(const BlockArgs<T>& A, const InstD
     tr.dnext += (long long)A.nsteps * dq2;
     if constexpr (NB == 2) tr.dnext2 += (long long)A.nsteps * dq2;
   } else {
+  // Tiles at the ends of the domain (Sec. 4 reading: all fields are zero outside
+  // [0, nz), with E*_nz = H*_-1 = 0): the neighbours beyond an end read as zero,
+  // the cells of lane 31 at or past nz are held at zero, and the two terms where
+  // the fused update differs from those boundary values are corrected:
+  // H'_-1 = 0 adds cb D_0 to D_0, and for v >= 0 E'_nz = 0 subtracts
+  // cb (B_nz-1 + B_nz-2) from B_nz-1.
+  const bool ledge = (ft.edge & 1) != 0, redge = (ft.edge & 2) != 0;
+  const bool zl = ledge && lane == 0, zr = redge && lane == 31;
+  const int rpast = ft.edge >> 8;                  // cells of the window at or past nz (< 16 / sizeof(T))
+  constexpr int VW = 16 / sizeof(T);
+  auto zero_past_end = [&](R (&X)[C]) {
+#pragma unroll
+    for (int c = C - VW + 1; c < C; ++c)
+      if (zr && c >= C - rpast) X[c] = (R)0;
+  };
+  if (redge) {
+    zero_past_end(B);
+    zero_past_end(D);
+  }
   for (int s = 0; s < A.nsteps; ++s) {
     // ---- material at level n-1/2 for this lane's cells: c >= c1 lies beyond the next boundary
     const int c1 = (int)((tr.dnext + 0xFFFFFFFFLL) >> 32);
-    const R v = c1 <= 0 ? vR : vL;       // exact for the whole run unless 0 < c1 < C
 
-    // ---- B^n with P_c = v_c D_c: one multiplier per lane unless a lane of the
-    // warp holds a boundary inside its run (cells c >= c1 take vR)
-    if (__any_sync(FULL, c1 > 0 && c1 < C)) {
-      if constexpr (NB == 2) {
-        const int c2 = (int)((tr.dnext2 + 0xFFFFFFFFLL) >> 32);
-        fast_b_update_cells<C, POS>(B, D, [&](int c) { return c >= c2 ? vR : (c >= c1 ? vM : vL); },
-                                    bB0, cc, cb);
-      } else {
-        fast_b_update_cells<C, POS>(B, D, [&](int c) { return c >= c1 ? vR : vL; }, bB0, cc, cb);
+    R bend = 0;                          // right end, v >= 0: B_nz-1 + B_nz-2 at level n-1
+    if (POS && redge) {
+#pragma unroll
+      for (int q = 0; q < VW; ++q)
+        if (rpast == q) bend = B[C - 1 - q] + B[C - 2 - q];
+    }
+
+    // ---- B^n with P_c = v_c D_c: cells c >= c1 take vM (NB = 2) or vR, c >= c2 vR.
+    // Wide runs keep one copy of the update (per-cell multiplier) so that the
+    // loop fits the instruction cache next to the quiet loop; 16-cell runs
+    // also keep a copy with one multiplier for warps without a boundary inside.
+    if constexpr (NB == 2) {
+      const int c2 = (int)((tr.dnext2 + 0xFFFFFFFFLL) >> 32);
+      fast_b_update_cells<C, POS>(B, D, [&](int c) { return c >= c2 ? vR : (c >= c1 ? vM : vL); },
+                                  bB0, cc, cb, zl, zr);
+    } else {
+      if (__any_sync(FULL, c1 < C))
+        fast_b_update_cells<C, POS>(B, D, [&](int c) { return c >= c1 ? vR : vL; }, bB0, cc, cb, zl, zr);
+      else
+        fast_b_update_cells<C, POS>(B, D, [&](int) { return vL; }, bB0, cc, cb, zl, zr);
+    }
+    if (redge) {
+      if (POS) {
+#pragma unroll
+        for (int q = 0; q < VW; ++q)
+          if (zr && rpast == q) B[C - 1 - q] -= cb * bend;
       }
-    } else
-      fast_b_update<C, POS>(B, D, v, bB0, cc, cb);
+      zero_past_end(B);
+    }
+    const R d0 = D[0];                   // left end: D_0 at level n-1/2
 
     // ---- D^{n+1/2}
-    fast_d_update<C, POS>(B, D, a, bD1, bD2);
+    fast_d_update<C, POS>(B, D, a, bD1, bD2, zl, zr);
+    if (ledge && zl) D[0] += cb * d0;
+    if (redge) zero_past_end(D);
 
     // ---- soft sources at t_{n+1/2}
     for (unsigned m = smask; m; m &= m - 1) {

@@ -96,12 +96,14 @@ __host__ __device__ constexpr int tile_width(int C, int TB, bool pos, int V) {
 // A tile of the fast kernel: where its input window starts in the field
 // arrays and which sources and probes of its instance it holds (host-built).
 struct FastTile {
-  long long e;       // element offset of the first input cell, off + x0 - (upwind cone)
+  long long e;       // element offset of the first input cell: off + base
   int inst;          // instance
   int x0;            // first output cell
   unsigned smask;    // bit q: source src0 + q has its node in the tile's input window
   unsigned pmask;    // bit q: probe prb0 + q has its node among the tile's output cells
-  int pad0, pad1;
+  int base;          // first cell of the window, x0 - tile_margin inside the domain
+  int edge;          // bit 0: the window starts at cell 0; bit 1: it ends at or past nz,
+                     // with (edge >> 8) cells of the window beyond nz
 };
 static_assert(sizeof(FastTile) == 32, "FastTile is copied by TMA in 16-byte units");
 

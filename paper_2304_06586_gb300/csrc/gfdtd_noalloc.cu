@@ -155,6 +155,7 @@ extern "C" gfdtd_status gfdtd_step_noalloc(int64_t nz, double S, gfdtd_kind kind
         f.e = b0;
         f.inst = 0;
         f.x0 = (int)x0;
+        f.base = (int)b0;
         fast.push_back(f);
       }
     }
