@@ -48,7 +48,7 @@ def kernel_source_hash():
 def measured_traffic():
     """DRAM bytes per cell-update of the fast kernel from the committed ncu
     summary, if it was taken on the kernel as it is now (else None)."""
-    path = os.path.join(ROOT, "profiles", "fast_kernel_crystal256x64steps.md")
+    path = os.path.join(ROOT, "profiles", "fast_kernel_crystal.md")
     if not os.path.exists(path):
         return None
     fields = {}
