@@ -87,6 +87,66 @@ def roofline_of(kt):
                     % FLOPS_PER_CELL_UPDATE}
 
 
+FP64_PEAK_TFLOPS = 2 * 2 * SM_COUNT * SM_MAX_MHZ * 1e6 / 1e12   # 2 FP64 FMA per SM per cycle
+STAB_FLOPS_PER_SAMPLE = 110      # FP64 operations of one amplification matrix and its eigenvalues
+TMM_FLOPS_PER_LAYER = 67         # FP64 operations of one interface + propagation matrix product
+
+
+def sweep_measurements(torch, gb, stream, reps=3):
+    """Throughput of the two batched FP64 sweep kernels (stability map, star TMM)
+    on seeded synthetic parameter sets, CUDA events on the launching stream."""
+    rng = np.random.default_rng(20230413 + 9)
+    out = {}
+    n, n_theta = 1 << 20, 1024
+    P = [torch.as_tensor(v).to("cuda") for v in (rng.uniform(0.1, 1.0, n), rng.uniform(-0.9, 0.9, n),
+                                                   rng.uniform(1.0, 9.0, n), rng.uniform(1.0, 2.0, n))]
+    K = torch.as_tensor(rng.integers(0, 2, n), dtype=torch.int32).to("cuda")
+    res = torch.empty(n, dtype=torch.float64, device="cuda")
+    lib = gb.load()
+
+    def stab():
+        rc = lib.gfdtd_stability_map(n, *[t.data_ptr() for t in P], K.data_ptr(), n_theta, res.data_ptr(),
+                                     stream.cuda_stream)
+        assert rc == 0, rc
+
+    n_s, n_l, n_f = 1 << 16, 16, 64
+    off = torch.arange(0, (n_s + 1) * n_l, n_l, dtype=torch.int64).to("cuda")
+    eps = torch.as_tensor(rng.uniform(1.0, 6.0, n_s * n_l)).to("cuda")
+    mu = torch.ones(n_s * n_l, dtype=torch.float64, device="cuda")
+    th = torch.as_tensor(rng.uniform(5.0, 80.0, n_s * n_l)).to("cuda")
+    beta = torch.as_tensor(rng.uniform(-0.3, 0.3, n_s)).to("cuda")
+    om = torch.linspace(0.05, 0.6, n_f, dtype=torch.float64, device="cuda")
+    T = torch.empty(2 * n_s * n_f, dtype=torch.float64, device="cuda")
+    G = torch.empty_like(T)
+
+    def tmm():
+        rc = lib.gfdtd_star_tmm(n_s, off.data_ptr(), eps.data_ptr(), mu.data_ptr(), th.data_ptr(), beta.data_ptr(),
+                                n_f, om.data_ptr(), T.data_ptr(), G.data_ptr(), stream.cuda_stream)
+        assert rc == 0, rc
+
+    for name, fn, units, flops_per_unit, unit_name in (
+            ("stability_map", stab, n * n_theta, STAB_FLOPS_PER_SAMPLE, "G samples/s"),
+            ("star_tmm", tmm, n_s * n_f * (n_l - 1), TMM_FLOPS_PER_LAYER, "G layer-frequencies/s")):
+        fn()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(reps):
+            fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        sec = e0.elapsed_time(e1) / 1e3 / reps
+        achieved = flops_per_unit * units / sec / 1e12
+        out[name] = {"value": units / sec / 1e9, "unit": unit_name, "ms_per_launch": sec * 1e3,
+                     "roofline": {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS,
+                                  "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS, "traffic": None,
+                                  "note": "FP64 pipe: %d flops per unit (algorithmic, sin/cos not counted), "
+                                          "peak = 2 FMA x 152 SMs x 2070 MHz (derived)" % flops_per_unit}}
+    out["stability_map"]["config"] = "%d points x %d kz samples, kinds mixed" % (n, n_theta)
+    out["star_tmm"]["config"] = "%d stacks x %d layers x %d frequencies" % (n_s, n_l, n_f)
+    return out
+
+
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -98,6 +158,7 @@ def parse():
     ap.add_argument("--plain-steps", type=int, default=4)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-sweeps", action="store_true", help="skip the stability-map and star-TMM timings")
     ap.add_argument("--tile", default="", help="cells_per_lane,time_block[,blocks_per_sm] (default: autotune)")
     return ap.parse_args()
 
@@ -321,6 +382,7 @@ def main():
             plain = {"value": pv, "unit": "Gcell-updates/s", "steps": args.plain_steps,
                      "batched_over_plain": value / world / pv}
         sim.close()
+        sweeps = None if args.no_sweeps else sweep_measurements(torch, gb, stream)
 
     if rank != 0:
         return
@@ -334,7 +396,7 @@ def main():
                        "l2": "inputs larger than L2 (%.2f GB of fields)" % (cells * 16 / 1e9),
                        "parallelism": "instances sharded per rank" if world > 1 else "1 GPU"},
             "e2e": e2e, "gpu_launches": launches, "roofline": roofline, "plain": plain,
-            "clocks": clocks}
+            "clocks": clocks, "sweeps": sweeps}
     if not args.no_cpu:
         line["cpu_baseline"] = cpu_baseline(wl)
     print(json.dumps(line), flush=True)

@@ -243,6 +243,41 @@ typedef struct {
 
 gfdtd_status gfdtd_profile_kernels(gfdtd_ctx* ctx, int64_t n_steps, gfdtd_kernel_times* out);
 
+/* ---- batched parameter sweeps (context-free, GPU, FP64) ----
+ *
+ * Von Neumann stability map (Sec. 5 and App. A): for each point i, the
+ * largest eigenvalue modulus of the one-step amplification matrix of a
+ * uniform medium (eps_r[i], mu_r[i]) under the scheme of Sec. 4 / Table 1
+ * with Courant number S[i] and velocity beta[i] (kind[i]: GFDTD_PERTURBATION
+ * or GFDTD_MATTER), maximised over kz dz = pi (j + 1) / n_theta,
+ * j = 0 .. n_theta - 1.  The scheme is stable for a medium where the result
+ * is <= 1 (to rounding).  S, beta, eps_r, mu_r, kind and out are DEVICE
+ * arrays of n elements owned by the caller; the call only enqueues the work
+ * on cuda_stream (NULL: the legacy default stream) and returns.  Valid inputs
+ * are those of gfdtd_stability (0 < S <= 1, |beta| < 1, eps_r, mu_r > 0);
+ * others give unspecified values.  E_ARG for n < 0, n_theta < 1 or a NULL
+ * array (n > 0); E_CUDA if the launch fails.  n == 0 does nothing. */
+gfdtd_status gfdtd_stability_map(int64_t n, const double* S, const double* beta, const double* eps_r,
+                                 const double* mu_r, const int* kind, int n_theta, double* out,
+                                 void* cuda_stream);
+
+/* Star transfer-matrix scattering of moving layered stacks (App. B.3, with
+ * the matrices derived from Eq. cont and Eq. star): stack s has the layers
+ * layer_off[s] .. layer_off[s+1]-1 (at least two), the first and last being
+ * the semi-infinite media, all moving at beta[s] (moving perturbation, c = 1,
+ * lengths in cells).  eps_r, mu_r: per layer; thick: per layer, the length in
+ * the moving frame (read for the inner layers only).  For each incident lab
+ * frequency omega[f] (a +z wave in the first medium) it writes the
+ * transmission T and reflection Gamma as ratios of physical E amplitudes,
+ * complex, interleaved (re, im), at index s * n_freq + f.  All arrays are
+ * DEVICE arrays owned by the caller (layer_off: n_stacks + 1 entries; T and
+ * Gamma: 2 n_stacks n_freq doubles); asynchronous on cuda_stream.  A stack
+ * with fewer than two layers gets NaN.  E_ARG for negative counts or a NULL
+ * array (nonzero counts); E_CUDA if the launch fails. */
+gfdtd_status gfdtd_star_tmm(int64_t n_stacks, const int64_t* layer_off, const double* eps_r,
+                            const double* mu_r, const double* thick, const double* beta, int64_t n_freq,
+                            const double* omega, double* T, double* Gamma, void* cuda_stream);
+
 /* Wait for all work queued on the context's stream; returns E_TIMEOUT (once)
  * if a kernel reported that a bounded wait gave up since the last check.
  * gfdtd_read_fields and gfdtd_read_spectrum report it the same way. */

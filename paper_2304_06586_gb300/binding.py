@@ -63,6 +63,10 @@ SIGNATURES = {
     "gfdtd_read_spectrum": (C.c_int, [C.c_void_p, C.c_int, C.c_int, _dp, _dp]),
     "gfdtd_steps_done": (C.c_int, [C.c_void_p, _i64p]),
     "gfdtd_stability": (C.c_int, [C.c_double, C.c_double, C.c_double, C.c_double, C.c_int, _dp]),
+    "gfdtd_stability_map": (C.c_int, [C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
+                                      C.c_int, C.c_void_p, C.c_void_p]),
+    "gfdtd_star_tmm": (C.c_int, [C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
+                                 C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
     "gfdtd_adjoint": (C.c_int, [C.c_void_p, C.c_int64, C.c_int, C.c_int, C.c_int, _dp, _dp]),
     "gfdtd_set_tuning": (C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_int]),
     "gfdtd_get_stats": (C.c_int, [C.c_void_p, C.POINTER(Stats)]),
@@ -145,6 +149,58 @@ def stability(S, beta, eps_r, mu_r=1.0, kind=PERTURBATION):
     if rc != OK:
         raise GfdtdError(rc, "gfdtd_stability")
     return out.value
+
+
+def _dev(x, dtype):
+    """A contiguous CUDA tensor of x (argument marshalling for the sweep entry points)."""
+    import torch
+    t = torch.as_tensor(x, dtype=dtype)
+    return t.to("cuda").contiguous()
+
+
+def stability_map(S, beta, eps_r, mu_r, kind=PERTURBATION, n_theta=2048, stream=None):
+    """gfdtd_stability_map: max |zeta| for every point of the (broadcast) parameter
+    arrays, on the GPU.  Accepts numpy arrays or CUDA tensors; returns a CUDA
+    float64 tensor (call .cpu() for numpy)."""
+    import torch
+    S, beta, eps_r, mu_r, kind = torch.broadcast_tensors(
+        *[torch.as_tensor(v, dtype=torch.float64) for v in (S, beta, eps_r, mu_r, kind)])
+    n = S.numel()
+    a = [_dev(v.reshape(-1), torch.float64) for v in (S, beta, eps_r, mu_r)]
+    k = _dev(kind.reshape(-1), torch.int32)
+    out = torch.empty(n, dtype=torch.float64, device="cuda")
+    st = stream if stream is not None else torch.cuda.current_stream().cuda_stream
+    rc = load().gfdtd_stability_map(n, *[t.data_ptr() for t in a], k.data_ptr(), int(n_theta),
+                                    out.data_ptr(), st)
+    if rc != OK:
+        raise GfdtdError(rc, "gfdtd_stability_map")
+    return out.reshape(S.shape)
+
+
+def star_tmm(stacks, beta, omega, stream=None):
+    """gfdtd_star_tmm: (T, Gamma) of moving stacks for every incident frequency.
+
+    stacks: list of (eps, mu, thick) per stack (eps, mu per layer, first and
+    last semi-infinite; thick per layer, inner layers used); beta: per stack;
+    omega: frequencies.  Returns two complex CUDA tensors [n_stacks, n_freq]."""
+    import torch
+    off = np.zeros(len(stacks) + 1, dtype=np.int64)
+    off[1:] = np.cumsum([len(e) for e, _, _ in stacks])
+    cat = lambda i: np.concatenate([np.asarray(st[i], float) for st in stacks]) if stacks else np.zeros(0)
+    d_off = _dev(off, torch.int64)
+    d_eps, d_mu, d_th = (_dev(cat(i), torch.float64) for i in range(3))
+    d_beta = _dev(np.broadcast_to(np.asarray(beta, float), (len(stacks),)).copy(), torch.float64)
+    d_om = _dev(np.asarray(omega, float).reshape(-1), torch.float64)
+    n_s, n_f = len(stacks), d_om.numel()
+    T = torch.empty(n_s * n_f * 2, dtype=torch.float64, device="cuda")
+    G = torch.empty_like(T)
+    st = stream if stream is not None else torch.cuda.current_stream().cuda_stream
+    rc = load().gfdtd_star_tmm(n_s, d_off.data_ptr(), d_eps.data_ptr(), d_mu.data_ptr(), d_th.data_ptr(),
+                               d_beta.data_ptr(), n_f, d_om.data_ptr(), T.data_ptr(), G.data_ptr(), st)
+    if rc != OK:
+        raise GfdtdError(rc, "gfdtd_star_tmm")
+    as_c = lambda x: torch.view_as_complex(x.reshape(n_s, n_f, 2))
+    return as_c(T), as_c(G)
 
 
 def step_noalloc(B_ptr, D_ptr, nz, S, kind=PERTURBATION, beta=0.0, interp=LAYERS, z=(), eps=(1.0,),
