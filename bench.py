@@ -367,6 +367,26 @@ def main():
             e2e = {"value": cu * world / dt / 1e9, "unit": "Gcell-updates/s",
                    "h2d_bytes_per_step": 2 * nbytes, "d2h_bytes_per_step": 2 * nbytes}
 
+        # space-time capture of the largest instance (every cell, FP16, one frame per time
+        # block): throughput of the same step with frames recorded
+        capture = None
+        if not args.no_sweeps:
+            big = int(np.argmax([i.nz for i in wl.instances]))
+            tb = st["time_block"]
+            sim.set_capture(big, gb.FIELD_E, 0, wl.instances[big].nz, 1, tb, max_frames=T // tb + 1, half=True)
+            c0, c1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            barrier()
+            c0.record(stream)
+            sim.step(T)
+            c1.record(stream)
+            barrier()
+            cms = c0.elapsed_time(c1)
+            nfr = sim.capture()[0].shape[0]
+            sim.set_capture(0, gb.FIELD_D, 0, 1, 1, 0)
+            capture = {"value": cells * T / (cms / 1e3) / 1e9, "unit": "Gcell-updates/s",
+                       "frames": nfr, "cells_per_frame": wl.instances[big].nz, "field": "E, FP16",
+                       "t_stride": tb, "relative_to_value": (cells * T / (cms / 1e3) / 1e9) / (value / world)}
+
         # plain kernel (one step, one instance per launch) on a few steps
         plain = None
         if args.plain_steps > 0:
@@ -396,7 +416,7 @@ def main():
                        "l2": "inputs larger than L2 (%.2f GB of fields)" % (cells * 16 / 1e9),
                        "parallelism": "instances sharded per rank" if world > 1 else "1 GPU"},
             "e2e": e2e, "gpu_launches": launches, "roofline": roofline, "plain": plain,
-            "clocks": clocks, "sweeps": sweeps}
+            "clocks": clocks, "sweeps": sweeps, "capture": capture}
     if not args.no_cpu:
         line["cpu_baseline"] = cpu_baseline(wl)
     print(json.dumps(line), flush=True)

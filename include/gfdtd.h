@@ -226,6 +226,30 @@ typedef struct {
 
 gfdtd_status gfdtd_get_stats(const gfdtd_ctx* ctx, gfdtd_stats* out);
 
+/* Space-time capture (the z-t field maps of Fig. 5(a)): after every t_stride
+ * steps taken by gfdtd_step, counted from the call, record field `which`
+ * (any gfdtd_field, as gfdtd_read_fields defines it, at the state reached) of
+ * instance inst at cells z0, z0 + z_stride, ... < z1 as one frame, rounded to
+ * FP32 (half = 0) or FP16 (half = 1), in a device buffer of max_frames frames
+ * that the context allocates here (through the allocator hooks); frames past
+ * max_frames are counted as dropped.  gfdtd_step ends its CUDA-graph chunks at
+ * frame steps, so a t_stride below the tile time block shortens the blocks.
+ * Frames are not recorded by gfdtd_step_plain, gfdtd_profile_kernels or
+ * gfdtd_adjoint.  One capture per context; a new call replaces it (frames
+ * discarded), t_stride = 0 turns it off (frames kept).  E_ARG unless
+ * 0 <= z0 < z1 <= nz, z_stride, t_stride, max_frames >= 1 and half is 0 or 1;
+ * E_UNSUPPORTED for H of moving matter; E_OOM if the buffer cannot be had. */
+gfdtd_status gfdtd_set_capture(gfdtd_ctx* ctx, int inst, gfdtd_field which, int64_t z0, int64_t z1,
+                               int64_t z_stride, int64_t t_stride, int64_t max_frames, int half);
+
+/* Frames recorded, values per frame and frames dropped so far. */
+gfdtd_status gfdtd_capture_info(const gfdtd_ctx* ctx, int64_t* frames, int64_t* cells_per_frame,
+                                int64_t* dropped);
+
+/* Copy the recorded frames, frame after frame (n = frames x cells_per_frame),
+ * widened to FP64, into host_dst.  Synchronises the context's stream. */
+gfdtd_status gfdtd_read_capture(gfdtd_ctx* ctx, double* host_dst, int64_t n);
+
 /* Measurement hook (no counterpart in the paper).  Advances every instance by
  * n_steps exactly as gfdtd_step does (same kernels, same results), but
  * launches them one by one outside CUDA graphs, brackets each batched-kernel

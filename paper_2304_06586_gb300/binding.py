@@ -70,6 +70,10 @@ SIGNATURES = {
     "gfdtd_adjoint": (C.c_int, [C.c_void_p, C.c_int64, C.c_int, C.c_int, C.c_int, _dp, _dp]),
     "gfdtd_set_tuning": (C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_int]),
     "gfdtd_get_stats": (C.c_int, [C.c_void_p, C.POINTER(Stats)]),
+    "gfdtd_set_capture": (C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_int64, C.c_int64, C.c_int64, C.c_int64,
+                                    C.c_int64, C.c_int]),
+    "gfdtd_capture_info": (C.c_int, [C.c_void_p, _i64p, _i64p, _i64p]),
+    "gfdtd_read_capture": (C.c_int, [C.c_void_p, _dp, C.c_int64]),
     "gfdtd_profile_kernels": (C.c_int, [C.c_void_p, C.c_int64, C.POINTER(KernelTimes)]),
     "gfdtd_synchronize": (C.c_int, [C.c_void_p]),
     "gfdtd_last_error": (C.c_char_p, [C.c_void_p]),
@@ -338,6 +342,20 @@ class Simulation:
         s = Stats()
         self._check(self._L.gfdtd_get_stats(self._h, C.byref(s)), "get_stats")
         return {k: getattr(s, k) for k, _ in Stats._fields_}
+
+    def set_capture(self, inst, which, z0, z1, z_stride=1, t_stride=1, max_frames=1024, half=False):
+        """Record field `which` of instance inst at cells z0:z1:z_stride after every
+        t_stride steps (t_stride=0 turns capture off)."""
+        self._check(self._L.gfdtd_set_capture(self._h, inst, which, z0, z1, z_stride, t_stride, max_frames,
+                                              1 if half else 0), "set_capture")
+
+    def capture(self):
+        """The recorded frames as a [frames, cells] float64 array, and the dropped count."""
+        f, m, d = C.c_int64(), C.c_int64(), C.c_int64()
+        self._check(self._L.gfdtd_capture_info(self._h, C.byref(f), C.byref(m), C.byref(d)), "capture_info")
+        out = np.empty(f.value * m.value)
+        self._check(self._L.gfdtd_read_capture(self._h, _ptr(out), len(out)), "read_capture")
+        return out.reshape(f.value, m.value), d.value
 
     def profile_kernels(self, n):
         """Advance n steps like step(), timing each batched-kernel launch with

@@ -116,6 +116,14 @@ struct gfdtd_ctx {
       d_bin0, d_pnode, d_acc0_re, d_acc0_im, d_adj_tiles;
   int n_adj_tiles = 0;
 
+  // space-time capture: frames of one field of one instance every ts steps
+  struct Capture {
+    bool on = false;
+    int inst = 0, which = 0, half = 0;
+    long long z0 = 0, zs = 1, m = 0, ts = 0, max_frames = 0, frames = 0, dropped = 0, n_start = 0;
+    DevBuf buf;
+  } cap;
+
   // graphs keyed by (chunk length, parity)
   std::map<std::pair<int, int>, cudaGraphExec_t> graphs;
   long long launches = 0;
@@ -1015,12 +1023,83 @@ gfdtd_status gfdtd_step(gfdtd_ctx* c, int64_t n_steps) {
     if (s) return s;
   }
   while (n_steps > 0) {
-    const int ch = (int)std::min<int64_t>(n_steps, kChunk);
+    int ch = (int)std::min<int64_t>(n_steps, kChunk);
+    if (c->cap.on)   // end the chunk at the next frame
+      ch = (int)std::min<long long>(ch, c->cap.ts - (c->n_done - c->cap.n_start) % c->cap.ts);
     s = run_chunk(c, ch);
     if (s) return s;
     n_steps -= ch;
+    if (c->cap.on && (c->n_done - c->cap.n_start) % c->cap.ts == 0) {
+      gfdtd_ctx::Capture& k = c->cap;
+      if (k.frames < k.max_frames) {
+        char* dst = (char*)k.buf.p + (size_t)(k.frames * k.m) * (k.half ? 2 : 4);
+        CKI(c, capture_launch(c->prec, k.which, (const InstDev*)c->d_inst.p, k.inst, tables_of(c),
+                              c->B[c->cur].p, c->D[c->cur].p, k.z0, k.zs, k.m, c->n_done, k.half, dst,
+                              c->stream));
+        ++c->launches;
+        ++k.frames;
+      } else {
+        ++k.dropped;
+      }
+    }
   }
   return GFDTD_OK;
+}
+
+gfdtd_status gfdtd_set_capture(gfdtd_ctx* c, int inst, gfdtd_field which, int64_t z0, int64_t z1,
+                               int64_t z_stride, int64_t t_stride, int64_t max_frames, int half) {
+  if (!c) return GFDTD_E_ARG;
+  if (t_stride == 0) {
+    c->cap.on = false;
+    return GFDTD_OK;
+  }
+  gfdtd_status s = check_inst(c, inst);
+  if (s) return s;
+  if (which < GFDTD_FIELD_D || which > GFDTD_FIELD_ESTAR) return fail(c, GFDTD_E_ARG, "bad field");
+  if (which == GFDTD_FIELD_H && c->media[inst].kind == GFDTD_MATTER)
+    return fail(c, GFDTD_E_UNSUPPORTED, "H is not available for moving matter");
+  if (z0 < 0 || z1 > c->nz[inst] || z0 >= z1 || z_stride < 1 || t_stride < 1 || max_frames < 1 ||
+      (half != 0 && half != 1))
+    return fail(c, GFDTD_E_ARG, "need 0 <= z0 < z1 <= nz, strides >= 1, max_frames >= 1, half 0 or 1");
+  const long long m = (z1 - z0 + z_stride - 1) / z_stride;
+  if ((s = dalloc(c, c->cap.buf, (size_t)(max_frames * m) * (half ? 2 : 4)))) return s;
+  gfdtd_ctx::Capture& k = c->cap;
+  k.on = true;
+  k.inst = inst;
+  k.which = (int)which;
+  k.half = half;
+  k.z0 = z0;
+  k.zs = z_stride;
+  k.m = m;
+  k.ts = t_stride;
+  k.max_frames = max_frames;
+  k.frames = 0;
+  k.dropped = 0;
+  k.n_start = c->n_done;
+  return GFDTD_OK;
+}
+
+gfdtd_status gfdtd_capture_info(const gfdtd_ctx* c, int64_t* frames, int64_t* cells_per_frame,
+                                int64_t* dropped) {
+  if (!c || !frames || !cells_per_frame || !dropped) return GFDTD_E_ARG;
+  *frames = c->cap.frames;
+  *cells_per_frame = c->cap.m;
+  *dropped = c->cap.dropped;
+  return GFDTD_OK;
+}
+
+gfdtd_status gfdtd_read_capture(gfdtd_ctx* c, double* host_dst, int64_t n) {
+  if (!c) return GFDTD_E_ARG;
+  const long long have = c->cap.frames * c->cap.m;
+  if (!host_dst || n != have) return fail(c, GFDTD_E_ARG, "n must equal frames x cells_per_frame (%lld)", have);
+  if (n == 0) return GFDTD_OK;
+  gfdtd_status s = dalloc(c, c->d_tmp, (size_t)n * sizeof(double));
+  if (s) return s;
+  // frames are stored in FP32 or FP16: widen with the converters of those storage types
+  CKI(c, convert_launch(c->cap.half ? GFDTD_F16 : GFDTD_F32, 1, c->cap.buf.p, c->d_tmp.p, n, c->stream));
+  CK(c, cudaMemcpyAsync(host_dst, c->d_tmp.p, (size_t)n * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+  CK(c, cudaStreamSynchronize(c->stream));
+  return device_status(c);
 }
 
 gfdtd_status gfdtd_profile_kernels(gfdtd_ctx* c, int64_t n_steps, gfdtd_kernel_times* out) {
@@ -1293,7 +1372,7 @@ void gfdtd_destroy(gfdtd_ctx* c) {
                     &c->cD[1], &c->d_ndone, &c->d_inst, &c->d_zq,
                     &c->d_tabE, &c->d_tabH, &c->d_srcs, &c->d_prbs, &c->d_amp, &c->d_samples,
                     &c->d_omega, &c->d_binprb, &c->d_acc_re, &c->d_acc_im, &c->d_tiles[0],
-                    &c->d_tiles[1], &c->d_tiles[2], &c->d_tmp, &c->d_tabE32, &c->d_tabH32, &c->d_ftiles, &c->d_track,
+                    &c->d_tiles[1], &c->d_tiles[2], &c->d_tmp, &c->d_tabE32, &c->d_tabH32, &c->d_ftiles, &c->d_track, &c->cap.buf,
                     &c->d_ckB, &c->d_ckD, &c->d_dseg, &c->d_wB[0], &c->d_wB[1], &c->d_lB[0],
                     &c->d_lB[1], &c->d_lD[0], &c->d_lD[1], &c->d_grad, &c->d_gn, &c->d_adjn,
                     &c->d_Xre, &c->d_Xim, &c->d_bin0, &c->d_pnode, &c->d_acc0_re, &c->d_acc0_im,

@@ -244,6 +244,8 @@ int src_amp_launch(const SrcDev* srcs, int nsrc, double* amp, int stride, int ns
 int fold_launch(const FoldArgs& a, cudaStream_t st);
 int advance_launch(long long* n_done, long long by, cudaStream_t st);
 int convert_launch(int prec, int to_double, const void* src, void* dst, long long n, cudaStream_t st);
+int capture_launch(int prec, int which, const InstDev* inst, int i, Tables tb, const void* B, const void* D,
+                   long long z0, long long zs, long long m, long long n, int half, void* out, cudaStream_t st);
 int derived_launch(int prec, int which, const InstDev* inst, int i, Tables tb, const void* B,
                    const void* D, double* out, int nz, long long n_done, cudaStream_t st);
 

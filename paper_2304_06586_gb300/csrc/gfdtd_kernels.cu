@@ -247,8 +247,8 @@ int convert_launch(int prec, int to_double, const void* src, void* dst, long lon
 // Derived fields of one instance at the state (B^n, D^{n+1/2}), in FP64:
 // which 2 = E (level n+1/2), 3 = H (level n, moving perturbation), 4 = E*.
 template <bool MATTER, typename T>
-__device__ void derived_cell(int which, const InstDev& I, const Tables& tb, const T* Bi,
-                             const T* Di, double* out, long long n, int k) {
+__device__ double derived_value(int which, const InstDev& I, const Tables& tb, const T* Bi, const T* Di,
+                                long long n, int k) {
   using R = typename Real<T>::type;
   auto ld = [&](const T* p, int j) -> double {
     return (j >= 0 && j < I.nz) ? (double)(R)p[j] : 0.0;
@@ -256,15 +256,20 @@ __device__ void derived_cell(int which, const InstDev& I, const Tables& tb, cons
   if (which == 3) {
     double sm, cb;
     node_coef<MATTER, false>(I, tb, I.dq * (2 * n) - HALF_CELL, k, sm, cb);
-    out[k] = ld(Bi, k) * sm / I.S;
-    return;
+    return ld(Bi, k) * sm / I.S;
   }
   double se, cb;
   node_coef<MATTER, true>(I, tb, I.dq * (2 * n + 1), k, se, cb);
   const bool pos = (I.flags & F_POS) != 0;
   const double bbar = pos ? 0.5 * (ld(Bi, k - 1) + ld(Bi, k - 2)) : 0.5 * (ld(Bi, k) + ld(Bi, k + 1));
   const double estar = (se * ld(Di, k) - 2.0 * cb * bbar) / I.S;
-  out[k] = which == 4 ? estar : estar + I.beta * bbar;
+  return which == 4 ? estar : estar + I.beta * bbar;
+}
+
+template <bool MATTER, typename T>
+__device__ void derived_cell(int which, const InstDev& I, const Tables& tb, const T* Bi,
+                             const T* Di, double* out, long long n, int k) {
+  out[k] = derived_value<MATTER, T>(which, I, tb, Bi, Di, n, k);
 }
 
 template <typename T>
@@ -292,6 +297,55 @@ int derived_launch(int prec, int which, const InstDev* inst, int i, Tables tb, c
     case 2: return derived_t<__nv_bfloat16>(which, inst, i, tb, B, D, out, nz, n, st);
     case 3: return derived_t<__half>(which, inst, i, tb, B, D, out, nz, n, st);
     case 4: return derived_t<double>(which, inst, i, tb, B, D, out, nz, n, st);
+  }
+  return (int)cudaErrorInvalidValue;
+}
+
+// ------------------------------------------------------------ space-time capture
+//
+// One frame: field `which` (0 D, 1 B, 2 E, 3 H, 4 E*) of instance i at the
+// state (B^n, D^{n+1/2}), at cells z0 + j zs, j < m, stored as FP32 or FP16.
+
+__device__ __forceinline__ void store_frame(float* o, long long j, double v) { o[j] = (float)v; }
+__device__ __forceinline__ void store_frame(__half* o, long long j, double v) { o[j] = __double2half(v); }
+
+template <typename T, typename O>
+__global__ void capture_kernel(int which, const InstDev* inst, int i, Tables tb, const T* B, const T* D,
+                               long long z0, long long zs, long long m, long long n, O* out) {
+  using R = typename Real<T>::type;
+  const long long j = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= m) return;
+  const InstDev I = inst[i];
+  const int k = (int)(z0 + j * zs);
+  double v;
+  if (which == 0) v = (double)(R)D[I.off + k];
+  else if (which == 1) v = (double)(R)B[I.off + k];
+  else if (I.flags & F_MATTER) v = derived_value<true, T>(which, I, tb, B + I.off, D + I.off, n, k);
+  else v = derived_value<false, T>(which, I, tb, B + I.off, D + I.off, n, k);
+  store_frame(out, j, v);
+}
+
+template <typename T>
+static int capture_t(int which, const InstDev* inst, int i, Tables tb, const void* B, const void* D,
+                     long long z0, long long zs, long long m, long long n, int half, void* out,
+                     cudaStream_t st) {
+  const unsigned grid = (unsigned)((m + 255) / 256);
+  if (half)
+    capture_kernel<T, __half><<<grid, 256, 0, st>>>(which, inst, i, tb, (const T*)B, (const T*)D, z0, zs, m, n,
+                                                    (__half*)out);
+  else
+    capture_kernel<T, float><<<grid, 256, 0, st>>>(which, inst, i, tb, (const T*)B, (const T*)D, z0, zs, m, n,
+                                                   (float*)out);
+  return (int)cudaGetLastError();
+}
+
+int capture_launch(int prec, int which, const InstDev* inst, int i, Tables tb, const void* B, const void* D,
+                   long long z0, long long zs, long long m, long long n, int half, void* out, cudaStream_t st) {
+  switch (prec) {
+    case 0: case 1: return capture_t<float>(which, inst, i, tb, B, D, z0, zs, m, n, half, out, st);
+    case 2: return capture_t<__nv_bfloat16>(which, inst, i, tb, B, D, z0, zs, m, n, half, out, st);
+    case 3: return capture_t<__half>(which, inst, i, tb, B, D, z0, zs, m, n, half, out, st);
+    case 4: return capture_t<double>(which, inst, i, tb, B, D, z0, zs, m, n, half, out, st);
   }
   return (int)cudaErrorInvalidValue;
 }
