@@ -21,7 +21,8 @@ _dp = C.POINTER(C.c_double)
 class _Problem(C.Structure):
     _fields_ = [("kind", C.c_int32), ("interp", C.c_int32), ("n", C.c_int32),
                 ("reserved", C.c_int32), ("z", _dp), ("eps", _dp), ("mu", _dp),
-                ("beta", C.c_double), ("S", C.c_double), ("nz", C.c_int64)]
+                ("beta", C.c_double), ("S", C.c_double), ("nz", C.c_int64),
+                ("absorb_width", C.c_int64), ("absorb_sigma", C.c_double)]
 
 
 class _Source(C.Structure):
@@ -89,6 +90,12 @@ class Instance:
         self.n_done = 0
         self.sources = []
         self.probes = []
+        self.absorb_width, self.absorb_sigma = 0, 0.0
+
+    def set_absorber(self, width, sigma):
+        """Graded absorbing layers of `width` cells at both ends (0: none); see the C header."""
+        self.absorb_width, self.absorb_sigma = int(width), float(sigma)
+        return self
 
     def add_source(self, node, omega0, tau, t0, amp=1.0):
         self.sources.append((int(node), float(omega0), float(tau), float(t0), float(amp)))
@@ -102,7 +109,7 @@ class Instance:
 
     def _problem(self):
         return _Problem(self.kind, self.interp, len(self.eps), 0, _ptr(self.z), _ptr(self.eps),
-                        _ptr(self.mu), self.beta, self.S, self.nz)
+                        _ptr(self.mu), self.beta, self.S, self.nz, self.absorb_width, self.absorb_sigma)
 
     def run(self, n_steps, record=False):
         """Advance ``n_steps`` leapfrog steps in FP64."""

@@ -55,6 +55,12 @@
  *   Source (Eq. spectrum_incident, real carrier): after the D update of step n,
  *     D_ks += amp * sin(w0 (t - t0)) * exp(-((t - t0)/tau)^2),  t = (n + 1/2) S.
  *
+ *   Absorbing layers (the paper is silent on domain ends; an option of this
+ *   library, not of the paper): with width W > 0, a field sample at position
+ *   x (D_k at x = k, B_k at x = k + 1/2) is multiplied right after its update
+ *   by g(x) = exp(-sigma d(x)^2), d = (W - x)/W for x < W, d = (x - (nz-1-W))/W
+ *   for x > nz-1-W, else 0; the source is added after the D damping.
+ *
  *   Probes: F = E at the probe node at level n+1/2 (moving perturbation:
  *   E = D/eps exactly, Eq. const_1d; moving matter: E = E* + beta * Bbar with
  *   E* from the relation above and Bbar the Table 1 average of B^n), and for
@@ -77,6 +83,8 @@ typedef struct {
     double beta;         /* v / c */
     double S;            /* Courant number dt/dz */
     int64_t nz;          /* cells */
+    int64_t absorb_width;  /* cells of the graded absorbing layer at each end (0: none) */
+    double absorb_sigma;   /* its strength at the outer end */
 } orc_problem;
 
 typedef struct {
@@ -161,6 +169,18 @@ static double hstar(int kind, double beta, double e, double m, double b, double 
     return g * e / den * b - beta * g / den * dbar;
 }
 
+/* ---- absorbing layers ------------------------------------------------------ */
+
+/* damping factor of a field sample at position x (cells) */
+static double absorb_factor(const orc_problem* p, double x)
+{
+    const double W = (double)p->absorb_width;
+    double d = 0.0;
+    if (x < W) d = (W - x) / W;
+    else if (x > (double)(p->nz - 1) - W) d = (x - ((double)(p->nz - 1) - W)) / W;
+    return exp(-p->absorb_sigma * d * d);
+}
+
 /* ---- the time loop ------------------------------------------------------- */
 
 int orc_run(const orc_problem* p, int n_src, const orc_source* src,
@@ -206,6 +226,8 @@ int orc_run(const orc_problem* p, int n_src, const orc_source* src,
             double dB = pos ? Bo[k] - at(Bo, k - 1, nz) : at(Bo, k + 1, nz) - Bo[k];
             B[k] = Bo[k] - S * (at(Es, k + 1, nz) - Es[k]) - beta * S * dB;
         }
+        if (p->absorb_width > 0)
+            for (int64_t k = 0; k < nz; ++k) B[k] *= absorb_factor(p, (double)k + 0.5);
 
         /* H*^n (Eq. Bconst_discr with Table 1 Da/Db, D at level n-1/2) */
         for (int64_t k = 0; k < nz; ++k) {
@@ -220,6 +242,8 @@ int orc_run(const orc_problem* p, int n_src, const orc_source* src,
             double dD = pos ? Do[k] - at(Do, k - 1, nz) : at(Do, k + 1, nz) - Do[k];
             D[k] = Do[k] - S * (Hs[k] - at(Hs, k - 1, nz)) - beta * S * dD;
         }
+        if (p->absorb_width > 0)
+            for (int64_t k = 0; k < nz; ++k) D[k] *= absorb_factor(p, (double)k);
 
         /* soft source at t_{n+1/2} */
         const double t = (double)(2 * n + 1) * S * 0.5;
@@ -289,7 +313,7 @@ int orc_step_transpose(const orc_problem* p, int64_t n, const double* aBn, const
     const int64_t nz = p->nz;
     const double beta = p->beta, S = p->S;
     const int pos = beta >= 0.0;
-    if (p->kind != 0) return -1;
+    if (p->kind != 0 || p->absorb_width > 0) return -1;   /* no transpose of the absorber here */
     int nb = p->interp == 0 ? p->n - 1 : p->n;
     int64_t* zq = (int64_t*)malloc(sizeof(int64_t) * (size_t)(nb > 0 ? nb : 1));
     for (int i = 0; i < nb; ++i) zq[i] = to_fixed(p->z[i]);
@@ -377,7 +401,7 @@ int orc_adjoint(const orc_problem* p, int n_src, const orc_source* src, const or
 {
     const int64_t nz = p->nz;
     const double S = p->S;
-    if (p->kind != 0 || n_steps < 1) return -1;
+    if (p->kind != 0 || p->absorb_width > 0 || n_steps < 1) return -1;
     double* Dh = (double*)malloc(sizeof(double) * (size_t)nz * (size_t)(n_steps + 1));
     double* B = (double*)malloc(sizeof(double) * (size_t)nz);
     double* series = (double*)malloc(sizeof(double) * (size_t)n_steps);
