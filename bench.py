@@ -387,6 +387,25 @@ def main():
                        "frames": nfr, "cells_per_frame": wl.instances[big].nz, "field": "E, FP16",
                        "t_stride": tb, "relative_to_value": (cells * T / (cms / 1e3) / 1e9) / (value / world)}
 
+        # absorbing layers (64 cells at both ends of every instance): throughput of the same step
+        absorber = None
+        if not args.no_sweeps:
+            for k in range(len(wl.instances)):
+                sim.set_absorber(k, 64, 0.2)
+            sim.step(T)                    # rebuilds the tiling, warms the new graphs
+            a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            barrier()
+            a0.record(stream)
+            sim.step(T)
+            a1.record(stream)
+            barrier()
+            ams = a0.elapsed_time(a1)
+            av = cells * T / (ams / 1e3) / 1e9
+            absorber = {"value": av, "unit": "Gcell-updates/s", "width": 64, "sigma": 0.2,
+                        "relative_to_value": av / (value / world)}
+            for k in range(len(wl.instances)):
+                sim.set_absorber(k, 0, 0.0)
+
         # plain kernel (one step, one instance per launch) on a few steps
         plain = None
         if args.plain_steps > 0:
@@ -416,7 +435,7 @@ def main():
                        "l2": "inputs larger than L2 (%.2f GB of fields)" % (cells * 16 / 1e9),
                        "parallelism": "instances sharded per rank" if world > 1 else "1 GPU"},
             "e2e": e2e, "gpu_launches": launches, "roofline": roofline, "plain": plain,
-            "clocks": clocks, "sweeps": sweeps, "capture": capture}
+            "clocks": clocks, "sweeps": sweeps, "capture": capture, "absorber": absorber}
     if not args.no_cpu:
         line["cpu_baseline"] = cpu_baseline(wl)
     print(json.dumps(line), flush=True)

@@ -70,6 +70,7 @@ SIGNATURES = {
     "gfdtd_adjoint": (C.c_int, [C.c_void_p, C.c_int64, C.c_int, C.c_int, C.c_int, _dp, _dp]),
     "gfdtd_set_tuning": (C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_int]),
     "gfdtd_get_stats": (C.c_int, [C.c_void_p, C.POINTER(Stats)]),
+    "gfdtd_set_absorber": (C.c_int, [C.c_void_p, C.c_int, C.c_int64, C.c_double]),
     "gfdtd_set_capture": (C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_int64, C.c_int64, C.c_int64, C.c_int64,
                                     C.c_int64, C.c_int]),
     "gfdtd_capture_info": (C.c_int, [C.c_void_p, _i64p, _i64p, _i64p]),
@@ -342,6 +343,10 @@ class Simulation:
         s = Stats()
         self._check(self._L.gfdtd_get_stats(self._h, C.byref(s)), "get_stats")
         return {k: getattr(s, k) for k, _ in Stats._fields_}
+
+    def set_absorber(self, inst, width=64, sigma=0.2):
+        """Graded absorbing layers of `width` cells at both ends of instance inst (0: none)."""
+        self._check(self._L.gfdtd_set_absorber(self._h, inst, int(width), float(sigma)), "set_absorber")
 
     def set_capture(self, inst, which, z0, z1, z_stride=1, t_stride=1, max_frames=1024, half=False):
         """Record field `which` of instance inst at cells z0:z1:z_stride after every

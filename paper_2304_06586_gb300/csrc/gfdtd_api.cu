@@ -52,6 +52,8 @@ struct Medium {
   double beta = 0.0;
   gfdtd_interp interp = GFDTD_LAYERS;
   std::vector<double> z, eps{1.0}, mu{1.0};
+  long long absorb_width = 0;     // absorbing layers at both ends (0: none)
+  double absorb_sigma = 0.0;
 };
 
 struct Probe {
@@ -274,7 +276,7 @@ static gfdtd_status build_tiles(gfdtd_ctx* c, int C, int TB, std::vector<int2> o
       // right end.  Tiles at both ends, or whose window would not cover the
       // output range, stay with the general kernel.
       int edge = 0;
-      bool fast_tile = fast_ok && !(left && right);
+      bool fast_tile = fast_ok && !(left && right) && !window_absorbs(d, base, span);
       if (fast_tile && left) {
         base = 0;
         edge = 1;
@@ -400,6 +402,8 @@ static gfdtd_status finalize(gfdtd_ctx* c) {
     d.c32 = (float)d.c;
     d.cb32 = (float)d.cb;
     d.sm32 = 0.0f;
+    d.abs_w = (int)m.absorb_width;
+    d.abs_sigma = m.absorb_sigma;
     int flags = 0;
     if (m.beta >= 0.0) flags |= F_POS;
     if (m.kind == GFDTD_MATTER) flags |= F_MATTER;
@@ -697,6 +701,8 @@ extern "C" gfdtd_status gfdtd_adjoint(gfdtd_ctx* c, int64_t n_steps, int probe_i
   for (int i = 0; i < c->n_inst; ++i) {
     if (c->media[i].kind != GFDTD_PERTURBATION)
       return fail(c, GFDTD_E_UNSUPPORTED, "the adjoint is built for moving perturbation");
+    if (c->media[i].absorb_width > 0)
+      return fail(c, GFDTD_E_UNSUPPORTED, "the adjoint has no absorbing layers");
     if (probe_id < 0 || probe_id >= (int)c->inst_probes[i].size())
       return fail(c, GFDTD_E_ARG, "instance %d has no probe %d", i, probe_id);
     if ((int)c->probes[c->inst_probes[i][probe_id]].omega.size() < bin_hi)
@@ -969,6 +975,17 @@ gfdtd_status gfdtd_set_medium(gfdtd_ctx* c, int inst, gfdtd_kind kind, double be
   m.z.assign(z ? z : eps_r, (z ? z : eps_r) + (z ? nz_pos : 0));
   m.eps.assign(eps_r, eps_r + n);
   m.mu.assign(mu_r, mu_r + n);
+  c->dirty = true;
+  return GFDTD_OK;
+}
+
+gfdtd_status gfdtd_set_absorber(gfdtd_ctx* c, int inst, int64_t width, double sigma) {
+  gfdtd_status s = check_inst(c, inst);
+  if (s) return s;
+  if (width < 0 || 2 * width >= c->nz[inst] || !(sigma >= 0.0) || !std::isfinite(sigma))
+    return fail(c, GFDTD_E_ARG, "need 0 <= width, 2 width < nz and a finite sigma >= 0");
+  c->media[inst].absorb_width = width;
+  c->media[inst].absorb_sigma = sigma;
   c->dirty = true;
   return GFDTD_OK;
 }

@@ -129,6 +129,24 @@ __device__ __forceinline__ int node_of(long long zq, long long off) {
   return (int)((zq + off + 0xFFFFFFFFLL) >> 32);
 }
 
+// Graded absorbing layers of width W = I.abs_w at both domain ends (an option
+// of this library; the paper is silent on the ends): a field sample at
+// position x (D_k: x = k, B_k: x = k + 1/2) is multiplied right after its
+// update by exp(-sigma d^2), d = (W - x) / W left of W, (x - (nz - 1 - W)) / W
+// right of nz - 1 - W, else 0.
+template <typename R>
+__device__ __forceinline__ R absorb_factor(const InstDev& I, R x) {
+  const R W = (R)I.abs_w, right = (R)(I.nz - 1) - W;
+  R d = 0;
+  if (x < W) d = (W - x) / W;
+  else if (x > right) d = (x - right) / W;
+  return exp(-(R)I.abs_sigma * d * d);
+}
+// Whether the window [base, base + span) reaches an absorbing layer.
+__host__ __device__ inline bool window_absorbs(const InstDev& I, long long base, long long span) {
+  return I.abs_w > 0 && (base < I.abs_w + 1 || base + span > I.nz - 2 - I.abs_w);
+}
+
 // Number of profile positions b in [0, nb) with node_of(zq[b]) <= k (binary search).
 __device__ __forceinline__ int count_at_or_left(const long long* __restrict__ zq, int nb,
                                                 long long off, int k) {
@@ -287,6 +305,7 @@ __device__ __forceinline__ void run_tile(const BlockArgs<T>& A, const InstDev& I
   }
 
   const R a = (R)I.a, cc = (R)I.c;
+  const bool damp = window_absorbs(I, base, 32 * C);   // the tile reaches an absorbing layer
   const bool eps_const = (I.flags & F_EPS_CONST) != 0;
   const bool mu_const = (I.flags & F_MU_CONST) != 0;
   const long long dq = I.dq;
@@ -374,6 +393,15 @@ __device__ __forceinline__ void run_tile(const BlockArgs<T>& A, const InstDev& I
       }
     }
 
+    if (damp) {   // absorbing layers: B^n at x = k + 1/2
+#pragma unroll
+      for (int c = 0; c < C; ++c) {
+        const R g = absorb_factor<R>(I, (R)(k0 + c) + (R)0.5);
+        B[c] *= g;
+        if constexpr (KAHAN) cBv[c] *= g;
+      }
+    }
+
     // ---- H'^n = sm B - cb (D_j + D_{j+1})  (D at level n-1/2, material at level n)
     const R dr = __shfl_down_sync(FULL, D[0], 1);
     {
@@ -414,6 +442,14 @@ __device__ __forceinline__ void run_tile(const BlockArgs<T>& A, const InstDev& I
           else D[c] = a * D[c] + (cc * du + (hp - X[c]));
           if (EDGE) D[c] = ((unsigned)(k0 + c) < (unsigned)nz) ? D[c] : (R)0;
         }
+      }
+    }
+    if (damp) {   // absorbing layers: D^{n+1/2} at x = k
+#pragma unroll
+      for (int c = 0; c < C; ++c) {
+        const R g = absorb_factor<R>(I, (R)(k0 + c));
+        D[c] *= g;
+        if constexpr (KAHAN) cDv[c] *= g;
       }
     }
 

@@ -39,6 +39,9 @@ struct InstDev {
   float a32, c32, cb32;   // a, c, cb rounded to FP32 (the FP32-arithmetic kernels read these)
   float sm32;              // S / mu of layer 0 (half nodes) in FP32: the uniform value when F_MU_CONST
   int pad0, pad1;
+  double abs_sigma;        // absorbing layers at both ends: strength at the outer end
+  int abs_w;               // their width in cells (0: none)
+  int pad2;
 };
 static_assert(sizeof(InstDev) % 16 == 0, "InstDev is copied by TMA in 16-byte units");
 

@@ -80,10 +80,11 @@ __device__ void plain_cell(const PlainArgs<T>& A, const InstDev& I, int k) {
     const R bs = pos ? ld(Bi, j - 1) + ld(Bi, j - 2) : ld(Bi, j) + ld(Bi, j + 1);
     return se * ld(Di, j) - cb * bs;
   };
-  auto Bn = [&](int j) -> R {   // B^n at half node j
+  auto Bn = [&](int j) -> R {   // B^n at half node j (after the absorbing layers' damping)
     if (j < 0 || j >= nz) return (R)0;
     const R bu = pos ? ld(Bi, j - 1) : ld(Bi, j + 1);
-    return a * ld(Bi, j) + (cc * bu + (Ep(j) - Ep(j + 1)));
+    const R b = a * ld(Bi, j) + (cc * bu + (Ep(j) - Ep(j + 1)));
+    return I.abs_w > 0 ? b * absorb_factor<R>(I, (R)j + (R)0.5) : b;
   };
   auto Hp = [&](int j, R bn) -> R {   // H' at half node j, level n
     if (j < 0 || j >= nz) return (R)0;
@@ -94,6 +95,7 @@ __device__ void plain_cell(const PlainArgs<T>& A, const InstDev& I, int k) {
   const R bk = Bn(k), bkm = Bn(k - 1);
   const R du = pos ? ld(Di, k - 1) : ld(Di, k + 1);
   R d = a * ld(Di, k) + (cc * du + (Hp(k - 1, bkm) - Hp(k, bk)));
+  if (I.abs_w > 0) d *= absorb_factor<R>(I, (R)k);
   const double t = (double)(2 * n + 1) * I.S * 0.5;
   for (int q = 0; q < I.nsrc; ++q) {
     const SrcDev sd = A.srcs[I.src0 + q];
