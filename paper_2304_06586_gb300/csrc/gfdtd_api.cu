@@ -110,6 +110,7 @@ struct gfdtd_ctx {
   bool tuned = false;
   int n_tiles[3] = {0, 0, 0};           // [general perturbation, general matter, fast interior]
   long long valid_cells[3] = {0, 0, 0}; // exact output cells of each list's tiles per step
+  int n_fast_damped = 0;                // the last ones of the fast list reach absorbing layers
   int grid[3] = {0, 0, 0};
   int num_sms = 0;
 
@@ -256,8 +257,8 @@ static std::vector<float2> to_f32(const std::vector<double2>& v) {
 // same time execute the same code.
 static gfdtd_status build_tiles(gfdtd_ctx* c, int C, int TB, std::vector<int2> out[3],
                                 std::vector<FastTile>& fast) {
-  std::vector<int2> part[3][2];
-  std::vector<FastTile> fpart[2];
+  std::vector<int2> part[3][2], pdamp[2];
+  std::vector<FastTile> fpart[2], fdamp[2];   // fast tiles; those that reach an absorbing layer
   for (int v = 0; v < 3; ++v) c->valid_cells[v] = 0;
   for (int i = 0; i < c->n_inst; ++i) {
     const InstDev& d = c->h_inst[i];
@@ -276,7 +277,8 @@ static gfdtd_status build_tiles(gfdtd_ctx* c, int C, int TB, std::vector<int2> o
       // right end.  Tiles at both ends, or whose window would not cover the
       // output range, stay with the general kernel.
       int edge = 0;
-      bool fast_tile = fast_ok && !(left && right) && !window_absorbs(d, base, span);
+      bool fast_tile = fast_ok && !(left && right);
+      const bool damped = window_absorbs(d, base, span);
       if (fast_tile && left) {
         base = 0;
         edge = 1;
@@ -288,7 +290,7 @@ static gfdtd_status build_tiles(gfdtd_ctx* c, int C, int TB, std::vector<int2> o
         if (base < 0 || base + L > x0 || base + span - nz > C - 2) fast_tile = false;
       }
       const int v = matter ? 1 : (fast_tile ? 2 : 0);
-      part[v][pos ? 0 : 1].push_back(make_int2(i, (int)x0));
+      (v == 2 && damped ? pdamp[pos ? 0 : 1] : part[v][pos ? 0 : 1]).push_back(make_int2(i, (int)x0));
       c->valid_cells[v] += std::min<long long>(W, nz - x0);
       if (v == 2) {
         FastTile f{};
@@ -305,7 +307,7 @@ static gfdtd_status build_tiles(gfdtd_ctx* c, int C, int TB, std::vector<int2> o
           const long long node = c->probes[prb[q]].node;
           if (node >= x0 && node < x0 + W && node < c->nz[i]) f.pmask |= 1u << q;
         }
-        fpart[pos ? 0 : 1].push_back(f);
+        (damped ? fdamp : fpart)[pos ? 0 : 1].push_back(f);
       }
     }
   }
@@ -313,8 +315,13 @@ static gfdtd_status build_tiles(gfdtd_ctx* c, int C, int TB, std::vector<int2> o
     out[v] = part[v][0];
     out[v].insert(out[v].end(), part[v][1].begin(), part[v][1].end());
   }
+  // the fast list ends with the tiles that reach an absorbing layer (their own launch)
+  out[2].insert(out[2].end(), pdamp[0].begin(), pdamp[0].end());
+  out[2].insert(out[2].end(), pdamp[1].begin(), pdamp[1].end());
   fast = fpart[0];
   fast.insert(fast.end(), fpart[1].begin(), fpart[1].end());
+  for (int k = 0; k < 2; ++k) fast.insert(fast.end(), fdamp[k].begin(), fdamp[k].end());
+  c->n_fast_damped = (int)(fdamp[0].size() + fdamp[1].size());
   if (out[0].size() + out[1].size() + out[2].size() > (size_t)INT32_MAX)
     return fail(c, GFDTD_E_ARG, "too many tiles");
   return GFDTD_OK;
@@ -529,6 +536,23 @@ static gfdtd_status enqueue_block(gfdtd_ctx* c, cudaStream_t st, int from, int s
     a.s0 = s0;
     a.nsteps = nsteps;
     a.record = record ? 1 : 0;
+    if (k == 2 && c->n_fast_damped > 0) {
+      // the tiles that reach an absorbing layer, at the end of the list, get their own launch
+      const int nd = c->n_fast_damped, nn = c->n_tiles[2] - nd;
+      if (nn > 0) {
+        a.n_tiles = nn;
+        CKI(c, block_launch(c->prec, 2, c->C, c->TB, c->MB, &a, std::min(c->grid[2], (nn + 3) / 4), kBlock, st));
+        ++c->launches;
+      }
+      BlockArgs<float> d = a;
+      d.tiles = a.tiles + nn;
+      d.ftiles = a.ftiles + nn;
+      d.track = a.track ? a.track + nn : nullptr;
+      d.n_tiles = nd;
+      CKI(c, block_launch(c->prec, 3, c->C, c->TB, c->MB, &d, std::min(c->grid[2], (nd + 3) / 4), kBlock, st));
+      ++c->launches;
+      continue;
+    }
     CKI(c, block_launch(c->prec, k, c->C, c->TB, c->MB, &a, c->grid[k], kBlock, st));
     ++c->launches;
   }
@@ -596,7 +620,8 @@ static gfdtd_status run_chunk(gfdtd_ctx* c, int nsteps) {
     it = c->graphs.emplace(key, ex).first;
   }
   CK(c, cudaGraphLaunch(it->second, c->stream));
-  const int kinds = (c->n_tiles[0] > 0) + (c->n_tiles[1] > 0) + (c->n_tiles[2] > 0);
+  const int kinds = (c->n_tiles[0] > 0) + (c->n_tiles[1] > 0) + (c->n_tiles[2] > c->n_fast_damped) +
+                    (c->n_fast_damped > 0);
   c->launches += (long long)m * kinds + (c->n_src > 0) + (c->n_bins > 0) + 1;
   if (m & 1) c->cur = 1 - c->cur;
   c->n_done += nsteps;

@@ -669,7 +669,9 @@ __device__ __forceinline__ void fast_d_update(const R (&B)[C], R (&D)[C], R a, R
 // sB, sD: the tile's 32 C cells of B and D, and sT: the tracker state saved
 // for the tile by the previous launch (NULL: none kept), all in shared memory.
 // refill() is called once every lane has read them: it may overwrite them.
-template <int C, int TB, bool POS, typename T, typename Refill>
+// DAMP: the tile reaches an absorbing layer (a separate instantiation, so that
+// the damping adds nothing to the loops of the other tiles).
+template <int C, int TB, bool POS, typename T, bool DAMP, typename Refill>
 __device__ __forceinline__ void run_tile_fast(const BlockArgs<T>& A, const InstDev& I, const FastTile& ft,
                                               long long n0, const T* sB, const T* sD,
                                               const TrackTile* sT, int t, Refill&& refill) {
@@ -760,7 +762,7 @@ __device__ __forceinline__ void run_tile_fast(const BlockArgs<T>& A, const InstD
     const int c1b = (int)((tr.dnext + span + 0xFFFFFFFFLL) >> 32);   // last step
     const bool no_event = POS ? tr.dprev + span + dq2 <= 0 : tr.dnext + span + dq2 > 0;
     const bool one_side = POS ? (c1a >= C || c1b <= 0) : (c1a <= 0 || c1b >= C);
-    quiet = __all_sync(FULL, (smask | pmask) == 0u && ft.edge == 0 && no_event && one_side);
+    quiet = !DAMP && __all_sync(FULL, (smask | pmask) == 0u && ft.edge == 0 && no_event && one_side);
   }
   if (quiet) {
     const int c1 = (int)((tr.dnext + 0xFFFFFFFFLL) >> 32);
@@ -792,6 +794,21 @@ __device__ __forceinline__ void run_tile_fast(const BlockArgs<T>& A, const InstD
     zero_past_end(B);
     zero_past_end(D);
   }
+  // absorbing layers: each sample is multiplied after its update (x = k for D,
+  // k + 1/2 for B; B is carried as (S/mu) B, which the factor leaves
+  // proportional).  The layer's parameters are re-read from the instance
+  // record in global memory at each use, so no register stays reserved for them.
+  const InstDev* __restrict__ gI = A.inst + ft.inst;
+  auto damp_cells = [gI, k0](R (&X)[C], R half) {
+    const R aw = (R)__ldg(&gI->abs_w), aright = (R)(__ldg(&gI->nz) - 1) - aw, ainv = (R)1 / aw;
+    const R asig = (R)__ldg(&gI->abs_sigma);
+#pragma unroll
+    for (int c = 0; c < C; ++c) {
+      const R x = (R)(k0 + c) + half;
+      const R d = x < aw ? (aw - x) * ainv : (x > aright ? (x - aright) * ainv : (R)0);
+      X[c] *= exp(-asig * d * d);
+    }
+  };
   for (int s = 0; s < A.nsteps; ++s) {
     // ---- material at level n-1/2 for this lane's cells: c >= c1 lies beyond the next boundary
     const int c1 = (int)((tr.dnext + 0xFFFFFFFFLL) >> 32);
@@ -825,12 +842,14 @@ __device__ __forceinline__ void run_tile_fast(const BlockArgs<T>& A, const InstD
       }
       zero_past_end(B);
     }
+    if constexpr (DAMP) damp_cells(B, (R)0.5);
     const R d0 = D[0];                   // left end: D_0 at level n-1/2
 
     // ---- D^{n+1/2}
     fast_d_update<C, POS>(B, D, a, bD1, bD2, zl, zr);
     if (ledge && zl) D[0] += cb * d0;
     if (redge) zero_past_end(D);
+    if constexpr (DAMP) damp_cells(D, (R)0);
 
     // ---- soft sources at t_{n+1/2}
     for (unsigned m = smask; m; m &= m - 1) {
@@ -937,7 +956,7 @@ __global__ void __launch_bounds__(128) block_kernel(const BlockArgs<T> A) {
 // tile's cells in registers, bulk copies start bringing the next tile's
 // cells, instance record, tile record and saved tracker state into it, and
 // they land while the warp steps the current tile.
-template <int C, int TB, typename T, int MB>
+template <int C, int TB, typename T, int MB, bool DAMP = false>
 __global__ void __launch_bounds__(128, MB) fast_kernel(const BlockArgs<T> A) {
   constexpr int WPB = 4;                    // warps per block (blockDim.x == 128)
   constexpr int CELLS = 32 * C;
@@ -1003,8 +1022,10 @@ __global__ void __launch_bounds__(128, MB) fast_kernel(const BlockArgs<T> A) {
       prefetch(tn);
       fetch_record(tn + nw);
     };
-    if (I.flags & F_POS) run_tile_fast<C, TB, true>(A, I, ft, n0, sbuf[wib][0], sbuf[wib][1], sT, t, refill);
-    else run_tile_fast<C, TB, false>(A, I, ft, n0, sbuf[wib][0], sbuf[wib][1], sT, t, refill);
+    if (I.flags & F_POS)
+      run_tile_fast<C, TB, true, T, DAMP>(A, I, ft, n0, sbuf[wib][0], sbuf[wib][1], sT, t, refill);
+    else
+      run_tile_fast<C, TB, false, T, DAMP>(A, I, ft, n0, sbuf[wib][0], sbuf[wib][1], sT, t, refill);
   }
 }
 
@@ -1013,6 +1034,7 @@ template <int C, int TB, typename T, bool KAHAN = false, int MB = 4>
 int launch_block_shape(int variant, const void* args, int grid, int block, cudaStream_t st) {
   const BlockArgs<T>& a = *static_cast<const BlockArgs<T>*>(args);
   if (variant == 2 && !KAHAN) fast_kernel<C, TB, T, MB><<<grid, block, 0, st>>>(a);
+  else if (variant == 3 && !KAHAN) fast_kernel<C, TB, T, MB, true><<<grid, block, 0, st>>>(a);
   else if (variant == 1) block_kernel<C, TB, true, T, KAHAN><<<grid, block, 0, st>>>(a);
   else if (variant == 0) block_kernel<C, TB, false, T, KAHAN><<<grid, block, 0, st>>>(a);
   else return (int)cudaErrorInvalidValue;
@@ -1027,6 +1049,10 @@ int occupancy_block_shape(int variant, int block, int* nb) {
                                                cudaFuncAttributePreferredSharedMemoryCarveout,
                                                (int)cudaSharedmemCarveoutMaxShared);
     if (e != cudaSuccess) return (int)e;
+    const cudaError_t e3 = cudaFuncSetAttribute(fast_kernel<C, TB, T, MB, true>,
+                                                cudaFuncAttributePreferredSharedMemoryCarveout,
+                                                (int)cudaSharedmemCarveoutMaxShared);
+    if (e3 != cudaSuccess) return (int)e3;
     return (int)cudaOccupancyMaxActiveBlocksPerMultiprocessor(nb, fast_kernel<C, TB, T, MB>, block, 0);
   }
   if (variant == 1)

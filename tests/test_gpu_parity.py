@@ -17,7 +17,7 @@ from paper_2304_06586_gb300 import workloads as w
 pytestmark = pytest.mark.gpu
 
 TOL32 = 1e-4
-SHAPES = [(16, 8), (16, 16), (16, 24), (16, 32), (8, 16), (16, 16, 5), (24, 16), (24, 24)]
+SHAPES = [(16, 16), (16, 24), (8, 16), (16, 16, 5), (24, 16), (24, 24)]
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -139,7 +139,7 @@ def test_deterministic_and_chunking_independent():
     wl = _mixed_workload(seed=10)
     res = {}
     for shape, parts in (((16, 16), [1500]), ((16, 16), [1500]), ((16, 16), [700, 3, 797]),
-                         ((16, 8), [1500]), ((8, 16), [1024, 476])):
+                         ((24, 24), [1500]), ((8, 16), [1024, 476])):
         sim = make_sim(wl, tuning=shape)
         rng = np.random.default_rng(3)
         for k, I in enumerate(wl.instances):
@@ -153,7 +153,7 @@ def test_deterministic_and_chunking_independent():
     first, again = res[((16, 16), (1500,))]
     for a, b in zip(first, again):
         np.testing.assert_array_equal(a, b)
-    for key in (((16, 16), (700, 3, 797)), ((16, 8), (1500,)), ((8, 16), (1024, 476))):
+    for key in (((16, 16), (700, 3, 797)), ((24, 24), (1500,)), ((8, 16), (1024, 476))):
         for a, b in zip(first, res[key][0]):
             assert rel_l2(b, a) <= 1e-5
 
