@@ -62,8 +62,8 @@ __device__ __forceinline__ cd cexpi(double phi) {   // exp(i phi)
 // const_3d).  The result is the largest eigenvalue modulus of G over the
 // samples theta_j = pi (j + 1) / n_theta.
 
-__device__ double max_zeta_at(double S, double beta, double ie, double im, double bc, double theta) {
-  const cd h = cexpi(0.5 * theta);                   // e^{+i theta/2}
+// h = e^{+i theta / 2} of the sample.
+__device__ double max_zeta_at(double S, double beta, double ie, double im, double bc, cd h) {
   const cd w = h * h;                                // e^{+i theta}
   const cd h3 = h * w;                               // e^{+3i theta/2}
   cd bsum, adv;
@@ -109,10 +109,18 @@ __global__ void stability_map_kernel(int64_t n, const double* __restrict__ S, co
       im = g * e / den;
       bc = b * g / den;
     }
+    // e^{i theta_j / 2} advances by e^{i 16 pi / n_theta} from one sample of the
+    // lane to the next; it is recomputed from the angle every 16 samples, which
+    // keeps the accumulated rounding near 1e-15.
+    const double half_step = 3.14159265358979323846 / (double)n_theta * 0.5;   // theta / 2 per j
+    const cd rot = cexpi(32.0 * half_step);
     double worst = 0.0;
-    for (int j = lane; j < n_theta; j += 32) {
-      const double theta = 3.14159265358979323846 * (double)(j + 1) / (double)n_theta;
-      worst = fmax(worst, max_zeta_at(s, b, ie, im, bc, theta));
+    cd h = mk(1.0, 0.0);
+    int k = 0;
+    for (int j = lane; j < n_theta; j += 32, ++k) {
+      if ((k & 15) == 0) h = cexpi((double)(j + 1) * half_step);
+      else h = h * rot;
+      worst = fmax(worst, max_zeta_at(s, b, ie, im, bc, h));
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) worst = fmax(worst, __shfl_xor_sync(0xffffffffu, worst, o));
