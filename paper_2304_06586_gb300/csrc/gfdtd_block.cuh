@@ -966,7 +966,9 @@ __global__ void __launch_bounds__(128, MB) fast_kernel(const BlockArgs<T> A) {
   __shared__ __align__(16) FastTile sft[WPB];
   __shared__ __align__(16) TrackTile strk[WPB];
   __shared__ __align__(8) unsigned long long sbar[WPB];
-  const int wib = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  // (the warp index taken by shuffle is known to the compiler to be warp-uniform,
+  // which lets it keep the tile bookkeeping out of the per-lane registers)
+  const int wib = __shfl_sync(0xffffffffu, (int)(threadIdx.x >> 5), 0), lane = threadIdx.x & 31;
   const int gw = blockIdx.x * WPB + wib;
   const int nw = gridDim.x * WPB;
   const long long n0 = *A.n_done + A.s0;
