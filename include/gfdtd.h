@@ -223,9 +223,9 @@ gfdtd_status gfdtd_adjoint(gfdtd_ctx* ctx, int64_t n_steps, int probe_id, int bi
 gfdtd_status gfdtd_stability(double S, double beta, double eps_r, double mu_r,
                              gfdtd_kind kind, double* max_abs_zeta);
 
-/* Tile shape of the batched kernel: cells per lane (8, 16 or 24), steps per
- * time block (8 to 24) and the number of 128-thread blocks per SM the fast
- * kernel's registers are limited to (4 or 5; 0 = first built match).  The
+/* Tile shape of the batched kernel: cells per lane (8 to 24), steps per time
+ * block (8 to 32) and the number of 128-thread blocks per SM the fast
+ * kernel's registers are limited to (4 to 8; 0 = first built match).  The
  * shapes built depend on the precision; E_UNSUPPORTED if the shape is not
  * built.  0, 0, 0 selects autotuning at the next step. */
 gfdtd_status gfdtd_set_tuning(gfdtd_ctx* ctx, int cells_per_lane, int time_block, int blocks_per_sm);

@@ -61,7 +61,7 @@ def _compare(wl, sim, orcs, spectra=True):
                 assert e <= TOL32, (k, "probe", p, e)
 
 
-@pytest.mark.parametrize("tuning", [None, (16, 16, 5), (24, 24, 4), (8, 16)])
+@pytest.mark.parametrize("tuning", [None, (16, 24, 8), (24, 24, 6), (8, 16)])
 @pytest.mark.parametrize("kind", [w.PERTURBATION, w.MATTER])
 def test_absorber_random_fields(tuning, kind):
     wl, layers = _workload(kind)

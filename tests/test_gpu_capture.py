@@ -10,7 +10,7 @@ from paper_2304_06586_gb300 import workloads as w
 
 pytestmark = pytest.mark.gpu
 
-TUNING = (16, 16, 5)
+TUNING = (20, 24, 7)
 
 
 @pytest.fixture(scope="module", autouse=True)

@@ -17,7 +17,7 @@ from paper_2304_06586_gb300 import workloads as w
 pytestmark = pytest.mark.gpu
 
 TOL32 = 1e-4
-SHAPES = [(16, 16), (16, 24), (8, 16), (16, 16, 5), (24, 16), (24, 24)]
+SHAPES = [(16, 16), (8, 16), (16, 24, 8), (20, 16), (20, 24), (20, 32), (24, 24)]
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -204,7 +204,7 @@ def test_precision_tiers(prec, tol):
     print("precision tier", prec, "worst relative L2", worst)
 
 
-@pytest.mark.parametrize("tuning", [None, (16, 16, 5), (24, 24, 4)])
+@pytest.mark.parametrize("tuning", [None, (20, 24, 7), (24, 24, 6)])
 def test_crystal_small_matches_oracle(tuning):
     """Config-3 shape at reduced size (stable velocities), from rest, sources and probes."""
     wl = w.config3(n_inst=48, nz_lo=1 << 10, nz_hi=1 << 13, n_steps=600, stable_only=True)
@@ -335,8 +335,8 @@ def test_profile_kernels_matches_step_and_covers_every_cell():
     fields and spectra, and its per-kernel cell-updates add up to every cell
     of every instance once per step."""
     wl = w.config3(n_inst=24, nz_lo=1 << 10, nz_hi=1 << 13, n_steps=0, stable_only=True)
-    a = make_sim(wl, allow_unstable=False, tuning=(16, 16, 5))
-    b = make_sim(wl, allow_unstable=False, tuning=(16, 16, 5))
+    a = make_sim(wl, allow_unstable=False, tuning=(20, 24, 7))
+    b = make_sim(wl, allow_unstable=False, tuning=(20, 24, 7))
     n = 1100                       # more than one chunk, ragged last time block
     a.step(n)
     t = b.profile_kernels(n)
@@ -349,7 +349,7 @@ def test_profile_kernels_matches_step_and_covers_every_cell():
     assert a.steps_done() == b.steps_done() == n
 
 
-@pytest.mark.parametrize("tuning", [(24, 24, 4), (24, 16, 4)])
+@pytest.mark.parametrize("tuning", [(24, 24, 6), (20, 16, 7)])
 def test_two_boundaries_per_lane_run(tuning):
     """Layers of 14-30 cells under 24-cell lane runs: runs hold two boundaries
     at a time and boundaries pass lane starts in both directions, with sources
