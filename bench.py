@@ -32,7 +32,7 @@ FLOPS_PER_CELL_UPDATE = 20        # FP32 operations of one B and D update (E*, B
 SM_COUNT, FP32_LANES_PER_SM, SM_MAX_MHZ = 152, 128, 2070.0
 
 
-KERNEL_SOURCES = ("gfdtd_block.cuh", "gfdtd_internal.cuh", "gfdtd_block_f32.cu")
+KERNEL_SOURCES = ("gfdtd_block.cuh", "gfdtd_internal.cuh", "gfdtd_block_f32.cu", "gfdtd_block_f32w.cu")
 
 
 def kernel_source_hash():

@@ -6,7 +6,7 @@
 
 namespace gfdtd {
 
-#define GFDTD_SHAPES(X) X(16,16,4) X(8,16,4)
+#define GFDTD_SHAPES(X) X(16,16,4) X(8,16,4) X(16,24,8) X(24,24,6)
 
 int block_launch_f16(int variant, int C, int TB, int MB, const void* a, int grid, int block,
                         cudaStream_t st) {

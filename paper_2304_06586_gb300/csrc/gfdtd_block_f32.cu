@@ -1,12 +1,13 @@
 // gfdtd_block_f32.cu -- instantiations of the batched time-block kernels for
-// FP32 field storage.  One translation unit per precision so they compile in parallel.
+// FP32 field storage with up to 16 cells per lane (gfdtd_block_f32w.cu has the
+// wider shapes).  One or two translation units per precision so they compile in parallel.
 // A shape is (cells per lane, steps per time block, blocks per SM that the
 // fast kernel's registers are limited to).
 #include "gfdtd_block.cuh"
 
 namespace gfdtd {
 
-#define GFDTD_SHAPES(X) X(8,16,4) X(16,16,4) X(16,24,8) X(20,16,7) X(20,24,7) X(20,32,7) X(24,24,6)
+#define GFDTD_SHAPES(X) X(8,16,4) X(16,16,4) X(16,24,8)
 
 int block_launch_f32(int variant, int C, int TB, int MB, const void* a, int grid, int block,
                         cudaStream_t st) {

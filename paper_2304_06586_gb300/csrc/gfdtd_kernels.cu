@@ -5,16 +5,19 @@
 namespace gfdtd {
 
 int block_launch_f32(int, int, int, int, const void*, int, int, cudaStream_t);
+int block_launch_f32w(int, int, int, int, const void*, int, int, cudaStream_t);
 int block_launch_bf16(int, int, int, int, const void*, int, int, cudaStream_t);
 int block_launch_f16(int, int, int, int, const void*, int, int, cudaStream_t);
 int block_launch_f64(int, int, int, int, const void*, int, int, cudaStream_t);
 int block_launch_f32k(int, int, int, int, const void*, int, int, cudaStream_t);
 int block_occupancy_f32(int, int, int, int, int, int*);
+int block_occupancy_f32w(int, int, int, int, int, int*);
 int block_occupancy_bf16(int, int, int, int, int, int*);
 int block_occupancy_f16(int, int, int, int, int, int*);
 int block_occupancy_f64(int, int, int, int, int, int*);
 int block_occupancy_f32k(int, int, int, int, int, int*);
 int block_shapes_f32(int*, int*, int*, int);
+int block_shapes_f32w(int*, int*, int*, int);
 int block_shapes_bf16(int*, int*, int*, int);
 int block_shapes_f16(int*, int*, int*, int);
 int block_shapes_f64(int*, int*, int*, int);
@@ -24,7 +27,8 @@ int block_shapes_f32k(int*, int*, int*, int);
 int block_launch(int prec, int variant, int C, int TB, int MB, const void* args, int grid, int block,
                  cudaStream_t st) {
   switch (prec) {
-    case 0: return block_launch_f32(variant, C, TB, MB, args, grid, block, st);
+    case 0: return C <= 16 ? block_launch_f32(variant, C, TB, MB, args, grid, block, st)
+                           : block_launch_f32w(variant, C, TB, MB, args, grid, block, st);
     case 1: return block_launch_f32k(variant, C, TB, MB, args, grid, block, st);
     case 2: return block_launch_bf16(variant, C, TB, MB, args, grid, block, st);
     case 3: return block_launch_f16(variant, C, TB, MB, args, grid, block, st);
@@ -35,7 +39,8 @@ int block_launch(int prec, int variant, int C, int TB, int MB, const void* args,
 
 int block_occupancy(int prec, int variant, int C, int TB, int MB, int block, int* nb) {
   switch (prec) {
-    case 0: return block_occupancy_f32(variant, C, TB, MB, block, nb);
+    case 0: return C <= 16 ? block_occupancy_f32(variant, C, TB, MB, block, nb)
+                           : block_occupancy_f32w(variant, C, TB, MB, block, nb);
     case 1: return block_occupancy_f32k(variant, C, TB, MB, block, nb);
     case 2: return block_occupancy_bf16(variant, C, TB, MB, block, nb);
     case 3: return block_occupancy_f16(variant, C, TB, MB, block, nb);
@@ -46,7 +51,10 @@ int block_occupancy(int prec, int variant, int C, int TB, int MB, int block, int
 
 int block_shapes(int prec, int* C, int* TB, int* MB, int max) {
   switch (prec) {
-    case 0: return block_shapes_f32(C, TB, MB, max);
+    case 0: {
+      const int n = block_shapes_f32(C, TB, MB, max);
+      return n + block_shapes_f32w(C + n, TB + n, MB + n, max - n);
+    }
     case 1: return block_shapes_f32k(C, TB, MB, max);
     case 2: return block_shapes_bf16(C, TB, MB, max);
     case 3: return block_shapes_f16(C, TB, MB, max);
