@@ -147,6 +147,42 @@ def sweep_measurements(torch, gb, stream, reps=3):
     return out
 
 
+def adjoint_measurement(gb):
+    """The adjoint workload (256 x 2^14 piecewise-linear profiles, 16000 steps):
+    wall time of gfdtd_adjoint (forward, sqrt(T) checkpoints, reverse sweep and
+    FP64 gradients, host results) against gfdtd_step over the same steps."""
+    import torch
+    from paper_2304_06586_gb300 import workloads as w
+    wl = w.config5()
+    T = wl.n_steps
+    cells = sum(i.nz for i in wl.instances)
+
+    def make():
+        sim = gb.Simulation([i.nz for i in wl.instances], wl.S, gb.F32)
+        configure(sim, wl, gb)
+        return sim
+
+    f = make()
+    f.step(64)                      # tiling, graphs
+    f.synchronize()
+    t0 = time.perf_counter()
+    f.step(T)
+    f.synchronize()
+    tf = time.perf_counter() - t0
+    f.close()
+    a = make()
+    nv = [len(i.eps) for i in wl.instances]
+    a.adjoint(64, 0, 0, 16, nv)     # warm-up
+    t0 = time.perf_counter()
+    loss, _ = a.adjoint(T, 0, 0, 16, nv)
+    ta = time.perf_counter() - t0
+    a.close()
+    torch.cuda.synchronize()
+    return {"value": cells * T / ta / 1e9, "unit": "Gcell-updates/s (forward steps covered per second)",
+            "seconds": ta, "forward_seconds": tf, "adjoint_over_forward": ta / tf,
+            "config": wl.description, "loss_finite": bool(np.all(np.isfinite(loss)))}
+
+
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -244,7 +280,7 @@ def configure(sim, wl, gb):
             sim.add_probe(k, p[0], p[1])
 
 
-def cpu_baseline(wl, n_inst=32, n_steps=100, seed=1):
+def cpu_baseline(wl, n_inst=32, n_steps=100, seed=1, single_core=False):
     """The FP64 oracle, as it stands, on a bounded sample of the workload."""
     import oracle
     rng = np.random.default_rng(seed)
@@ -263,9 +299,16 @@ def cpu_baseline(wl, n_inst=32, n_steps=100, seed=1):
     oracle.run_many(orcs, n_steps, threads=threads)
     dt = time.perf_counter() - t0
     cu = sum(o.nz for o in orcs) * n_steps
-    return {"value": cu / dt / 1e9, "unit": "Gcell-updates/s", "cores": threads, "kind": "oracle",
-            "sample": "%d of %d instances x %d steps (%.3g cell-updates, %.1f s)"
-                      % (len(orcs), len(wl.instances), n_steps, cu, dt)}
+    out = {"value": cu / dt / 1e9, "unit": "Gcell-updates/s", "cores": threads, "kind": "oracle",
+           "sample": "%d of %d instances x %d steps (%.3g cell-updates, %.1f s)"
+                     % (len(orcs), len(wl.instances), n_steps, cu, dt)}
+    if single_core:   # the same instances on one core, a quarter of the steps
+        n1 = max(1, n_steps // 4)
+        t1 = time.perf_counter()
+        oracle.run_many(orcs, n1, threads=1)
+        out["single_core"] = sum(o.nz for o in orcs) * n1 / (time.perf_counter() - t1) / 1e9
+        out["sample"] += "; one core: %d steps" % n1
+    return out
 
 
 def run_reference(args, wl, rank):
@@ -422,6 +465,7 @@ def main():
                      "batched_over_plain": value / world / pv}
         sim.close()
         sweeps = None if args.no_sweeps else sweep_measurements(torch, gb, stream)
+        adjoint = None if args.no_sweeps else adjoint_measurement(gb)
 
     if rank != 0:
         return
@@ -435,9 +479,9 @@ def main():
                        "l2": "inputs larger than L2 (%.2f GB of fields)" % (cells * 16 / 1e9),
                        "parallelism": "instances sharded per rank" if world > 1 else "1 GPU"},
             "e2e": e2e, "gpu_launches": launches, "roofline": roofline, "plain": plain,
-            "clocks": clocks, "sweeps": sweeps, "capture": capture, "absorber": absorber}
+            "clocks": clocks, "sweeps": sweeps, "capture": capture, "absorber": absorber, "adjoint": adjoint}
     if not args.no_cpu:
-        line["cpu_baseline"] = cpu_baseline(wl)
+        line["cpu_baseline"] = cpu_baseline(wl, single_core=True)
     print(json.dumps(line), flush=True)
     if pg:
         pg.destroy_process_group()

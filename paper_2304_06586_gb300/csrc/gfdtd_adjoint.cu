@@ -23,26 +23,28 @@ namespace gfdtd {
 
 
 // Weights of eps at moving coordinate xi on the profile values: (i0, w0), (i1, w1).
+template <typename W>
 __device__ __forceinline__ void eps_weights(const InstDev& I, const long long* zq, long long xi,
-                                            int& i0, double& w0, int& i1, double& w1) {
+                                            int& i0, W& w0, int& i1, W& w1) {
   if (!(I.flags & F_LINEAR)) {
     int lo = 0, hi = I.n - 1;                 // count of boundaries <= xi
     while (lo < hi) { const int mid = (lo + hi) >> 1; if (__ldg(zq + mid) <= xi) lo = mid + 1; else hi = mid; }
-    i0 = lo; w0 = 1.0; i1 = lo; w1 = 0.0;
+    i0 = lo; w0 = 1; i1 = lo; w1 = 0;
     return;
   }
   const int n = I.n;
-  if (xi <= __ldg(zq)) { i0 = i1 = 0; w0 = 1.0; w1 = 0.0; return; }
-  if (xi >= __ldg(zq + n - 1)) { i0 = i1 = n - 1; w0 = 1.0; w1 = 0.0; return; }
+  if (xi <= __ldg(zq)) { i0 = i1 = 0; w0 = 1; w1 = 0; return; }
+  if (xi >= __ldg(zq + n - 1)) { i0 = i1 = n - 1; w0 = 1; w1 = 0; return; }
   int lo = 0, hi = n;                         // last knot <= xi
   while (hi - lo > 1) { const int mid = (lo + hi) >> 1; if (__ldg(zq + mid) <= xi) lo = mid; else hi = mid; }
-  const double w = (double)(xi - __ldg(zq + lo)) / (double)(__ldg(zq + lo + 1) - __ldg(zq + lo));
-  i0 = lo; w0 = 1.0 - w; i1 = lo + 1; w1 = w;
+  const W w = (W)(xi - __ldg(zq + lo)) / (W)(__ldg(zq + lo + 1) - __ldg(zq + lo));
+  i0 = lo; w0 = (W)1 - w; i1 = lo + 1; w1 = w;
 }
 
 // Sum v over the lanes of the warp that share `key` (keys are non-decreasing
-// across lanes) and add the sum once, from the segment's first lane.
-__device__ __forceinline__ void segmented_atomic_add(double* base, int key, double v, bool active) {
+// across lanes); returns whether this lane is its segment's first, which then
+// holds the sum.
+__device__ __forceinline__ bool segment_sum(int& key, double& v, bool active) {
   const int lane = threadIdx.x & 31;
   if (!active) key = -1 - lane;               // inactive lanes form singleton segments
   for (int o = 1; o < 32; o <<= 1) {
@@ -51,56 +53,98 @@ __device__ __forceinline__ void segmented_atomic_add(double* base, int key, doub
     if (lane + o < 32 && tk == key) v += t;
   }
   const int prev = __shfl_up_sync(FULL, key, 1);
-  if (active && (lane == 0 || prev != key) && v != 0.0) atomicAdd(base + key, v);
+  return active && (lane == 0 || prev != key) && v != 0.0;
 }
 
-__global__ void __launch_bounds__(256) adjoint_step_kernel(const AdjArgs A) {
+constexpr int kAdjCells = 256;   // cells per block (one per thread)
+constexpr int kAdjKeys = 512;    // profile values one block can reduce in shared memory
+
+// One block transposes the step for 256 consecutive cells of one instance, in
+// FP32 like the forward step; the permittivity gradient is summed per warp
+// segment, then per block in shared memory, and added to the FP64 gradient
+// with one atomic per profile value per block.
+__global__ void __launch_bounds__(kAdjCells) adjoint_step_kernel(const AdjArgs A) {
+  __shared__ float s_lb[kAdjCells + 8], s_ld[kAdjCells + 8];   // cells x0 - 2 .. x0 + 259
+  __shared__ double s_g[kAdjKeys];
+  __shared__ int s_key[2];
   const int2 tl = A.tiles[blockIdx.x];
   const InstDev I = A.inst[tl.x];
-  const int k = tl.y + threadIdx.x;
-  const int nz = I.nz;
+  const int x0 = tl.y, nz = I.nz, tid = threadIdx.x;
+  const float* __restrict__ lBn = A.lBn + I.off;
+  const float* __restrict__ lDn = A.lDn + I.off;
+  for (int i = tid; i < kAdjCells + 6; i += kAdjCells) {
+    const int j = x0 - 2 + i;
+    const bool in = j >= 0 && j < nz;
+    s_lb[i] = in ? lBn[j] : 0.0f;
+    s_ld[i] = in ? lDn[j] : 0.0f;
+  }
+  for (int i = tid; i < kAdjKeys; i += kAdjCells) s_g[i] = 0.0;
+  const int k = x0 + tid;
   const bool valid = k < nz;
-  const float* lBn = A.lBn + I.off;
-  const float* lDn = A.lDn + I.off;
-  auto lb = [&](int j) -> double { return (j >= 0 && j < nz) ? (double)lBn[j] : 0.0; };
-  auto ld = [&](int j) -> double { return (j >= 0 && j < nz) ? (double)lDn[j] : 0.0; };
   const bool pos = (I.flags & F_POS) != 0;
-  const double a = I.a, c = I.c, cb = I.cb, S = I.S;
+  const float a = I.a32, c = I.c32, cb = I.cb32;
   const long long n = A.n;
-  const long long offH = I.dq * (2 * n) - HALF_CELL;
+  const long long offH = I.dq * (2 * n) - HALF_CELL, offE = I.dq * (2 * n - 1);
   const bool mu_const = (I.flags & F_MU_CONST) != 0;
-  const double sm0 = __ldg(A.tb.tabH + I.tab).x;
-  auto sm = [&](int j) -> double {
-    if (mu_const) return sm0;
-    double x, y;
+  auto in = [&](int j) { return j >= 0 && j < nz; };
+  auto LB = [&](int j) -> float { return s_lb[j - x0 + 2]; };   // zero outside [0, nz)
+  auto LD = [&](int j) -> float { return s_ld[j - x0 + 2]; };
+  auto sm = [&](int j) -> float {
+    if (mu_const) return I.sm32;
+    float x, y;
     node_coef<false, false>(I, A.tb, offH, j, x, y);
     return x;
   };
-  auto lH = [&](int j) -> double { return (j >= 0 && j < nz) ? ld(j + 1) - ld(j) : 0.0; };
-  auto lBt = [&](int j) -> double { return (j >= 0 && j < nz) ? lb(j) + sm(j) * lH(j) : 0.0; };
-  auto lE = [&](int j) -> double { return (j >= 0 && j < nz) ? lBt(j) - lBt(j - 1) : 0.0; };
+  auto lH = [&](int j) -> float { return in(j) ? LD(j + 1) - LD(j) : 0.0f; };
+  auto lBt = [&](int j) -> float { return in(j) ? LB(j) + sm(j) * lH(j) : 0.0f; };
+  __syncthreads();
 
-  int gkey0 = 0, gkey1 = 0;
-  double gval0 = 0.0, gval1 = 0.0;
+  int key0 = 0, key1 = 0;
+  double g0 = 0.0, g1 = 0.0;
   if (valid) {
-    const long long offE = I.dq * (2 * n - 1);
-    double se, cbx;
+    float se, cbx;
     node_coef<false, true>(I, A.tb, offE, k, se, cbx);
-    const double lEk = lE(k);
-    const double lDk = a * ld(k) + c * ld(pos ? k + 1 : k - 1) - cb * (lH(k) + lH(k - 1)) + se * lEk;
-    const double lBk = a * lBt(k) + c * lBt(pos ? k + 1 : k - 1)
-                     - cb * (pos ? lE(k + 1) + lE(k + 2) : lE(k) + lE(k - 1));
-    A.lD[I.off + k] = (float)lDk;
-    A.lB[I.off + k] = (float)lBk;
-    const double gE = lEk * (-se * se * (double)A.Dold[I.off + k] / S);
-    double w0, w1;
-    eps_weights(I, A.tb.zq + I.tab, ((long long)k << 32) - offE, gkey0, w0, gkey1, w1);
-    gval0 = gE * w0;
-    gval1 = gE * w1;
+    float lDk, lBk, lEk;
+    if (pos) {
+      const float tm1 = lBt(k - 1), t0 = lBt(k), t1 = lBt(k + 1), t2 = lBt(k + 2);
+      lEk = t0 - tm1;
+      const float lE1 = in(k + 1) ? t1 - t0 : 0.0f, lE2 = in(k + 2) ? t2 - t1 : 0.0f;
+      lDk = a * LD(k) + c * LD(k + 1) - cb * (lH(k) + lH(k - 1)) + se * lEk;
+      lBk = a * t0 + c * t1 - cb * (lE1 + lE2);
+    } else {
+      const float tm2 = lBt(k - 2), tm1 = lBt(k - 1), t0 = lBt(k);
+      lEk = t0 - tm1;
+      const float lEm1 = in(k - 1) ? tm1 - tm2 : 0.0f;
+      lDk = a * LD(k) + c * LD(k - 1) - cb * (lH(k) + lH(k - 1)) + se * lEk;
+      lBk = a * t0 + c * tm1 - cb * (lEk + lEm1);
+    }
+    A.lD[I.off + k] = lDk;
+    A.lB[I.off + k] = lBk;
+    // dL/deps_k = lE_k (-S D_k / eps_k^2) = lE_k (-se^2 D_k / S)
+    const float gE = lEk * (-se * se * A.Dold[I.off + k] * (float)I.inv_S);
+    float w0, w1;
+    eps_weights(I, A.tb.zq + I.tab, ((long long)k << 32) - offE, key0, w0, key1, w1);
+    g0 = (double)(gE * w0);
+    g1 = (double)(gE * w1);
+    if (tid == 0) s_key[0] = key0;
+    if (tid == kAdjCells - 1 || k + 1 == nz) s_key[1] = key1;   // keys grow with k
   }
-  double* g = A.grad + I.tab;
-  segmented_atomic_add(g, gkey0, gval0, valid);
-  segmented_atomic_add(g, gkey1, gval1, valid && (I.flags & F_LINEAR));
+  __syncthreads();
+  double* grad = A.grad + I.tab;
+  const int kmin = s_key[0], span = s_key[1] - kmin + 1;
+  const bool lin = (I.flags & F_LINEAR) != 0;
+  const bool h0 = segment_sum(key0, g0, valid);
+  const bool h1 = segment_sum(key1, g1, valid && lin);
+  if (span <= kAdjKeys) {
+    if (h0) atomicAdd(&s_g[key0 - kmin], g0);
+    if (h1) atomicAdd(&s_g[key1 - kmin], g1);
+    __syncthreads();
+    for (int i = tid; i < span; i += kAdjCells)
+      if (s_g[i] != 0.0) atomicAdd(grad + kmin + i, s_g[i]);
+  } else {
+    if (h0) atomicAdd(grad + key0, g0);
+    if (h1) atomicAdd(grad + key1, g1);
+  }
 }
 
 // The probe term of step n: F_n = D^{n+1/2}_p se_p / S = D_p / eps_p (level

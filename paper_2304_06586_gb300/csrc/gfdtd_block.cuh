@@ -713,7 +713,7 @@ __device__ __forceinline__ void run_tile_fast(const BlockArgs<T>& A, const InstD
   // the state the previous launch left for this tile if it ended at n0, else
   // found by binary search.
   constexpr int NB = fast_boundaries_per_run(C);
-  BoundaryTrack tr;
+  BoundaryTrack tr{};
   R vL, vM = 0, vR;      // sm se of the layers: k0's, past dnext (NB = 2: up to dnext2), past the last tracked
   auto load_layers = [&]() {
     vL = sm * __ldg(tv + tr.bnext).x;
