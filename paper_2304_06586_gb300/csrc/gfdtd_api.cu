@@ -533,6 +533,8 @@ static gfdtd_status enqueue_block(gfdtd_ctx* c, cudaStream_t st, int from, int s
     a.err = (int*)((char*)c->d_ndone.p + 8);
     a.ftiles = k == 2 ? (const FastTile*)c->d_ftiles.p : nullptr;
     a.track = (k == 2 && record) ? (TrackTile*)c->d_track.p : nullptr;   // tuning trials leave it alone
+    a.dseg = nullptr;
+    a.dseg_stride = 0;
     a.s0 = s0;
     a.nsteps = nsteps;
     a.record = record ? 1 : 0;
@@ -682,13 +684,14 @@ static gfdtd_status check_inst(gfdtd_ctx* c, int inst) {
 }
 
 
-// One forward step of every instance with explicit buffers: reads (Bin, Din),
-// writes (Bout, Dout); the step taken is *n_done + s0 + 1.  Used by the
-// adjoint's segment recomputation (plain FP32 kernels, no probe samples).
-static gfdtd_status enqueue_one_step(gfdtd_ctx* c, const void* Bin, const void* Din, void* Bout,
-                                     void* Dout, const long long* n_done, int s0) {
-  const int prec = c->prec == GFDTD_F32_KAHAN ? GFDTD_F32 : c->prec;
-  for (int k = 0; k < 3; ++k) {
+// Up to one time block of forward steps for the adjoint's segment recomputation:
+// reads (Bin, dseg slice s0), writes Bout and D after every step into dseg
+// slices s0 + 1 .. s0 + nsteps (the last one is also the block's D output).
+// Every tile, the fast kernel's included, runs in the general FP32 kernel,
+// whose per-step D store the reverse sweep needs.
+static gfdtd_status enqueue_segment_block(gfdtd_ctx* c, const void* Bin, void* Bout, char* dseg, size_t fb,
+                                          const long long* n_done, int s0, int nsteps) {
+  for (int k : {0, 2}) {
     if (c->n_tiles[k] == 0) continue;
     BlockArgs<float> a{};
     a.inst = (const InstDev*)c->d_inst.p;
@@ -701,16 +704,18 @@ static gfdtd_status enqueue_one_step(gfdtd_ctx* c, const void* Bin, const void* 
     a.samples = (double*)c->d_samples.p;
     a.chunk_stride = kChunk;
     a.Bin = (const float*)Bin;
-    a.Din = (const float*)Din;
+    a.Din = (const float*)(dseg + (size_t)s0 * fb);
     a.Bout = (float*)Bout;
-    a.Dout = (float*)Dout;
+    a.Dout = (float*)(dseg + (size_t)(s0 + nsteps) * fb);
     a.n_done = n_done;
     a.err = (int*)((char*)c->d_ndone.p + 8);
     a.s0 = s0;
-    a.nsteps = 1;
+    a.nsteps = nsteps;
     a.record = 0;
-    a.ftiles = k == 2 ? (const FastTile*)c->d_ftiles.p : nullptr;
-    CKI(c, block_launch(prec, k, c->C, c->TB, c->MB, &a, c->grid[k], kBlock, c->stream));
+    a.dseg = (float*)dseg;
+    a.dseg_stride = (long long)(fb / sizeof(float));
+    const int grid = std::min(c->grid[0] > 0 ? c->grid[0] : c->num_sms, (a.n_tiles + 3) / 4);
+    CKI(c, block_launch(GFDTD_F32, 0, c->C, c->TB, c->MB, &a, std::max(grid, 1), kBlock, c->stream));
     ++c->launches;
   }
   return GFDTD_OK;
@@ -819,10 +824,9 @@ extern "C" gfdtd_status gfdtd_adjoint(gfdtd_ctx* c, int64_t n_steps, int probe_i
     if (c->n_src > 0)
       CKI(c, src_amp_launch((const SrcDev*)c->d_srcs.p, c->n_src, (double*)c->d_amp.p, kChunk, Ks,
                             (const long long*)c->d_adjn.p, c->S, st));
-    for (int m = 1; m <= Ks; ++m) {
-      if ((s = enqueue_one_step(c, c->d_wB[(m - 1) & 1].p, (char*)c->d_dseg.p + (m - 1) * fb,
-                                c->d_wB[m & 1].p, (char*)c->d_dseg.p + m * fb,
-                                (const long long*)c->d_adjn.p, m - 1)))
+    for (int m0 = 0, w = 0; m0 < Ks; m0 += c->TB, w ^= 1) {
+      if ((s = enqueue_segment_block(c, c->d_wB[w].p, c->d_wB[w ^ 1].p, (char*)c->d_dseg.p, fb,
+                                     (const long long*)c->d_adjn.p, m0, std::min(c->TB, Ks - m0))))
         return s;
     }
     SourceAdjArgs sa;

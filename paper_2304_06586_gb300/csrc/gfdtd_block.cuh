@@ -493,6 +493,11 @@ __device__ __forceinline__ void run_tile(const BlockArgs<T>& A, const InstDev& I
         A.samples[(long long)(I.prb0 + q) * A.chunk_stride + A.s0 + s] = (double)(F * (R)I.inv_S);
       }
     }
+
+    // ---- D^{n+1/2} of every step, for the adjoint's segment recomputation
+    if (A.dseg)
+      store_cells<T, R, C>(A.dseg + (long long)(A.s0 + s + 1) * A.dseg_stride + I.off, k0, x0,
+                           min(x0 + W, I.nz_pad), D);
   }
 
   const int hi = min(x0 + W, I.nz_pad);

@@ -155,6 +155,8 @@ struct BlockArgs {
   int* err;                   // device status word: bit 0 = a bounded wait gave up
   const FastTile* ftiles;     // fast kernel: its tiles (n_tiles records, same order as `tiles`)
   TrackTile* track;           // fast kernel: tracker state per tile, kept between launches; NULL: not kept
+  T* dseg;                    // general kernel: D after each step s goes to dseg + (s0 + s + 1) dseg_stride
+  long long dseg_stride;      // (NULL: not recorded)
 };
 
 // Arguments of the plain kernel (one instance, one step).
