@@ -16,6 +16,8 @@
 // permittivity enters through se = S/eps at level n-1/2:
 //   dL/deps_k += lE_k * (-S D_k^{n-1/2} / eps_k^2) = lE_k * (-se_k^2 D_k / S),
 // scattered onto the profile values with the interpolation weights.
+#include <climits>
+
 #include "gfdtd_block.cuh"
 
 namespace gfdtd {
@@ -41,109 +43,220 @@ __device__ __forceinline__ void eps_weights(const InstDev& I, const long long* z
   i0 = lo; w0 = (W)1 - w; i1 = lo + 1; w1 = w;
 }
 
-// Sum v over the lanes of the warp that share `key` (keys are non-decreasing
-// across lanes); returns whether this lane is its segment's first, which then
-// holds the sum.
-__device__ __forceinline__ bool segment_sum(int& key, double& v, bool active) {
-  const int lane = threadIdx.x & 31;
-  if (!active) key = -1 - lane;               // inactive lanes form singleton segments
-  for (int o = 1; o < 32; o <<= 1) {
-    const double t = __shfl_down_sync(FULL, v, o);
-    const int tk = __shfl_down_sync(FULL, key, o);
-    if (lane + o < 32 && tk == key) v += t;
+// Number of profile positions b in [0, np) with zq[b] <= xi, i.e. at or left
+// of the node whose moving coordinate is xi = k 2^32 - off (binary search;
+// cells beyond the first or last position take two loads).
+__device__ __forceinline__ int positions_at_or_left(const long long* __restrict__ zq, int np, long long xi) {
+  if (np == 0 || __ldg(zq) > xi) return 0;
+  if (__ldg(zq + np - 1) <= xi) return np;
+  int lo = 1, hi = np - 1;                    // zq[0] <= xi < zq[np - 1]
+  while (lo < hi) {
+    const int mid = (lo + hi) >> 1;
+    if (__ldg(zq + mid) <= xi) lo = mid + 1; else hi = mid;
   }
-  const int prev = __shfl_up_sync(FULL, key, 1);
-  return active && (lane == 0 || prev != key) && v != 0.0;
+  return lo;
 }
 
-constexpr int kAdjCells = 256;   // cells per block (one per thread)
-constexpr int kAdjKeys = 512;    // profile values one block can reduce in shared memory
+// The same count one cell further on, from the previous cell's count `idx`:
+// a short walk, else a fresh search.
+__device__ __forceinline__ int advance_positions(const long long* __restrict__ zq, int np, long long xi, int idx) {
+  for (int w = 0; w < 4; ++w) {
+    if (idx >= np || __ldg(zq + idx) > xi) return idx;
+    ++idx;
+  }
+  return positions_at_or_left(zq, np, xi);
+}
 
-// One block transposes the step for 256 consecutive cells of one instance, in
-// FP32 like the forward step; the permittivity gradient is summed per warp
-// segment, then per block in shared memory, and added to the FP64 gradient
-// with one atomic per profile value per block.
-__global__ void __launch_bounds__(kAdjCells) adjoint_step_kernel(const AdjArgs A) {
-  __shared__ float s_lb[kAdjCells + 8], s_ld[kAdjCells + 8];   // cells x0 - 2 .. x0 + 259
-  __shared__ double s_g[kAdjKeys];
+// A non-negative 64-bit integer as FP32 from its two 32-bit halves (two 32-bit
+// conversions and one FMA instead of a 64-bit conversion).
+__device__ __forceinline__ float i64_to_f32(long long x) {
+  return fmaf((float)(int)(x >> 32), 4294967296.0f, (float)(unsigned)x);
+}
+
+constexpr int kAdjThreads = 256;
+constexpr int kAdjCPT = 4;                           // consecutive cells per thread
+static_assert(kAdjThreads * kAdjCPT == kAdjTileCells, "adjoint tile size");
+constexpr int kAdjKeys = 1024;                       // profile values one block reduces in shared memory
+
+// One block transposes the step for kAdjTileCells consecutive cells of one
+// instance, four per thread, in FP32 like the forward step.  The material at
+// level n-1/2 comes from one position search per thread and a walk to its
+// next cells.  The permittivity gradient is merged per thread over equal
+// profile values (a warp of one value sums with shuffles), then per block in
+// shared memory, and added to the FP64 gradient with one atomic per profile
+// value per block.  FP64 arithmetic is kept out of the per-cell work: GB300's
+// FP64 pipe is narrow.
+__global__ void __launch_bounds__(kAdjThreads) adjoint_step_kernel(const AdjArgs A) {
+  // cells x0 - 2 .. x0 + kAdjTileCells + 5, zero outside [0, nz)
+  __shared__ __align__(16) float s_lb[kAdjTileCells + 8];
+  __shared__ __align__(16) float s_ld[kAdjTileCells + 8];
+  __shared__ float s_g[kAdjKeys];
   __shared__ int s_key[2];
   const int2 tl = A.tiles[blockIdx.x];
   const InstDev I = A.inst[tl.x];
   const int x0 = tl.y, nz = I.nz, tid = threadIdx.x;
   const float* __restrict__ lBn = A.lBn + I.off;
   const float* __restrict__ lDn = A.lDn + I.off;
-  for (int i = tid; i < kAdjCells + 6; i += kAdjCells) {
+  for (int i = tid; i < kAdjTileCells + 8; i += kAdjThreads) {
     const int j = x0 - 2 + i;
     const bool in = j >= 0 && j < nz;
     s_lb[i] = in ? lBn[j] : 0.0f;
     s_ld[i] = in ? lDn[j] : 0.0f;
   }
-  for (int i = tid; i < kAdjKeys; i += kAdjCells) s_g[i] = 0.0;
-  const int k = x0 + tid;
-  const bool valid = k < nz;
+  for (int i = tid; i < kAdjKeys; i += kAdjThreads) s_g[i] = 0.0f;
+  const int k0 = x0 + kAdjCPT * tid;
+  const int nvalid = max(0, min(kAdjCPT, nz - k0));
   const bool pos = (I.flags & F_POS) != 0;
-  const float a = I.a32, c = I.c32, cb = I.cb32;
+  const bool lin = (I.flags & F_LINEAR) != 0;
+  const float a = I.a32, c = I.c32, cb = I.cb32, inv_S = (float)I.inv_S, S32 = (float)I.S;
   const long long n = A.n;
   const long long offH = I.dq * (2 * n) - HALF_CELL, offE = I.dq * (2 * n - 1);
   const bool mu_const = (I.flags & F_MU_CONST) != 0;
-  auto in = [&](int j) { return j >= 0 && j < nz; };
-  auto LB = [&](int j) -> float { return s_lb[j - x0 + 2]; };   // zero outside [0, nz)
-  auto LD = [&](int j) -> float { return s_ld[j - x0 + 2]; };
-  auto sm = [&](int j) -> float {
-    if (mu_const) return I.sm32;
-    float x, y;
-    node_coef<false, false>(I, A.tb, offH, j, x, y);
-    return x;
-  };
-  auto lH = [&](int j) -> float { return in(j) ? LD(j + 1) - LD(j) : 0.0f; };
-  auto lBt = [&](int j) -> float { return in(j) ? LB(j) + sm(j) * lH(j) : 0.0f; };
   __syncthreads();
 
-  int key0 = 0, key1 = 0;
-  double g0 = 0.0, g1 = 0.0;
-  if (valid) {
-    float se, cbx;
-    node_coef<false, true>(I, A.tb, offE, k, se, cbx);
-    float lDk, lBk, lEk;
-    if (pos) {
-      const float tm1 = lBt(k - 1), t0 = lBt(k), t1 = lBt(k + 1), t2 = lBt(k + 2);
-      lEk = t0 - tm1;
-      const float lE1 = in(k + 1) ? t1 - t0 : 0.0f, lE2 = in(k + 2) ? t2 - t1 : 0.0f;
-      lDk = a * LD(k) + c * LD(k + 1) - cb * (lH(k) + lH(k - 1)) + se * lEk;
-      lBk = a * t0 + c * t1 - cb * (lE1 + lE2);
-    } else {
-      const float tm2 = lBt(k - 2), tm1 = lBt(k - 1), t0 = lBt(k);
-      lEk = t0 - tm1;
-      const float lEm1 = in(k - 1) ? tm1 - tm2 : 0.0f;
-      lDk = a * LD(k) + c * LD(k - 1) - cb * (lH(k) + lH(k - 1)) + se * lEk;
-      lBk = a * t0 + c * tm1 - cb * (lEk + lEm1);
+  int key0[kAdjCPT], key1[kAdjCPT];
+  float g0[kAdjCPT], g1[kAdjCPT];
+  if (nvalid > 0) {
+    // adjoint fields at cells k0 - 2 + q (LD up to q = 8)
+    float LB[8], LD[9];
+    {
+      const float4 b0 = *reinterpret_cast<const float4*>(s_lb + kAdjCPT * tid);
+      const float4 b1 = *reinterpret_cast<const float4*>(s_lb + kAdjCPT * tid + 4);
+      const float4 d0 = *reinterpret_cast<const float4*>(s_ld + kAdjCPT * tid);
+      const float4 d1 = *reinterpret_cast<const float4*>(s_ld + kAdjCPT * tid + 4);
+      LB[0] = b0.x; LB[1] = b0.y; LB[2] = b0.z; LB[3] = b0.w; LB[4] = b1.x; LB[5] = b1.y; LB[6] = b1.z; LB[7] = b1.w;
+      LD[0] = d0.x; LD[1] = d0.y; LD[2] = d0.z; LD[3] = d0.w; LD[4] = d1.x; LD[5] = d1.y; LD[6] = d1.z; LD[7] = d1.w;
+      LD[8] = s_ld[kAdjCPT * tid + 8];
     }
-    A.lD[I.off + k] = lDk;
-    A.lB[I.off + k] = lBk;
-    // dL/deps_k = lE_k (-S D_k / eps_k^2) = lE_k (-se^2 D_k / S)
-    const float gE = lEk * (-se * se * A.Dold[I.off + k] * (float)I.inv_S);
-    float w0, w1;
-    eps_weights(I, A.tb.zq + I.tab, ((long long)k << 32) - offE, key0, w0, key1, w1);
-    g0 = (double)(gE * w0);
-    g1 = (double)(gE * w1);
-    if (tid == 0) s_key[0] = key0;
-    if (tid == kAdjCells - 1 || k + 1 == nz) s_key[1] = key1;   // keys grow with k
+    // lH_j = lD'_{j+1} - lD'_j and lBt_j = lB'_j + sm_j lH_j for j = k0 - 2 + q
+    float lH[8], t[8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      const int j = k0 - 2 + q;
+      const bool in = j >= 0 && j < nz;
+      float sm = I.sm32;
+      if (!mu_const && in) {
+        float y;
+        node_coef<false, false>(I, A.tb, offH, j, sm, y);
+      }
+      lH[q] = in ? LD[q + 1] - LD[q] : 0.0f;
+      t[q] = in ? LB[q] + sm * lH[q] : 0.0f;
+    }
+    // material at level n-1/2 of the four cells
+    const long long* __restrict__ zq = A.tb.zq + I.tab;
+    const float2* __restrict__ tv = A.tb.tabE32 + I.tab;
+    const int np = lin ? I.n : I.n - 1;        // profile positions
+    long long xi = ((long long)k0 << 32) - offE;
+    int idx = positions_at_or_left(zq, np, xi);
+    float Dold[kAdjCPT];
+    {
+      const float4 d = *reinterpret_cast<const float4*>(A.Dold + I.off + k0);   // padded to 32 cells
+      Dold[0] = d.x; Dold[1] = d.y; Dold[2] = d.z; Dold[3] = d.w;
+    }
+    float oD[kAdjCPT], oB[kAdjCPT];
+#pragma unroll
+    for (int q = 0; q < kAdjCPT; ++q) {
+      if (q > 0) {
+        xi += 1LL << 32;
+        idx = advance_positions(zq, np, xi, idx);
+      }
+      float se, w1 = 0.0f;
+      if (lin) {
+        float e;
+        if (idx <= 0) { e = __ldg(tv).x; key0[q] = key1[q] = 0; }
+        else if (idx >= np) { e = __ldg(tv + np - 1).x; key0[q] = key1[q] = np - 1; }
+        else {
+          const long long z0 = __ldg(zq + idx - 1), z1 = __ldg(zq + idx);
+          w1 = i64_to_f32(xi - z0) / i64_to_f32(z1 - z0);
+          const float e0 = __ldg(tv + idx - 1).x, e1 = __ldg(tv + idx).x;
+          e = e0 + w1 * (e1 - e0);
+          key0[q] = idx - 1;
+          key1[q] = idx;
+        }
+        se = S32 / e;
+      } else {
+        se = __ldg(tv + idx).x;
+        key0[q] = key1[q] = idx;
+      }
+      const int k = k0 + q, p = q + 2;
+      const float lEk = t[p] - t[p - 1];
+      if (pos) {
+        const float lE1 = k + 1 < nz ? t[p + 1] - t[p] : 0.0f;
+        const float lE2 = k + 2 < nz ? t[p + 2] - t[p + 1] : 0.0f;
+        oD[q] = a * LD[p] + c * LD[p + 1] - cb * (lH[p] + lH[p - 1]) + se * lEk;
+        oB[q] = a * t[p] + c * t[p + 1] - cb * (lE1 + lE2);
+      } else {
+        const float lEm1 = k >= 1 ? t[p - 1] - t[p - 2] : 0.0f;
+        oD[q] = a * LD[p] + c * LD[p - 1] - cb * (lH[p] + lH[p - 1]) + se * lEk;
+        oB[q] = a * t[p] + c * t[p - 1] - cb * (lEk + lEm1);
+      }
+      // dL/deps_k = lE_k (-S D_k / eps_k^2) = lE_k (-se^2 D_k / S)
+      const float gE = q < nvalid ? lEk * (-se * se * Dold[q] * inv_S) : 0.0f;
+      g0[q] = gE * (1.0f - w1);
+      g1[q] = gE * w1;
+    }
+    float* oLD = A.lD + I.off + k0;
+    float* oLB = A.lB + I.off + k0;
+    if (nvalid == kAdjCPT) {
+      *reinterpret_cast<float4*>(oLD) = make_float4(oD[0], oD[1], oD[2], oD[3]);
+      *reinterpret_cast<float4*>(oLB) = make_float4(oB[0], oB[1], oB[2], oB[3]);
+    } else {
+#pragma unroll
+      for (int q = 0; q < kAdjCPT; ++q)
+        if (q < nvalid) { oLD[q] = oD[q]; oLB[q] = oB[q]; }
+    }
+    // keys grow with k: the block's first cell holds its smallest, its last valid cell its largest
+    if (tid == 0) s_key[0] = key0[0];
+    const int klast = min(x0 + kAdjTileCells, nz) - 1;
+#pragma unroll
+    for (int q = 0; q < kAdjCPT; ++q)
+      if (k0 + q == klast) s_key[1] = key1[q];
   }
   __syncthreads();
-  double* grad = A.grad + I.tab;
   const int kmin = s_key[0], span = s_key[1] - kmin + 1;
-  const bool lin = (I.flags & F_LINEAR) != 0;
-  const bool h0 = segment_sum(key0, g0, valid);
-  const bool h1 = segment_sum(key1, g1, valid && lin);
-  if (span <= kAdjKeys) {
-    if (h0) atomicAdd(&s_g[key0 - kmin], g0);
-    if (h1) atomicAdd(&s_g[key1 - kmin], g1);
+  const bool in_smem = span <= kAdjKeys;      // uniform over the block
+  // (blocks add into different copies of the gradient, so that the many blocks of one
+  // uniform region do not all queue on the same profile value's atomics)
+  double* grad = A.grad + (size_t)(blockIdx.x % A.grad_copies) * A.grad_stride + I.tab;
+  auto add = [&](int key, float v) {
+    if (v == 0.0f) return;
+    if (in_smem) atomicAdd(&s_g[key - kmin], v);
+    else atomicAdd(grad + key, (double)v);
+  };
+  // a warp whose cells all map to one profile value sums with shuffles
+  const int lo = nvalid > 0 ? key0[0] : INT_MAX;
+  int hi = INT_MIN;
+#pragma unroll
+  for (int q = 0; q < kAdjCPT; ++q)
+    if (q < nvalid) hi = key1[q];
+  const int wlo = __reduce_min_sync(FULL, lo), whi = __reduce_max_sync(FULL, hi);
+  if (wlo == whi) {
+    float v = 0.0f;
+#pragma unroll
+    for (int q = 0; q < kAdjCPT; ++q)
+      if (q < nvalid) v += g0[q] + g1[q];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(FULL, v, o);
+    if ((tid & 31) == 0) add(wlo, v);
+  } else if (nvalid > 0) {
+    // contributions in the order key0[0], key1[0], key0[1], ...: runs of one key merge
+    int ck = key0[0];
+    float acc = 0.0f;
+#pragma unroll
+    for (int q = 0; q < kAdjCPT; ++q) {
+      if (q < nvalid) {
+        if (key0[q] != ck) { add(ck, acc); ck = key0[q]; acc = 0.0f; }
+        acc += g0[q];
+        if (key1[q] != ck) { add(ck, acc); ck = key1[q]; acc = 0.0f; }
+        acc += g1[q];
+      }
+    }
+    add(ck, acc);
+  }
+  if (in_smem) {
     __syncthreads();
-    for (int i = tid; i < span; i += kAdjCells)
-      if (s_g[i] != 0.0) atomicAdd(grad + kmin + i, s_g[i]);
-  } else {
-    if (h0) atomicAdd(grad + key0, g0);
-    if (h1) atomicAdd(grad + key1, g1);
+    for (int i = tid; i < span; i += kAdjThreads)
+      if (s_g[i] != 0.0f) atomicAdd(grad + kmin + i, (double)s_g[i]);
   }
 }
 
@@ -192,7 +305,23 @@ __global__ void loss_source_kernel(const SourceAdjArgs A) {
 }
 
 int adjoint_step_launch(const AdjArgs& a, cudaStream_t st) {
-  adjoint_step_kernel<<<a.n_tiles, 256, 0, st>>>(a);
+  adjoint_step_kernel<<<a.n_tiles, kAdjThreads, 0, st>>>(a);
+  return (int)cudaGetLastError();
+}
+
+__global__ void sum_copies_kernel(const double* __restrict__ copies, long long n_copies, long long stride,
+                                  long long n, double* __restrict__ out) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  double t = 0.0;
+  for (long long c = 0; c < n_copies; ++c) t += copies[c * stride + i];
+  out[i] = t;
+}
+
+int sum_copies_launch(const double* copies, long long n_copies, long long stride, long long n, double* out,
+                      cudaStream_t st) {
+  if (n == 0) return 0;
+  sum_copies_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(copies, n_copies, stride, n, out);
   return (int)cudaGetLastError();
 }
 

@@ -689,6 +689,8 @@ static gfdtd_status check_inst(gfdtd_ctx* c, int inst) {
 // slices s0 + 1 .. s0 + nsteps (the last one is also the block's D output).
 // Every tile, the fast kernel's included, runs in the general FP32 kernel,
 // whose per-step D store the reverse sweep needs.
+constexpr int kGradCopies = 64;   // copies of the adjoint's gradient that its blocks spread atomics over
+
 static gfdtd_status enqueue_segment_block(gfdtd_ctx* c, const void* Bin, void* Bout, char* dseg, size_t fb,
                                           const long long* n_done, int s0, int nsteps) {
   for (int k : {0, 2}) {
@@ -752,7 +754,7 @@ extern "C" gfdtd_status gfdtd_adjoint(gfdtd_ctx* c, int64_t n_steps, int probe_i
       (s = dalloc(c, c->d_dseg, fb * (K + 1))) || (s = dalloc(c, c->d_wB[0], fb)) ||
       (s = dalloc(c, c->d_wB[1], fb)) || (s = dalloc(c, c->d_lB[0], lb)) ||
       (s = dalloc(c, c->d_lB[1], lb)) || (s = dalloc(c, c->d_lD[0], lb)) ||
-      (s = dalloc(c, c->d_lD[1], lb)) || (s = dalloc(c, c->d_grad, sizeof(double) * ntab)) ||
+      (s = dalloc(c, c->d_lD[1], lb)) || (s = dalloc(c, c->d_grad, sizeof(double) * ntab * (kGradCopies + 1))) ||
       (s = dalloc(c, c->d_gn, sizeof(double) * K * c->n_inst)) || (s = dalloc(c, c->d_adjn, 16)) ||
       (s = dalloc(c, c->d_acc0_re, sizeof(double) * std::max(1, c->n_bins))) ||
       (s = dalloc(c, c->d_acc0_im, sizeof(double) * std::max(1, c->n_bins))))
@@ -764,7 +766,7 @@ extern "C" gfdtd_status gfdtd_adjoint(gfdtd_ctx* c, int64_t n_steps, int probe_i
   if (c->n_adj_tiles == 0) {
     std::vector<int2> t;
     for (int i = 0; i < c->n_inst; ++i)
-      for (long long x0 = 0; x0 < c->nz[i]; x0 += 256) t.push_back(make_int2(i, (int)x0));
+      for (long long x0 = 0; x0 < c->nz[i]; x0 += kAdjTileCells) t.push_back(make_int2(i, (int)x0));
     if ((s = upload(c, c->d_adj_tiles, t))) return s;
     c->n_adj_tiles = (int)t.size();
   }
@@ -811,7 +813,7 @@ extern "C" gfdtd_status gfdtd_adjoint(gfdtd_ctx* c, int64_t n_steps, int probe_i
   // ---- reverse sweep, segment by segment
   CK(c, cudaMemsetAsync(c->d_lB[0].p, 0, lb, st));
   CK(c, cudaMemsetAsync(c->d_lD[0].p, 0, lb, st));
-  CK(c, cudaMemsetAsync(c->d_grad.p, 0, sizeof(double) * ntab, st));
+  CK(c, cudaMemsetAsync(c->d_grad.p, 0, sizeof(double) * ntab * (kGradCopies + 1), st));
   int lc = 0;
   long long host_n = 0;
   for (long long sg = nseg - 1; sg >= 0; --sg) {
@@ -865,7 +867,9 @@ extern "C" gfdtd_status gfdtd_adjoint(gfdtd_ctx* c, int64_t n_steps, int probe_i
       aa.lD = (float*)c->d_lD[1 - lc].p;
       aa.Dold = (const float*)((char*)c->d_dseg.p + (m - 1) * fb);
       aa.n = n;
-      aa.grad = (double*)c->d_grad.p;
+      aa.grad = (double*)c->d_grad.p;       // copies 0 .. kGradCopies-1; the sum goes after them
+      aa.grad_copies = kGradCopies;
+      aa.grad_stride = ntab;
       CKI(c, adjoint_step_launch(aa, st));
       c->launches += 2;
       lc = 1 - lc;
@@ -873,7 +877,10 @@ extern "C" gfdtd_status gfdtd_adjoint(gfdtd_ctx* c, int64_t n_steps, int probe_i
     CK(c, cudaStreamSynchronize(st));   // host_n is reused by the next segment's copy
   }
   std::vector<double> g(ntab);
-  CK(c, cudaMemcpyAsync(g.data(), c->d_grad.p, sizeof(double) * ntab, cudaMemcpyDeviceToHost, st));
+  double* gsum = (double*)c->d_grad.p + (size_t)kGradCopies * ntab;
+  CKI(c, sum_copies_launch((const double*)c->d_grad.p, kGradCopies, ntab, ntab, gsum, st));
+  c->launches += 1;
+  CK(c, cudaMemcpyAsync(g.data(), gsum, sizeof(double) * ntab, cudaMemcpyDeviceToHost, st));
   CK(c, cudaStreamSynchronize(st));
   size_t o = 0;
   for (int i = 0; i < c->n_inst; ++i) {

@@ -193,9 +193,11 @@ struct FoldArgs {
 };
 
 // Adjoint (gfdtd_adjoint.cu).
+constexpr int kAdjTileCells = 1024;   // cells one block of the adjoint step transposes
+
 struct AdjArgs {
   const InstDev* inst;
-  const int2* tiles;          // (instance, first cell) of 256-cell blocks
+  const int2* tiles;          // (instance, first cell) of kAdjTileCells-cell blocks
   int n_tiles;
   Tables tb;
   const float* lBn;           // adjoint of B^n, D^{n+1/2}
@@ -205,6 +207,8 @@ struct AdjArgs {
   const float* Dold;          // D^{n-1/2}
   long long n;                // the forward step being transposed
   double* grad;               // dL/d(profile value), indexed by the instance's table offset
+  int grad_copies;            // copies of grad, grad_stride apart: block b adds into copy b % copies
+  long long grad_stride;
 };
 
 struct ProbeAdjArgs {
@@ -232,6 +236,8 @@ struct SourceAdjArgs {
   double* gn;                 // [step][inst]
 };
 int adjoint_step_launch(const AdjArgs& a, cudaStream_t st);
+int sum_copies_launch(const double* copies, long long n_copies, long long stride, long long n, double* out,
+                      cudaStream_t st);
 int probe_adjoint_launch(const ProbeAdjArgs& a, cudaStream_t st);
 int loss_source_launch(const SourceAdjArgs& a, cudaStream_t st);
 
