@@ -183,6 +183,37 @@ def adjoint_measurement(gb):
             "config": wl.description, "loss_finite": bool(np.all(np.isfinite(loss)))}
 
 
+def example_measurements(gb, torch):
+    """Throughput of the paper's other example workloads through gfdtd_step
+    (inputs resident, one warm-up call for tiling and graphs, then one timed
+    call): the moving interface in FP64, the moving-matter slab in FP32, and
+    the moving gradient (stable eps 1 -> 2 ramp, 2^20 cells) in every
+    precision tier.  Step counts are cut to keep each timing near 0.1-0.5 s."""
+    from paper_2304_06586_gb300 import workloads as w
+    cases = [("interface FP64 (4000 cells, v=0.3c)", w.config1(), gb.F64, 8000),
+             ("moving-matter slab FP32 (5 x 2^16 cells, v in +-0.5c)", w.config2(), gb.F32, 8000)]
+    for name, prec in (("F32", gb.F32), ("F32_KAHAN", gb.F32_KAHAN), ("BF16", gb.BF16),
+                       ("F16", gb.F16), ("F64", gb.F64)):
+        cases.append((f"gradient {name} (2^20 cells, ramp eps 1->2, v=0.7c)", w.config4("stable"), prec,
+                      2000 if prec == gb.F64 else 8000))
+    out = {}
+    for name, wl, prec, steps in cases:
+        sim = gb.Simulation([i.nz for i in wl.instances], wl.S, prec)
+        configure(sim, wl, gb)
+        sim.step(256)
+        sim.synchronize()
+        t0 = time.perf_counter()
+        sim.step(steps)
+        sim.synchronize()
+        dt = time.perf_counter() - t0
+        cells = sum(i.nz for i in wl.instances)
+        out[name] = {"value": cells * steps / dt / 1e9, "unit": "Gcell-updates/s", "steps": steps,
+                     "seconds": dt}
+        sim.close()
+    torch.cuda.synchronize()
+    return out
+
+
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -194,7 +225,7 @@ def parse():
     ap.add_argument("--plain-steps", type=int, default=4)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
-    ap.add_argument("--no-sweeps", action="store_true", help="skip the stability-map and star-TMM timings")
+    ap.add_argument("--no-sweeps", action="store_true", help="skip the side timings (sweeps, adjoint, example workloads)")
     ap.add_argument("--tile", default="", help="cells_per_lane,time_block[,blocks_per_sm] (default: autotune)")
     return ap.parse_args()
 
@@ -466,6 +497,7 @@ def main():
         sim.close()
         sweeps = None if args.no_sweeps else sweep_measurements(torch, gb, stream)
         adjoint = None if args.no_sweeps else adjoint_measurement(gb)
+        examples = None if args.no_sweeps else example_measurements(gb, torch)
 
     if rank != 0:
         return
@@ -479,7 +511,8 @@ def main():
                        "l2": "inputs larger than L2 (%.2f GB of fields)" % (cells * 16 / 1e9),
                        "parallelism": "instances sharded per rank" if world > 1 else "1 GPU"},
             "e2e": e2e, "gpu_launches": launches, "roofline": roofline, "plain": plain,
-            "clocks": clocks, "sweeps": sweeps, "capture": capture, "absorber": absorber, "adjoint": adjoint}
+            "clocks": clocks, "sweeps": sweeps, "capture": capture, "absorber": absorber, "adjoint": adjoint,
+            "examples": examples}
     if not args.no_cpu:
         line["cpu_baseline"] = cpu_baseline(wl, single_core=True)
     print(json.dumps(line), flush=True)

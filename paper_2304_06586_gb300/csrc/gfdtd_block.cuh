@@ -208,21 +208,101 @@ __device__ __forceinline__ void node_coef(const InstDev& I, const Tables& tb, lo
 
 // Per-lane material of the run of C cells starting at k0 at one half level.
 // `li` carries, between steps, the number of profile positions at or left of k0.
+// A 64-bit fixed-point difference in the arithmetic type: FP32 from the two
+// 32-bit halves (two 32-bit conversions and an FMA; a 64-bit conversion is far
+// slower), FP64 directly.
+template <typename R> __device__ __forceinline__ R fixed_to_real(long long x);
+template <> __device__ __forceinline__ float fixed_to_real<float>(long long x) {
+  return fmaf((float)(int)(x >> 32), 4294967296.0f, (float)(unsigned)x);
+}
+template <> __device__ __forceinline__ double fixed_to_real<double>(long long x) { return (double)x; }
+
+template <typename R> __device__ __forceinline__ R quick_div(R x, R y) { return x / y; }
+template <> __device__ __forceinline__ float quick_div<float>(float x, float y) { return __fdividef(x, y); }
+
+// The linear piece of a LINEAR profile between knots j-1 and j (j knots at or
+// left; constant beyond the end knots) as (eps, mu) = alpha + beta t, with t in
+// cells from the moving coordinate xi.
+template <typename R, typename V>
+__device__ __forceinline__ void lin_piece(const long long* __restrict__ zq, const V* __restrict__ raw, int nk,
+                                          int j, long long xi, R& ae, R& be, R& am, R& bm) {
+  if (j <= 0 || j >= nk) {
+    const auto v = __ldg(raw + (j <= 0 ? 0 : nk - 1));
+    ae = v.x; am = v.y; be = bm = (R)0;
+    return;
+  }
+  const long long z0 = __ldg(zq + j - 1), z1 = __ldg(zq + j);
+  const auto v0 = __ldg(raw + j - 1), v1 = __ldg(raw + j);
+  const R inv = (R)1 / fixed_to_real<R>(z1 - z0);
+  const R w = fixed_to_real<R>(xi - z0) * inv, dw = (R)4294967296.0 * inv;
+  const R de = (R)v1.x - (R)v0.x, dm = (R)v1.y - (R)v0.y;
+  ae = (R)v0.x + w * de; be = dw * de;
+  am = (R)v0.y + w * dm; bm = dw * dm;
+}
+
+// Coefficients (x: S/eps or S/mu, y: coupling) from the interpolated (eps, mu).
+template <bool MATTER, bool ESIDE, typename R>
+__device__ __forceinline__ void coef_of(R S, R beta, R cb, R e, R m, R& cx, R& cy) {
+  if (!MATTER) {
+    cx = quick_div(S, ESIDE ? e : m);
+    cy = cb;
+  } else {
+    const R g = (R)1 - beta * beta;
+    const R inv = quick_div((R)1, e * m - beta * beta);
+    cx = S * g * (ESIDE ? m : e) * inv;
+    cy = (R)0.5 * S * beta * g * inv;
+  }
+}
+
 template <int C, bool MATTER, bool ESIDE, typename R>
 __device__ __forceinline__ void lane_coefs(const InstDev& I, const Tables& tb, long long off,
                                            int k0, int& li, R (&cx)[C], R (&cy)[C]) {
   const long long* __restrict__ zq = tb.zq + I.tab;
   const auto* __restrict__ tv = TabOf<R>::get(tb, ESIDE) + I.tab;
   if (I.flags & F_LINEAR) {
+    // eps and mu are linear between knots, so over a lane's cells they are a
+    // few linear pieces in the cell index: each piece costs one evaluation per
+    // lane, each cell an FMA and a division.
     const int nk = I.n;
     while (li < nk && node_of(__ldg(zq + li), off) <= k0) ++li;
     while (li > 0 && node_of(__ldg(zq + li - 1), off) > k0) --li;
-    int idx = li;
+    const R S = (R)I.S, beta = (R)I.beta, cb = (R)I.cb;
+    const long long xi0 = ((long long)k0 << 32) - off;
+    const int K1 = li < nk ? node_of(__ldg(zq + li), off) : INT_MAX;
+    const int K2 = li + 1 < nk ? node_of(__ldg(zq + li + 1), off) : INT_MAX;
+    if (K2 >= k0 + C) {
+      // at most one knot among the lane's cells: the piece left of it from
+      // cell k0, the piece right of it from its first cell K1
+      R aeL, beL, amL, bmL, aeR = 0, beR = 0, amR = 0, bmR = 0, mR = 0;
+      lin_piece<R>(zq, tv, nk, li, xi0, aeL, beL, amL, bmL);
+      if (K1 < k0 + C) {
+        lin_piece<R>(zq, tv, nk, li + 1, xi0 + ((long long)(K1 - k0) << 32), aeR, beR, amR, bmR);
+        mR = (R)(K1 - k0);
+      }
 #pragma unroll
-    for (int c = 0; c < C; ++c) {
-      const int k = k0 + c;
-      while (idx < nk && node_of(__ldg(zq + idx), off) <= k) ++idx;
-      linear_coef<MATTER, ESIDE>(I, zq, tv, idx, k, off, cx[c], cy[c]);
+      for (int c = 0; c < C; ++c) {
+        const bool r = k0 + c >= K1;
+        const R t = (R)c - (r ? mR : (R)0);
+        const R e = (r ? aeR : aeL) + (r ? beR : beL) * t;
+        const R m = (r ? amR : amL) + (r ? bmR : bmL) * t;
+        coef_of<MATTER, ESIDE>(S, beta, cb, e, m, cx[c], cy[c]);
+      }
+    } else {
+      // several knots among the lane's cells: walk them cell by cell
+      int idx = li;
+      R ae, be, am, bm, t0 = 0;
+      lin_piece<R>(zq, tv, nk, idx, xi0, ae, be, am, bm);
+#pragma unroll
+      for (int c = 0; c < C; ++c) {
+        const long long xi = xi0 + ((long long)c << 32);
+        if (idx < nk && __ldg(zq + idx) <= xi) {
+          do ++idx; while (idx < nk && __ldg(zq + idx) <= xi);
+          lin_piece<R>(zq, tv, nk, idx, xi, ae, be, am, bm);
+          t0 = (R)c;
+        }
+        const R t = (R)c - t0;
+        coef_of<MATTER, ESIDE>(S, beta, cb, ae + be * t, am + bm * t, cx[c], cy[c]);
+      }
     }
     return;
   }

@@ -108,10 +108,11 @@ def test_batched_layers_random_fields(shape, kind):
     _compare(wl, sim, orcs, TOL32)
 
 
+@pytest.mark.parametrize("tuning", [(16, 16), (8, 16), (20, 32), (24, 24)])
 @pytest.mark.parametrize("kind", [w.PERTURBATION, w.MATTER])
-def test_batched_linear_profiles(kind):
+def test_batched_linear_profiles(kind, tuning):
     wl = _mixed_workload(seed=8, kind=kind, interp=w.LINEAR)
-    sim = make_sim(wl, tuning=(16, 16))
+    sim = make_sim(wl, tuning=tuning)
     orcs = make_oracle(wl)
     _seed_fields(wl, sim, orcs)
     sim.step(53)
@@ -190,6 +191,21 @@ def test_derived_fields():
         assert rel_l2(sim.read_fields(k, gb.FIELD_ESTAR), E - I.beta * bbar) <= TOL32
 
 
+@pytest.mark.parametrize("kind", [w.PERTURBATION, w.MATTER])
+def test_linear_profiles_f64(kind):
+    """Piecewise-linear profiles in the FP64 tier, where rounding differences
+    between the kernels' per-lane linear pieces and the oracle's per-node
+    interpolation would show above the 1e-11 bar if the pieces were wrong."""
+    wl = _mixed_workload(seed=8, kind=kind, interp=w.LINEAR)
+    sim = make_sim(wl, prec=gb.F64)
+    orcs = make_oracle(wl)
+    _seed_fields(wl, sim, orcs)
+    sim.step(37)
+    for o in orcs:
+        o.run(37)
+    _compare(wl, sim, orcs, 1e-11)
+
+
 @pytest.mark.parametrize("prec,tol", [(gb.F64, 1e-11), (gb.F32_KAHAN, TOL32), (gb.BF16, 3e-2),
                                       (gb.F16, 5e-3)])
 def test_precision_tiers(prec, tol):
@@ -214,6 +230,22 @@ def test_crystal_small_matches_oracle(tuning):
     import oracle
     oracle.run_many(orcs, wl.n_steps)
     _compare(wl, sim, orcs, TOL32)
+
+
+@pytest.mark.parametrize("prec,tol", [(gb.F32_KAHAN, TOL32), (gb.F64, 1e-11), (gb.F32, 5e-4)])
+def test_gradient_ramp_reduced(prec, tol):
+    """The moving-gradient shape (linear eps ramp 1 -> 2 over a quarter of the
+    grid, v = 0.7c) at 2^12 cells, from rest with its source and probe, long
+    enough for the pulse to cross the ramp and reach the probe.  Over these
+    8000 smooth steps plain FP32 accumulates rounding past 1e-4 (it is the
+    case the compensated tier is for), so plain FP32 is held to 5e-4."""
+    wl = w.config4("stable", nz=1 << 12, n_steps=8000)
+    sim = make_sim(wl, prec=prec)
+    orcs = make_oracle(wl)
+    sim.step(wl.n_steps)
+    for o in orcs:
+        o.run(wl.n_steps)
+    _compare(wl, sim, orcs, tol)
 
 
 def test_matter_slab_reduced():
