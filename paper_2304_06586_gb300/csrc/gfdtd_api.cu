@@ -417,11 +417,19 @@ static gfdtd_status finalize(gfdtd_ctx* c) {
     const int nvals = (int)m.eps.size();
     if (m.interp == GFDTD_LINEAR) {
       flags |= F_LINEAR;
+      // a moving-perturbation profile whose eps (or mu) knots are all equal has a
+      // uniform S/eps (or S/mu): the kernels then skip that side's interpolation
+      bool econst = m.kind != GFDTD_MATTER, mconst = m.kind != GFDTD_MATTER;
       for (int k = 0; k < nvals; ++k) {
         zq.push_back(to_fixed(m.z[k]));
         tabE.push_back(make_double2(m.eps[k], m.mu[k]));
         tabH.push_back(make_double2(m.eps[k], m.mu[k]));
+        if (m.eps[k] != m.eps[0]) econst = false;
+        if (m.mu[k] != m.mu[0]) mconst = false;
       }
+      if (econst) flags |= F_EPS_CONST;
+      if (mconst) flags |= F_MU_CONST;
+      d.sm32 = (float)(S / m.mu[0]);
     } else {
       bool econst = true, mconst = true;
       for (int k = 0; k < nvals; ++k) {

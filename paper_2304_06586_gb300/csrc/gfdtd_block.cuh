@@ -391,7 +391,9 @@ __device__ __forceinline__ void run_tile(const BlockArgs<T>& A, const InstDev& I
   const long long dq = I.dq;
   const auto e0 = __ldg(TabOf<R>::get(A.tb, true) + I.tab);
   const auto h0 = __ldg(TabOf<R>::get(A.tb, false) + I.tab);
-  const R se0 = e0.x, sm0 = h0.x;
+  // (uniform values: LINEAR tables hold raw (eps, mu), LAYERS tables the coefficients)
+  const bool lin = (I.flags & F_LINEAR) != 0;
+  const R se0 = lin ? (R)I.S / e0.x : e0.x, sm0 = lin ? (R)I.S / h0.y : h0.x;
   const R cbe0 = MATTER ? e0.y : (R)I.cb, cbh0 = MATTER ? h0.y : (R)I.cb;
   int liE = 0, liH = 0;
   if (!eps_const || !mu_const) {

@@ -14,8 +14,8 @@ enum : int {
   F_POS = 1,         // beta >= 0: Table 1 first column (Ba, dBa, dDa); else second column
   F_MATTER = 2,      // moving matter: per-node coupling beta_c (see gfdtd.h)
   F_LINEAR = 4,      // piecewise-linear profile (per-cell interpolation)
-  F_MU_CONST = 8,    // layers profile whose H-side coefficients are all equal
-  F_EPS_CONST = 16,  // layers profile whose E-side coefficients are all equal
+  F_MU_CONST = 8,    // H-side coefficients all equal (layers), or all mu knots equal (linear, not matter)
+  F_EPS_CONST = 16,  // E-side coefficients all equal (layers), or all eps knots equal (linear, not matter)
 };
 
 // One instance of the batch, as the kernels see it.
@@ -37,7 +37,7 @@ struct InstDev {
   double beta;
   double cb;         // S beta / 2: coupling in the Table 1 averages (moving perturbation)
   float a32, c32, cb32;   // a, c, cb rounded to FP32 (the FP32-arithmetic kernels read these)
-  float sm32;              // S / mu of layer 0 (half nodes) in FP32: the uniform value when F_MU_CONST
+  float sm32;              // S / mu of the first layer or knot in FP32: the uniform value when F_MU_CONST
   int pad0, pad1;
   double abs_sigma;        // absorbing layers at both ends: strength at the outer end
   int abs_w;               // their width in cells (0: none)
