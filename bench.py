@@ -45,9 +45,11 @@ def kernel_source_hash():
     return h.hexdigest()
 
 
-def measured_traffic():
-    """DRAM bytes per cell-update of the fast kernel from the committed ncu
-    summary, if it was taken on the kernel as it is now (else None)."""
+def measured_traffic(tile):
+    """DRAM bytes per cell-update of the fast kernel in tile shape `tile`
+    (cells per lane, time block, blocks per SM) from the committed ncu summary,
+    if it was taken on the kernel sources as they are now and on that shape
+    (else None)."""
     path = os.path.join(ROOT, "profiles", "fast_kernel_crystal.md")
     if not os.path.exists(path):
         return None
@@ -60,13 +62,14 @@ def measured_traffic():
     try:
         if fields.get("kernel source sha256") != kernel_source_hash():
             return None
-        return float(fields["dram bytes per cell-update"])
+        return float(fields["dram bytes per cell-update, tile %d,%d,%d" % tuple(tile)])
     except (KeyError, ValueError):
         return None
 
 
-def roofline_of(kt):
-    """FP32-pipe roofline of the fast kernel from per-launch CUDA-event times."""
+def roofline_of(kt, tile):
+    """FP32-pipe roofline of the fast kernel (tile shape `tile`) from per-launch
+    CUDA-event times."""
     fast = kt["fast"]
     if fast["launches"] == 0:
         return None
@@ -74,7 +77,7 @@ def roofline_of(kt):
     cu_per_launch = fast["cell_updates"] / fast["launches"]
     achieved = FLOPS_PER_CELL_UPDATE * cu_per_launch / (launch_ms / 1e3) / 1e12
     peak = 2 * FP32_LANES_PER_SM * SM_COUNT * SM_MAX_MHZ * 1e6 / 1e12
-    bpc = measured_traffic()
+    bpc = measured_traffic(tile)
     total_ms = sum(v["ms"] for v in kt.values())
     return {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
             "frac": achieved / peak,
@@ -415,7 +418,7 @@ def main():
         # roofline of the dominant kernel: the same step, each batched launch
         # bracketed by CUDA events on the simulation's stream
         kt = sim.profile_kernels(T)
-        roofline = roofline_of(kt)
+        roofline = roofline_of(kt, (st["cells_per_lane"], st["time_block"], st["blocks_per_sm"]))
 
         # end to end through the C ABI with pinned host buffers
         e2e = None

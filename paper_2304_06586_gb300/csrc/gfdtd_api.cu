@@ -648,26 +648,32 @@ static gfdtd_status autotune(gfdtd_ctx* c) {
   cudaEvent_t e0, e1;
   CK(c, cudaEventCreate(&e0));
   CK(c, cudaEventCreate(&e1));
-  double best = 1e300;
-  int bi = 0;
-  for (int i = 0; i < n; ++i) {
-    gfdtd_status s = set_tiles(c, Cs[i], TBs[i], MBs[i]);
-    if (s) return s;
-    s = enqueue_block(c, c->stream, c->cur, 0, TBs[i], false, false);
-    if (s) return s;
-    CK(c, cudaEventRecord(e0, c->stream));
-    const int reps = 3;
-    for (int r = 0; r < reps; ++r) {
+  // two passes over the candidates, each candidate keeping its faster pass, so
+  // that a clock or cache transient during one timing does not decide alone
+  double per_step[16];
+  for (int i = 0; i < n; ++i) per_step[i] = 1e300;
+  for (int pass = 0; pass < 2; ++pass) {
+    for (int i = 0; i < n; ++i) {
+      gfdtd_status s = set_tiles(c, Cs[i], TBs[i], MBs[i]);
+      if (s) return s;
       s = enqueue_block(c, c->stream, c->cur, 0, TBs[i], false, false);
       if (s) return s;
+      CK(c, cudaEventRecord(e0, c->stream));
+      const int reps = 3;
+      for (int r = 0; r < reps; ++r) {
+        s = enqueue_block(c, c->stream, c->cur, 0, TBs[i], false, false);
+        if (s) return s;
+      }
+      CK(c, cudaEventRecord(e1, c->stream));
+      CK(c, cudaEventSynchronize(e1));
+      float ms = 0.f;
+      CK(c, cudaEventElapsedTime(&ms, e0, e1));
+      per_step[i] = std::min(per_step[i], (double)ms / (reps * TBs[i]));
     }
-    CK(c, cudaEventRecord(e1, c->stream));
-    CK(c, cudaEventSynchronize(e1));
-    float ms = 0.f;
-    CK(c, cudaEventElapsedTime(&ms, e0, e1));
-    const double per_step = ms / (reps * TBs[i]);
-    if (per_step < best) { best = per_step; bi = i; }
   }
+  int bi = 0;
+  for (int i = 1; i < n; ++i)
+    if (per_step[i] < per_step[bi]) bi = i;
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   return set_tiles(c, Cs[bi], TBs[bi], MBs[bi]);
