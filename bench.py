@@ -217,6 +217,53 @@ def example_measurements(gb, torch):
     return out
 
 
+CASES = ["adjoint", "interface", "slab"] + ["gradient-" + t for t in ("F32", "F32_KAHAN", "BF16", "F16", "F64")]
+
+
+def run_case(args):
+    """One side workload alone (for profiling it): `adjoint` (256 x 2^14 PWL
+    profiles, gfdtd_adjoint over --time-steps steps), `interface` (FP64),
+    `slab` (moving matter, FP32) or `gradient-<tier>` (2^20-cell ramp), through
+    gfdtd_step with the tile shape of --tile if given.  Prints one JSON line."""
+    import torch
+    from paper_2304_06586_gb300 import binding as gb
+    from paper_2304_06586_gb300 import workloads as w
+    T = args.time_steps
+    if args.case == "adjoint":
+        wl = w.config5(n_steps=T)
+        sim = gb.Simulation([i.nz for i in wl.instances], wl.S, gb.F32)
+        configure(sim, wl, gb)
+        nv = [len(i.eps) for i in wl.instances]
+        sim.adjoint(64, 0, 0, 16, nv)
+        t0 = time.perf_counter()
+        sim.adjoint(T, 0, 0, 16, nv)
+        dt = time.perf_counter() - t0
+    else:
+        if args.case == "interface":
+            wl, prec = w.config1(), gb.F64
+        elif args.case == "slab":
+            wl, prec = w.config2(), gb.F32
+        else:
+            wl, prec = w.config4("stable"), getattr(gb, args.case.split("-", 1)[1])
+        sim = gb.Simulation([i.nz for i in wl.instances], wl.S, prec)
+        configure(sim, wl, gb)
+        if args.tile:
+            sim.set_tuning(*[int(x) for x in args.tile.split(",")])
+        sim.step(64)
+        sim.synchronize()
+        t0 = time.perf_counter()
+        sim.step(T)
+        sim.synchronize()
+        dt = time.perf_counter() - t0
+    st = sim.stats()
+    cells = sum(i.nz for i in wl.instances)
+    sim.close()
+    torch.cuda.synchronize()
+    print(json.dumps({"case": args.case, "workload": wl.description, "steps": T, "seconds": dt,
+                      "value": cells * T / dt / 1e9, "unit": "Gcell-updates/s",
+                      "tile": [st["cells_per_lane"], st["time_block"], st["blocks_per_sm"]]}), flush=True)
+
+
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -229,6 +276,8 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-sweeps", action="store_true", help="skip the side timings (sweeps, adjoint, example workloads)")
+    ap.add_argument("--case", default="", choices=[""] + CASES,
+                    help="time one side workload alone instead of the batched crystal")
     ap.add_argument("--tile", default="", help="cells_per_lane,time_block[,blocks_per_sm] (default: autotune)")
     return ap.parse_args()
 
@@ -367,6 +416,8 @@ def run_reference(args, wl, rank):
 
 def main():
     args = parse()
+    if args.case:
+        return run_case(args)
     rank, world, local = dist_setup()
     wl = rank_workload(rank, args.instances, args.time_steps)
     if args.impl == "reference":
