@@ -35,6 +35,13 @@ class _Probe(C.Structure):
                 ("omega", _dp), ("re", _dp), ("im", _dp), ("series", _dp)]
 
 
+class _Tfsf(C.Structure):
+    _fields_ = [("node", C.c_int64), ("omega0", C.c_double), ("tau", C.c_double),
+                ("t0", C.c_double), ("amp", C.c_double), ("aux_B", _dp), ("aux_D", _dp)]
+
+
+AUX_N = 1064   # cells of a one-way source's auxiliary grid (see the C header)
+
 _lib = None
 
 
@@ -46,6 +53,10 @@ def lib():
         L.orc_run.restype = C.c_int
         L.orc_run.argtypes = [C.POINTER(_Problem), C.c_int, C.POINTER(_Source), C.c_int,
                               C.POINTER(_Probe), C.c_int64, C.c_int64, _dp, _dp]
+        L.orc_run_tfsf.restype = C.c_int
+        L.orc_run_tfsf.argtypes = [C.POINTER(_Problem), C.c_int, C.POINTER(_Source), C.c_int,
+                                   C.POINTER(_Probe), C.c_int, C.POINTER(_Tfsf), C.c_int64, C.c_int64,
+                                   _dp, _dp]
         L.orc_sample_material.restype = C.c_int
         L.orc_sample_material.argtypes = [C.POINTER(_Problem), C.c_int, C.c_int, C.c_int64, _dp]
         L.orc_step_transpose.restype = C.c_int
@@ -91,6 +102,7 @@ class Instance:
         self.sources = []
         self.probes = []
         self.absorb_width, self.absorb_sigma = 0, 0.0
+        self.tfsf = []
 
     def set_absorber(self, width, sigma):
         """Graded absorbing layers of `width` cells at both ends (0: none); see the C header."""
@@ -99,6 +111,12 @@ class Instance:
 
     def add_source(self, node, omega0, tau, t0, amp=1.0):
         self.sources.append((int(node), float(omega0), float(tau), float(t0), float(amp)))
+
+    def add_tfsf(self, node, omega0, tau, t0, amp=1.0):
+        """One-way source: total field at nodes >= node, the incident wave being the
+        right-going wave of a soft source with this waveform (see the C header)."""
+        self.tfsf.append({"args": (int(node), float(omega0), float(tau), float(t0), float(amp)),
+                          "B": np.zeros(AUX_N), "D": np.zeros(AUX_N)})
 
     def add_probe(self, node, omega):
         omega = _f64(omega)
@@ -121,8 +139,10 @@ class Instance:
             _Probe(p["node"], len(p["omega"]), 0, _ptr(p["omega"]), _ptr(p["re"]),
                    _ptr(p["im"]), _ptr(series[i]))
             for i, p in enumerate(self.probes)])
-        rc = lib().orc_run(C.byref(prob), len(self.sources), srcs, len(self.probes), prbs,
-                           self.n_done, n_steps, _ptr(self.B), _ptr(self.D))
+        tfs = (_Tfsf * max(1, len(self.tfsf)))(*[
+            _Tfsf(*t["args"], _ptr(t["B"]), _ptr(t["D"])) for t in self.tfsf])
+        rc = lib().orc_run_tfsf(C.byref(prob), len(self.sources), srcs, len(self.probes), prbs,
+                                len(self.tfsf), tfs, self.n_done, n_steps, _ptr(self.B), _ptr(self.D))
         if rc != 0:
             raise ValueError("oracle rejected the problem")
         self.n_done += n_steps
@@ -155,6 +175,8 @@ class Instance:
         """L = sum over `bins` of |X_f|^2 of probe `probe_id`, accumulated over the next
         n_steps from the current state, and dL/d(eps value) of every profile value.
         The instance's state is left unchanged."""
+        if self.tfsf:
+            raise ValueError("the adjoint covers soft sources only")
         p = self.probes[probe_id]
         om = _f64(np.asarray(p["omega"])[list(bins)])
         scratch = np.zeros(len(om))

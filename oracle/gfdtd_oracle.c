@@ -61,6 +61,34 @@
  *   by g(x) = exp(-sigma d(x)^2), d = (W - x)/W for x < W, d = (x - (nz-1-W))/W
  *   for x > nz-1-W, else 0; the source is added after the D damping.
  *
+ *   One-way (total-field / scattered-field) source (the paper is silent on
+ *   sources beyond the soft one; an option of this library): a boundary at
+ *   node q splits the grid into the total-field region (D_k, B_k with k >= q)
+ *   and the scattered-field region (k < q).  The incident wave is the
+ *   right-going wave that a soft source with the given waveform emits in an
+ *   auxiliary grid of the same scheme filled with the uniform background (the
+ *   material at node q at t = 0): AUX_N = 1064 cells, graded absorbing layers
+ *   of AUX_W = 512 cells and strength 0.05 at both ends, the soft source at
+ *   aux node 520 and the boundary at aux node 532 (aux index = k - q + 532).
+ *   (What the auxiliary layers reflect, about 1e-6 of the incident amplitude
+ *   for |beta| <= 0.6, reaches the scattered-field region.)
+ *   Every update that reads a value across the boundary reads it in the
+ *   other region's convention: a total-field update adds the incident value
+ *   of a scattered-field input, a scattered-field update subtracts the
+ *   incident value of a total-field input.  Worked out on the stencil
+ *   above (hb = beta_c / 2, ie = 1/eps_m, im = 1/mu_m of the background;
+ *   Bi, Di the incident B^{n-1}, D^{n-1/2}, Bn the incident B^n), this adds
+ *   after the B update
+ *     beta >= 0: B_{q-1} += S ie Di_q,
+ *                B_q     += -S hb Bi_{q-2} + beta S Bi_{q-1},
+ *                B_{q+1} += -S hb Bi_{q-1};
+ *     beta <  0: B_{q-2} += -S hb Bi_q,
+ *                B_{q-1} += S ie Di_q - S hb Bi_{q+1} + beta S Bi_q;
+ *   and after the D update
+ *     D_{q-1} += -S hb Di_q  (+ beta S Di_q when beta < 0),
+ *     D_q     += S (im Bn_{q-1} - hb Di_{q-1})  (+ beta S Di_{q-1} when beta >= 0).
+ *   Outside the auxiliary grid's reach (q - 2 .. q + 1) nothing changes.
+ *
  *   Probes: F = E at the probe node at level n+1/2 (moving perturbation:
  *   E = D/eps exactly, Eq. const_1d; moving matter: E = E* + beta * Bbar with
  *   E* from the relation above and Bbar the Table 1 average of B^n), and for
@@ -91,6 +119,18 @@ typedef struct {
     int64_t node;
     double omega0, tau, t0, amp;
 } orc_source;
+
+typedef struct {
+    int64_t node;        /* q: first node of the total-field region */
+    double omega0, tau, t0, amp;   /* waveform of the auxiliary soft source */
+    double* aux_B;       /* AUX_N doubles: auxiliary state (caller-owned, zero at the start) */
+    double* aux_D;
+} orc_tfsf;
+
+#define AUX_N 1064
+#define AUX_W 512
+#define AUX_SRC 520
+#define AUX_Q 532
 
 typedef struct {
     int64_t node;
@@ -183,10 +223,42 @@ static double absorb_factor(const orc_problem* p, double x)
 
 /* ---- the time loop ------------------------------------------------------- */
 
+int orc_run_tfsf(const orc_problem* p, int n_src, const orc_source* src,
+                 int n_probe, orc_probe* probes, int n_tfsf, const orc_tfsf* tfsf,
+                 int64_t n_done, int64_t n_steps, double* B, double* D);
+
+/* The auxiliary problem of a one-way source: the background material of node
+   q at t = 0, uniform, with the same kind, velocity and Courant number. */
+static void tfsf_aux_problem(const orc_problem* p, const orc_profile* eps, const orc_profile* mu,
+                             int64_t q, double* e_bg, double* m_bg, orc_problem* aux)
+{
+    *e_bg = profile_at(eps, node_pos(q));
+    *m_bg = profile_at(mu, node_pos(q));
+    memset(aux, 0, sizeof(*aux));
+    aux->kind = p->kind;
+    aux->interp = 0;
+    aux->n = 1;
+    aux->z = NULL;
+    aux->eps = e_bg;
+    aux->mu = m_bg;
+    aux->beta = p->beta;
+    aux->S = p->S;
+    aux->nz = AUX_N;
+    aux->absorb_width = AUX_W;
+    aux->absorb_sigma = 0.05;
+}
+
 int orc_run(const orc_problem* p, int n_src, const orc_source* src,
             int n_probe, orc_probe* probes,
             int64_t n_done, int64_t n_steps,
             double* B, double* D)
+{
+    return orc_run_tfsf(p, n_src, src, n_probe, probes, 0, NULL, n_done, n_steps, B, D);
+}
+
+int orc_run_tfsf(const orc_problem* p, int n_src, const orc_source* src,
+                 int n_probe, orc_probe* probes, int n_tfsf, const orc_tfsf* tfsf,
+                 int64_t n_done, int64_t n_steps, double* B, double* D)
 {
     const int64_t nz = p->nz;
     const double beta = p->beta, S = p->S;
@@ -202,6 +274,13 @@ int orc_run(const orc_problem* p, int n_src, const orc_source* src,
     mu.zq = zq;
     const int64_t dq = llround(ldexp(beta * S, 31));   /* beta*S/2 cells per half step */
 
+    /* one-way sources: auxiliary problems, background coefficients, per-step corrections */
+    const int nt = n_tfsf > 0 ? n_tfsf : 0;
+    orc_problem* aux = (orc_problem*)malloc(sizeof(orc_problem) * (size_t)(nt + 1));
+    double* bg = (double*)malloc(sizeof(double) * (size_t)(2 * nt + 1));   /* eps, mu per source */
+    double* corr = (double*)malloc(sizeof(double) * (size_t)(6 * nt + 1));  /* dB q-2..q+1, dD q-1..q */
+    for (int i = 0; i < nt; ++i) tfsf_aux_problem(p, &eps, &mu, tfsf[i].node, &bg[2 * i], &bg[2 * i + 1], &aux[i]);
+
     double* Es = (double*)malloc(sizeof(double) * (size_t)nz);  /* E* (perturbation: recomputed) */
     double* Hs = (double*)malloc(sizeof(double) * (size_t)nz);  /* H* */
     double* Bo = (double*)malloc(sizeof(double) * (size_t)nz);  /* B^{n-1} */
@@ -211,6 +290,43 @@ int orc_run(const orc_problem* p, int n_src, const orc_source* src,
         const int64_t n = n_done + s + 1;      /* B^{n-1} -> B^n, D^{n-1/2} -> D^{n+1/2} */
         memcpy(Bo, B, sizeof(double) * (size_t)nz);
         memcpy(Do, D, sizeof(double) * (size_t)nz);
+
+        /* one-way sources: incident values before and after the auxiliary step */
+        for (int i = 0; i < nt; ++i) {
+            const int64_t q = tfsf[i].node, a = AUX_Q - q;   /* aux index = k + a */
+            double* aB = tfsf[i].aux_B;
+            double* aD = tfsf[i].aux_D;
+            const double Bim2 = aB[q - 2 + a], Bim1 = aB[q - 1 + a], Bi0 = aB[q + a], Bip1 = aB[q + 1 + a];
+            const double Dim1 = aD[q - 1 + a], Di0 = aD[q + a];
+            orc_source as = {AUX_SRC, tfsf[i].omega0, tfsf[i].tau, tfsf[i].t0, tfsf[i].amp};
+            orc_run_tfsf(&aux[i], 1, &as, 0, NULL, 0, NULL, n - 1, 1, aB, aD);
+            const double Bn_m1 = aB[q - 1 + a];
+            const double e = bg[2 * i], m = bg[2 * i + 1];
+            double ie, im, bc;
+            if (p->kind == 0) {
+                ie = 1.0 / e; im = 1.0 / m; bc = beta;
+            } else {
+                const double den = e * m - beta * beta, g = 1.0 - beta * beta;
+                ie = g * m / den; im = g * e / den; bc = beta * g / den;
+            }
+            const double hb = 0.5 * bc;
+            double* c = &corr[6 * i];
+            if (pos) {
+                c[0] = 0.0;
+                c[1] = S * ie * Di0;
+                c[2] = -S * hb * Bim2 + beta * S * Bim1;
+                c[3] = -S * hb * Bim1;
+                c[4] = -S * hb * Di0;
+                c[5] = S * (im * Bn_m1 - hb * Dim1) + beta * S * Dim1;
+            } else {
+                c[0] = -S * hb * Bi0;
+                c[1] = S * ie * Di0 - S * hb * Bip1 + beta * S * Bi0;
+                c[2] = 0.0;
+                c[3] = 0.0;
+                c[4] = -S * hb * Di0 + beta * S * Di0;
+                c[5] = S * (im * Bn_m1 - hb * Dim1);
+            }
+        }
 
         /* E*^{n-1/2} (Eq. Dconst_discr with Table 1 Ba/Bb, B at level n-1) */
         for (int64_t k = 0; k < nz; ++k) {
@@ -228,6 +344,11 @@ int orc_run(const orc_problem* p, int n_src, const orc_source* src,
         }
         if (p->absorb_width > 0)
             for (int64_t k = 0; k < nz; ++k) B[k] *= absorb_factor(p, (double)k + 0.5);
+        for (int i = 0; i < nt; ++i)
+            for (int j = 0; j < 4; ++j) {
+                const int64_t k = tfsf[i].node - 2 + j;
+                if (k >= 0 && k < nz) B[k] += corr[6 * i + j];
+            }
 
         /* H*^n (Eq. Bconst_discr with Table 1 Da/Db, D at level n-1/2) */
         for (int64_t k = 0; k < nz; ++k) {
@@ -244,6 +365,11 @@ int orc_run(const orc_problem* p, int n_src, const orc_source* src,
         }
         if (p->absorb_width > 0)
             for (int64_t k = 0; k < nz; ++k) D[k] *= absorb_factor(p, (double)k);
+        for (int i = 0; i < nt; ++i)
+            for (int j = 0; j < 2; ++j) {
+                const int64_t k = tfsf[i].node - 1 + j;
+                if (k >= 0 && k < nz) D[k] += corr[6 * i + 4 + j];
+            }
 
         /* soft source at t_{n+1/2} */
         const double t = (double)(2 * n + 1) * S * 0.5;
@@ -273,7 +399,7 @@ int orc_run(const orc_problem* p, int n_src, const orc_source* src,
             }
         }
     }
-    free(zq); free(Es); free(Hs); free(Bo); free(Do);
+    free(zq); free(Es); free(Hs); free(Bo); free(Do); free(aux); free(bg); free(corr);
     return 0;
 }
 

@@ -1,0 +1,117 @@
+"""Pins of the oracle's one-way (total-field / scattered-field) source.
+
+The scattered-field region of a uniform medium stays empty up to what the
+auxiliary grid's absorbing layers reflect; the total field equals the wave a
+soft source (the scheme's own, without any correction) radiates to its right;
+and with a moving interface in the total-field region the scattered-field
+probe alone gives Eq. coef_interface's |Gamma|, with no reference run to
+subtract.
+"""
+import numpy as np
+import pytest
+
+from oracle import Instance, exact
+from oracle import vonneumann as vn
+
+AUX_OFFSET = 12     # the auxiliary soft source sits 12 cells left of the boundary
+
+
+def _pulse(lam0=40.0, periods=3.0):
+    w0 = 2 * np.pi / lam0
+    tau = periods * lam0 / (2 * np.sqrt(np.log(2)))
+    return w0, tau, 4 * tau
+
+
+CASES = [(0.0, 0, 1.0, 1.0), (0.3, 0, 1.0, 1.0), (-0.3, 0, 2.0, 1.0), (0.6, 0, 1.0, 1.0),
+         (-0.45, 0, 1.5, 1.2), (0.3, 1, 1.0, 1.0), (-0.2, 1, 2.25, 1.0), (0.4, 1, 3.0, 1.0)]
+
+
+@pytest.mark.parametrize("beta,kind,eps,mu", CASES)
+def test_scattered_region_stays_empty(beta, kind, eps, mu):
+    """Largest field left of the boundary's correction cells over 2500 steps,
+    relative to the largest total field (moving matter with n' > 1 damps the
+    pulse as it travels, the scheme's own dissipation of reading R3)."""
+    q = 600
+    I = Instance(3000, 0.5, beta, kind=kind, eps=[eps], mu=[mu])
+    I.add_tfsf(q, *_pulse())
+    tf = sf = 0.0
+    for _ in range(10):
+        I.run(250)
+        tf = max(tf, np.abs(I.D[q:]).max(), np.abs(I.B[q:]).max())
+        sf = max(sf, np.abs(I.D[:q - 1]).max(), np.abs(I.B[:q - 2]).max())
+    assert tf > 0.1
+    assert sf <= (1e-8 if beta == 0 else 3e-6) * tf, (sf, tf)
+
+
+@pytest.mark.parametrize("beta,kind,eps,mu", CASES)
+def test_total_field_is_the_soft_source_wave(beta, kind, eps, mu):
+    """Total field right of the boundary = right-going wave of a plain soft
+    source 12 cells left of it (a separate run with no correction terms),
+    while the pulse has not reached either end of that run."""
+    q, nz, steps = 2000, 4200, 2400
+    w0, tau, t0 = _pulse()
+    A = Instance(nz, 0.5, beta, kind=kind, eps=[eps], mu=[mu])
+    A.add_tfsf(q, w0, tau, t0)
+    A.run(steps)
+    R = Instance(nz, 0.5, beta, kind=kind, eps=[eps], mu=[mu])
+    R.add_source(q - AUX_OFFSET, w0, tau, t0)
+    R.run(steps)
+    for a, r in ((A.D[q:], R.D[q:]), (A.B[q:], R.B[q:])):
+        assert np.abs(r).max() > 1e-3
+        assert np.linalg.norm(a - r) <= 1e-5 * np.linalg.norm(r)
+
+
+def test_zero_velocity_corrections_are_textbook_tfsf():
+    """At v = 0 the correction terms reduce to the textbook 1D TF/SF pair:
+    B_{q-1} += S Einc_q, D_q += S Hinc_{q-1}.  Checked through the fields: a
+    run whose boundary sits at q equals the same run shifted by one cell when
+    the medium is uniform (the corrections are translation invariant), and
+    the scattered region is empty to 1e-8."""
+    w0, tau, t0 = _pulse()
+    runs = []
+    for q in (700, 701):
+        I = Instance(3000, 0.5, 0.0, eps=[2.0])
+        I.add_tfsf(q, w0, tau, t0)
+        I.run(1500)
+        runs.append(I)
+    assert np.allclose(runs[0].D[700:2500], runs[1].D[701:2501], rtol=0, atol=1e-12)
+    assert np.abs(runs[0].D[:699]).max() < 1e-8 * np.abs(runs[0].D).max()
+
+
+@pytest.mark.slow
+def test_moving_interface_reflection_without_reference_run():
+    """Fig. 5 parameters (v = -0.3c, eps 2 | 4, S = 0.2, lambda0 = 150 cells):
+    the scattered-field probe records only the reflected pulse, whose spectrum
+    over the incident one (a total-field probe before the reflection returns)
+    gives |Gamma| of Eq. coef_interface within 1% after the scheme's own
+    propagation loss is removed."""
+    beta, e1, e2, S, lam0 = -0.3, 2.0, 4.0, 0.2, 150.0
+    w0, tau, t0 = _pulse(lam0, 3)
+    q, zI, zr, zi, nz, t_end = 1000, 3000, 950, 1050, 4500, 6000.0
+    steps = int(t_end / S)
+    ex = exact.interface(e1, e2, beta)
+    I = Instance(nz, S, beta, eps=[e1, e2], z=[zI])
+    I.add_tfsf(q, w0, tau, t0)
+    I.add_probe(zr, [w0])
+    I.add_probe(zi, [w0])
+    I.run(steps, record=True)
+    fr, fi = I.series(0), I.series(1)
+    t = (np.arange(steps) + 1.5) * S
+    n1 = np.sqrt(e1)
+    src = q - AUX_OFFSET
+    tm = (zI - src + t0 / n1) / (1 / n1 - beta)       # pulse centre meets the interface
+    zm = zI + beta * tm
+    t_back = tm + (zm - zi) / (1 / n1 + beta)          # reflected centre back at zi
+    mask_i = t < t_back - 3 * tau
+    # the incident pulse has passed zi before the mask closes, and the
+    # reflected pulse has passed zr before the run ends
+    assert np.abs(fi[mask_i][-200:]).max() < 1e-4 * np.abs(fi).max()
+    assert np.abs(fr[-200:]).max() < 1e-4 * np.abs(fr).max()
+    for f in (0.95, 1.0, 1.05):
+        w = f * w0
+        Xi = np.sum(fi * mask_i * np.exp(1j * w * t)) * S
+        Xr = np.sum(fr * np.exp(1j * ex["a_r"] * w * t)) * S
+        li = vn.propagation_loss(S, beta, e1, 1.0, w, zm - zi, +1)
+        lr = vn.propagation_loss(S, beta, e1, 1.0, ex["a_r"] * w, zm - zr, -1)
+        G = ex["a_r"] * abs(Xr) / abs(Xi) / (li * lr)
+        assert abs(G / abs(ex["Gamma"]) - 1) < 0.01, (f, G, ex["Gamma"])
