@@ -155,6 +155,30 @@ gfdtd_status gfdtd_set_absorber(gfdtd_ctx* ctx, int inst, int64_t width, double 
 gfdtd_status gfdtd_add_source(gfdtd_ctx* ctx, int inst, int64_t node, double omega0,
                               double tau, double t0, double amp);
 
+/* Add a one-way (total-field / scattered-field) source to instance `inst`
+ * (an option of this library; the paper's source is the soft one above).
+ * Nodes >= node hold the total field, nodes < node the scattered field, and
+ * the incident wave enters the total-field region only: it is the right-going
+ * wave that a soft source with this waveform emits in an auxiliary FP64 grid
+ * of the same scheme filled with the uniform background, taken as the
+ * material at `node` at t = 0 (1064 cells, graded layers of 512 cells and
+ * strength 0.05 at both ends, the auxiliary soft source 12 cells left of the
+ * boundary).  Each step, the updates of B at node-2 .. node+1 and of D at
+ * node-1 .. node that read a neighbour across the boundary get that
+ * neighbour's incident value added (total-field update) or subtracted
+ * (scattered-field update).  The background must stay uniform around the
+ * boundary for the whole run; what the auxiliary layers reflect (about 1e-6
+ * of the incident amplitude for |beta| <= 0.6) reaches the scattered-field
+ * region.  Tiles holding those cells take the general kernel; the auxiliary
+ * grids advance in their own launch per chunk of steps.  Adding a source
+ * restarts every auxiliary grid of the context from rest; write_fields and
+ * write_state leave them alone.  gfdtd_step_plain and gfdtd_adjoint reject
+ * contexts with one-way sources (E_UNSUPPORTED).  E_ARG unless node is in
+ * [0, nz), tau > 0, the other values finite, at most 4 per instance and 32
+ * per context.  Takes effect at the next step. */
+gfdtd_status gfdtd_add_tfsf(gfdtd_ctx* ctx, int inst, int64_t node, double omega0, double tau,
+                            double t0, double amp);
+
 /* Add a DFT probe at integer node `node` of instance `inst` with n_bins >= 1
  * angular frequencies omega[] (copied).  From the next step on, every step
  * adds E(node, t) exp(+i omega t) S to each bin, t = (n + 1/2) S, in FP64.

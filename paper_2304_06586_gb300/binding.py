@@ -52,6 +52,8 @@ SIGNATURES = {
                                    _dp, C.c_int]),
     "gfdtd_add_source": (C.c_int, [C.c_void_p, C.c_int, C.c_int64, C.c_double, C.c_double, C.c_double,
                                    C.c_double]),
+    "gfdtd_add_tfsf": (C.c_int, [C.c_void_p, C.c_int, C.c_int64, C.c_double, C.c_double, C.c_double,
+                                   C.c_double]),
     "gfdtd_add_probe": (C.c_int, [C.c_void_p, C.c_int, C.c_int64, C.c_int, _dp, C.POINTER(C.c_int)]),
     "gfdtd_step": (C.c_int, [C.c_void_p, C.c_int64]),
     "gfdtd_step_plain": (C.c_int, [C.c_void_p, C.c_int64]),
@@ -277,6 +279,12 @@ class Simulation:
     def add_source(self, inst, node, omega0, tau, t0, amp=1.0):
         self._check(self._L.gfdtd_add_source(self._h, inst, int(node), float(omega0), float(tau),
                                              float(t0), float(amp)), "add_source")
+
+    def add_tfsf(self, inst, node, omega0, tau, t0, amp=1.0):
+        """One-way source: total field at nodes >= node, the incident wave being the
+        right-going wave of a soft source with this waveform (gfdtd_add_tfsf)."""
+        self._check(self._L.gfdtd_add_tfsf(self._h, inst, int(node), float(omega0), float(tau),
+                                           float(t0), float(amp)), "add_tfsf")
 
     def add_probe(self, inst, node, omega):
         omega = _f64(np.atleast_1d(omega))

@@ -85,6 +85,7 @@ struct gfdtd_ctx {
   long long total = 0;                 // elements per field buffer
   std::vector<Medium> media;
   std::vector<std::vector<SrcDev>> sources;   // per instance
+  std::vector<std::vector<TfsfDev>> tfsf;     // per instance: one-way sources (background filled by finalize)
   std::vector<Probe> probes;                  // in creation order
   std::vector<std::vector<int>> inst_probes;  // per instance: indices into `probes`
 
@@ -104,6 +105,8 @@ struct gfdtd_ctx {
   std::vector<int> prb_bin0;
   int n_src = 0, n_prb = 0, n_bins = 0;
   std::vector<double> acc_keep_re, acc_keep_im;   // accumulators per creation-order bin
+  DevBuf d_tfsf, d_tfaux, d_tfcorr;     // one-way sources: records, auxiliary grids, corrections per chunk
+  int n_tfsf = 0;
 
   // tiling
   int C = 0, TB = 0, MB = 0;            // chosen tile shape (0 = autotune)
@@ -242,6 +245,32 @@ static void medium_coefs(gfdtd_kind kind, double beta, double e, double m, doubl
   *ie = g * m / den; *im = g * e / den; *bc = beta * g / den;
 }
 
+// Relative permittivity and permeability of a medium at moving coordinate xi
+// (units of 2^-32 cell): a layers profile holds value i on [z_{i-1}, z_i), a
+// linear one interpolates between knots and holds its end values beyond them.
+static void medium_at(const Medium& m, long long xi, double& e, double& u) {
+  const size_t n = m.eps.size();
+  if (m.interp == GFDTD_LINEAR) {
+    size_t j = 0;   // knots at or left of xi
+    while (j < n && to_fixed(m.z[j]) <= xi) ++j;
+    if (j == 0 || j == n) {
+      const size_t k = j == 0 ? 0 : n - 1;
+      e = m.eps[k];
+      u = m.mu[k];
+      return;
+    }
+    const long long z0 = to_fixed(m.z[j - 1]), z1 = to_fixed(m.z[j]);
+    const double w = (double)(xi - z0) / (double)(z1 - z0);
+    e = m.eps[j - 1] + w * (m.eps[j] - m.eps[j - 1]);
+    u = m.mu[j - 1] + w * (m.mu[j] - m.mu[j - 1]);
+    return;
+  }
+  size_t i = 0;     // boundaries at or left of xi
+  while (i + 1 < n && to_fixed(m.z[i]) <= xi) ++i;
+  e = m.eps[i];
+  u = m.mu[i];
+}
+
 // ------------------------------------------------------------------ finalize
 
 static std::vector<float2> to_f32(const std::vector<double2>& v) {
@@ -278,6 +307,13 @@ static gfdtd_status build_tiles(gfdtd_ctx* c, int C, int TB, std::vector<int2> o
       // output range, stay with the general kernel.
       int edge = 0;
       bool fast_tile = fast_ok && !(left && right);
+      // windows that hold a one-way source's correction cells run in the general kernel
+      auto holds_tfsf = [&](long long b) {
+        for (const TfsfDev& t : c->tfsf[i])
+          if (t.node + 1 >= b && t.node - 2 < b + span) return true;
+        return false;
+      };
+      if (holds_tfsf(base)) fast_tile = false;
       const bool damped = window_absorbs(d, base, span);
       if (fast_tile && left) {
         base = 0;
@@ -289,6 +325,7 @@ static gfdtd_status build_tiles(gfdtd_ctx* c, int C, int TB, std::vector<int2> o
         // the two cells before nz must lie in the last lane's run (B_nz-1 + B_nz-2 term)
         if (base < 0 || base + L > x0 || base + span - nz > C - 2) fast_tile = false;
       }
+      if (fast_tile && edge && holds_tfsf(base)) fast_tile = false;
       const int v = matter ? 1 : (fast_tile ? 2 : 0);
       (v == 2 && damped ? pdamp[pos ? 0 : 1] : part[v][pos ? 0 : 1]).push_back(make_int2(i, (int)x0));
       c->valid_cells[v] += std::min<long long>(W, nz - x0);
@@ -492,6 +529,32 @@ static gfdtd_status finalize(gfdtd_ctx* c) {
   if ((s = dalloc(c, c->d_amp, std::max<size_t>(16, (size_t)c->n_src * kChunk * sizeof(double)))) ||
       (s = dalloc(c, c->d_samples, std::max<size_t>(16, (size_t)c->n_prb * kChunk * sizeof(double)))))
     return s;
+  // one-way sources: background coefficients of the material at the boundary node at t = 0
+  std::vector<TfsfDev> tfs;
+  for (int i = 0; i < c->n_inst; ++i)
+    for (TfsfDev t : c->tfsf[i]) {
+      const Medium& m = c->media[i];
+      double e, u;
+      medium_at(m, (long long)t.node << 32, e, u);
+      double ie, im, bc;
+      medium_coefs(m.kind, m.beta, e, u, &ie, &im, &bc);
+      t.ie = ie;
+      t.im = im;
+      t.hb = 0.5 * bc;
+      t.beta = m.beta;
+      t.S = S;
+      tfs.push_back(t);
+    }
+  if ((s = upload(c, c->d_tfsf, tfs))) return s;
+  if ((int)tfs.size() != c->n_tfsf) {
+    // a new set of auxiliary grids starts from rest (the existing ones keep their state otherwise)
+    const size_t aux_bytes = std::max<size_t>(16, tfs.size() * 2 * kTfsfAuxN * sizeof(double));
+    if ((s = dalloc(c, c->d_tfaux, aux_bytes)) ||
+        (s = dalloc(c, c->d_tfcorr, std::max<size_t>(16, tfs.size() * kChunk * kTfsfCorr * sizeof(double)))))
+      return s;
+    CK(c, cudaMemsetAsync(c->d_tfaux.p, 0, aux_bytes, c->stream));
+    c->n_tfsf = (int)tfs.size();
+  }
   c->dirty = false;
   drop_graphs(c);
   if (c->C > 0) {
@@ -543,6 +606,9 @@ static gfdtd_status enqueue_block(gfdtd_ctx* c, cudaStream_t st, int from, int s
     a.track = (k == 2 && record) ? (TrackTile*)c->d_track.p : nullptr;   // tuning trials leave it alone
     a.dseg = nullptr;
     a.dseg_stride = 0;
+    a.tfsf = sources && c->n_tfsf > 0 ? (const TfsfDev*)c->d_tfsf.p : nullptr;
+    a.n_tfsf = sources ? c->n_tfsf : 0;
+    a.tf_corr = (const double*)c->d_tfcorr.p;
     a.s0 = s0;
     a.nsteps = nsteps;
     a.record = record ? 1 : 0;
@@ -593,12 +659,23 @@ static gfdtd_status enqueue_fold_advance(gfdtd_ctx* c, cudaStream_t st, int nste
 }
 
 // One chunk of the batched path; returns the number of block launches (for parity).
+static gfdtd_status enqueue_tfsf(gfdtd_ctx* c, cudaStream_t st, int nsteps) {
+  if (c->n_tfsf > 0) {
+    CKI(c, tfsf_aux_launch((const TfsfDev*)c->d_tfsf.p, c->n_tfsf, (double*)c->d_tfaux.p,
+                           (double*)c->d_tfcorr.p, kChunk, (const long long*)c->d_ndone.p, nsteps, st));
+    ++c->launches;
+  }
+  return GFDTD_OK;
+}
+
 static gfdtd_status enqueue_chunk(gfdtd_ctx* c, cudaStream_t st, int from, int nsteps, int* nlaunch) {
   if (c->n_src > 0) {
     CKI(c, src_amp_launch((const SrcDev*)c->d_srcs.p, c->n_src, (double*)c->d_amp.p, kChunk, nsteps,
                           (const long long*)c->d_ndone.p, c->S, st));
     ++c->launches;
   }
+  gfdtd_status ts = enqueue_tfsf(c, st, nsteps);
+  if (ts) return ts;
   int b = from, m = 0;
   for (int s0 = 0; s0 < nsteps; s0 += c->TB) {
     gfdtd_status s = enqueue_block(c, st, b, s0, std::min(c->TB, nsteps - s0), true, true);
@@ -632,7 +709,7 @@ static gfdtd_status run_chunk(gfdtd_ctx* c, int nsteps) {
   CK(c, cudaGraphLaunch(it->second, c->stream));
   const int kinds = (c->n_tiles[0] > 0) + (c->n_tiles[1] > 0) + (c->n_tiles[2] > c->n_fast_damped) +
                     (c->n_fast_damped > 0);
-  c->launches += (long long)m * kinds + (c->n_src > 0) + (c->n_bins > 0) + 1;
+  c->launches += (long long)m * kinds + (c->n_src > 0) + (c->n_tfsf > 0) + (c->n_bins > 0) + 1;
   if (m & 1) c->cur = 1 - c->cur;
   c->n_done += nsteps;
   return GFDTD_OK;
@@ -749,6 +826,8 @@ extern "C" gfdtd_status gfdtd_adjoint(gfdtd_ctx* c, int64_t n_steps, int probe_i
       return fail(c, GFDTD_E_UNSUPPORTED, "the adjoint is built for moving perturbation");
     if (c->media[i].absorb_width > 0)
       return fail(c, GFDTD_E_UNSUPPORTED, "the adjoint has no absorbing layers");
+    if (!c->tfsf[i].empty())
+      return fail(c, GFDTD_E_UNSUPPORTED, "the adjoint covers soft sources only");
     if (probe_id < 0 || probe_id >= (int)c->inst_probes[i].size())
       return fail(c, GFDTD_E_ARG, "instance %d has no probe %d", i, probe_id);
     if ((int)c->probes[c->inst_probes[i][probe_id]].omega.size() < bin_hi)
@@ -948,6 +1027,7 @@ gfdtd_status gfdtd_create(gfdtd_ctx** out, int n_inst, const int64_t* nz, double
   c->total = o + 32;   // one spare padded segment
   c->media.assign(n_inst, Medium());
   c->sources.assign(n_inst, {});
+  c->tfsf.assign(n_inst, {});
   c->inst_probes.assign(n_inst, {});
   int dev = 0;
   gfdtd_status s = GFDTD_OK;
@@ -1056,6 +1136,29 @@ gfdtd_status gfdtd_add_source(gfdtd_ctx* c, int inst, int64_t node, double omega
   d.t0 = t0;
   d.amp = amp;
   c->sources[inst].push_back(d);
+  c->dirty = true;
+  return GFDTD_OK;
+}
+
+gfdtd_status gfdtd_add_tfsf(gfdtd_ctx* c, int inst, int64_t node, double omega0, double tau, double t0,
+                            double amp) {
+  gfdtd_status s = check_inst(c, inst);
+  if (s) return s;
+  if (node < 0 || node >= c->nz[inst]) return fail(c, GFDTD_E_ARG, "one-way source node out of range");
+  if (!(tau > 0.0) || !std::isfinite(omega0) || !std::isfinite(t0) || !std::isfinite(amp))
+    return fail(c, GFDTD_E_ARG, "bad source parameters");
+  if (c->tfsf[inst].size() >= 4) return fail(c, GFDTD_E_ARG, "at most 4 one-way sources per instance");
+  int total = 0;
+  for (const auto& v : c->tfsf) total += (int)v.size();
+  if (total >= 32) return fail(c, GFDTD_E_ARG, "at most 32 one-way sources per context");
+  TfsfDev t{};
+  t.inst = inst;
+  t.node = (int)node;
+  t.omega0 = omega0;
+  t.tau = tau;
+  t.t0 = t0;
+  t.amp = amp;
+  c->tfsf[inst].push_back(t);
   c->dirty = true;
   return GFDTD_OK;
 }
@@ -1197,6 +1300,7 @@ gfdtd_status gfdtd_profile_kernels(gfdtd_ctx* c, int64_t n_steps, gfdtd_kernel_t
       }
       ++c->launches;
     }
+    if (s == GFDTD_OK) s = enqueue_tfsf(c, c->stream, ch);
     int b = c->cur, m = 0;
     for (int s0 = 0; s0 < ch && s == GFDTD_OK; s0 += c->TB) {
       const int nsteps = std::min(c->TB, ch - s0);
@@ -1251,6 +1355,7 @@ gfdtd_status gfdtd_step_plain(gfdtd_ctx* c, int64_t n_steps) {
   if (n_steps < 0) return fail(c, GFDTD_E_ARG, "n_steps < 0");
   gfdtd_status s = finalize(c);
   if (s) return s;
+  if (c->n_tfsf > 0) return fail(c, GFDTD_E_UNSUPPORTED, "one-way sources run in gfdtd_step only");
   while (n_steps > 0) {
     const int ch = (int)std::min<int64_t>(n_steps, kChunk);
     for (int st = 0; st < ch; ++st) {

@@ -129,6 +129,23 @@ struct TrackTile {
 static_assert(sizeof(TrackTile) % 16 == 0, "TrackTile is copied by TMA in 16-byte units");
 
 // Arguments of one time-block launch of the batched kernel.
+// One-way (total-field / scattered-field) source: total field at nodes >= node.
+// Its incident wave is computed in an auxiliary FP64 grid of the same scheme in
+// the uniform background (the material at `node` at t = 0): kTfsfAuxN cells,
+// graded absorbing layers of kTfsfAuxW cells and strength kTfsfAuxSigma at both
+// ends, a soft source with the given waveform at aux node kTfsfAuxSrc and the
+// boundary at aux node kTfsfAuxQ.
+struct TfsfDev {
+  int inst;
+  int node;
+  double ie, im, hb;            // background 1/eps_m, 1/mu_m and beta_c / 2
+  double beta, S;
+  double omega0, tau, t0, amp;  // waveform of the auxiliary soft source
+};
+constexpr int kTfsfAuxN = 1064, kTfsfAuxW = 512, kTfsfAuxSrc = 520, kTfsfAuxQ = 532;
+constexpr double kTfsfAuxSigma = 0.05;
+constexpr int kTfsfCorr = 6;    // corrections per step: B at node-2 .. node+1, D at node-1 .. node
+
 template <typename T>
 struct BlockArgs {
   const InstDev* inst;
@@ -157,6 +174,9 @@ struct BlockArgs {
   TrackTile* track;           // fast kernel: tracker state per tile, kept between launches; NULL: not kept
   T* dseg;                    // general kernel: D after each step s goes to dseg + (s0 + s + 1) dseg_stride
   long long dseg_stride;      // (NULL: not recorded)
+  const TfsfDev* tfsf;        // general kernel: one-way sources (n_tfsf of them; NULL: none)
+  int n_tfsf;
+  const double* tf_corr;      // [source][step in chunk (chunk_stride)][kTfsfCorr] additive corrections
 };
 
 // Arguments of the plain kernel (one instance, one step).
@@ -236,6 +256,10 @@ struct SourceAdjArgs {
   double* gn;                 // [step][inst]
 };
 int adjoint_step_launch(const AdjArgs& a, cudaStream_t st);
+// Advances the auxiliary grids of n one-way sources by nsteps steps from step
+// *n_done and writes each step's corrections to corr ([source][chunk_stride][kTfsfCorr]).
+int tfsf_aux_launch(const TfsfDev* tf, int n, double* aux, double* corr, int chunk_stride,
+                    const long long* n_done, int nsteps, cudaStream_t st);
 int sum_copies_launch(const double* copies, long long n_copies, long long stride, long long n, double* out,
                       cudaStream_t st);
 int probe_adjoint_launch(const ProbeAdjArgs& a, cudaStream_t st);
