@@ -64,15 +64,16 @@ def _pair(wl, tf, prec=gb.F32, tuning=None):
 
 
 def _compare(wl, sim, orcs, tol):
+    # spectra: relative L2, with probes that saw little (a pulse damped by
+    # moving matter, a weak reflection) measured against 1 % of the largest
+    # probe spectrum of the workload (an FP32 rounding of the incident wave is
+    # 1e-7 of that)
+    scale = max(np.linalg.norm(o.spectrum(p)) for o in orcs for p in range(len(o.probes)))
     for k, I in enumerate(wl.instances):
         for which, ref in ((gb.FIELD_B, orcs[k].B), (gb.FIELD_D, orcs[k].D)):
             assert np.abs(ref).max() > 1e-3, (k, which)
             e = rel_l2(sim.read_fields(k, which), ref)
             assert e <= tol, (k, I.nz, I.beta, which, e)
-        # spectra: relative L2, with probes that saw little (a pulse damped by
-        # moving matter, a reflection still on its way) measured against 1 % of
-        # the instance's largest probe spectrum
-        scale = max(np.linalg.norm(orcs[k].spectrum(p)) for p in range(len(I.probes)))
         for p, (node, om) in enumerate(I.probes):
             ref = orcs[k].spectrum(p)
             e = np.linalg.norm(sim.read_spectrum(k, p, len(om)) - ref) / max(np.linalg.norm(ref), 1e-2 * scale)
