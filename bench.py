@@ -534,6 +534,31 @@ def main():
             for k in range(len(wl.instances)):
                 sim.set_absorber(k, 0, 0.0)
 
+        # one-way sources: the same crystal with every soft source replaced by a
+        # one-way source at its node (a second context, same tile shape)
+        tfsf = None
+        if not args.no_sweeps:
+            sim2 = gb.Simulation([i.nz for i in wl.instances], wl.S, gb.F32, stream=stream.cuda_stream)
+            for k, I in enumerate(wl.instances):
+                sim2.set_medium(k, I.kind, I.beta, I.interp, I.z, I.eps, I.mu, allow_unstable=True)
+                for src in I.sources:
+                    sim2.add_tfsf(k, *src)
+                for p in I.probes:
+                    sim2.add_probe(k, p[0], p[1])
+            sim2.set_tuning(st["cells_per_lane"], st["time_block"], st["blocks_per_sm"])
+            sim2.step(T)
+            t0e, t1e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            barrier()
+            t0e.record(stream)
+            sim2.step(T)
+            t1e.record(stream)
+            barrier()
+            tv = cells * T / (t0e.elapsed_time(t1e) / 1e3) / 1e9
+            tfsf = {"value": tv, "unit": "Gcell-updates/s",
+                    "sources": sum(len(i.sources) for i in wl.instances),
+                    "relative_to_value": tv / (value / world)}
+            sim2.close()
+
         # plain kernel (one step, one instance per launch) on a few steps
         plain = None
         if args.plain_steps > 0:
@@ -566,7 +591,7 @@ def main():
                        "parallelism": "instances sharded per rank" if world > 1 else "1 GPU"},
             "e2e": e2e, "gpu_launches": launches, "roofline": roofline, "plain": plain,
             "clocks": clocks, "sweeps": sweeps, "capture": capture, "absorber": absorber, "adjoint": adjoint,
-            "examples": examples}
+            "tfsf": tfsf, "examples": examples}
     if not args.no_cpu:
         line["cpu_baseline"] = cpu_baseline(wl, single_core=True)
     print(json.dumps(line), flush=True)

@@ -159,8 +159,9 @@ gfdtd_status gfdtd_add_source(gfdtd_ctx* ctx, int inst, int64_t node, double ome
  * (an option of this library; the paper's source is the soft one above).
  * Nodes >= node hold the total field, nodes < node the scattered field, and
  * the incident wave enters the total-field region only: it is the right-going
- * wave that a soft source with this waveform emits in an auxiliary FP64 grid
- * of the same scheme filled with the uniform background, taken as the
+ * wave that a soft source with this waveform emits in an auxiliary grid of
+ * the same scheme (FP64 for FP64 fields, FP32 otherwise) filled with the
+ * uniform background, taken as the
  * material at `node` at t = 0 (1064 cells, graded layers of 512 cells and
  * strength 0.05 at both ends, the auxiliary soft source 12 cells left of the
  * boundary).  Each step, the updates of B at node-2 .. node+1 and of D at
@@ -174,8 +175,8 @@ gfdtd_status gfdtd_add_source(gfdtd_ctx* ctx, int inst, int64_t node, double ome
  * restarts every auxiliary grid of the context from rest; write_fields and
  * write_state leave them alone.  gfdtd_step_plain and gfdtd_adjoint reject
  * contexts with one-way sources (E_UNSUPPORTED).  E_ARG unless node is in
- * [0, nz), tau > 0, the other values finite, at most 4 per instance and 32
- * per context.  Takes effect at the next step. */
+ * [0, nz), tau > 0, the other values finite, at most 4 per instance.  Takes
+ * effect at the next step. */
 gfdtd_status gfdtd_add_tfsf(gfdtd_ctx* ctx, int inst, int64_t node, double omega0, double tau,
                             double t0, double amp);
 

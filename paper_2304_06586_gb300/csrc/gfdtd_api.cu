@@ -426,9 +426,13 @@ static gfdtd_status finalize(gfdtd_ctx* c) {
   // creation-order bin offsets of each probe
   std::vector<size_t> keep_off(c->probes.size() + 1, 0);
   for (size_t p = 0; p < c->probes.size(); ++p) keep_off[p + 1] = keep_off[p] + c->probes[p].omega.size();
+  int n_tf = 0;
   for (int i = 0; i < c->n_inst; ++i) {
     const Medium& m = c->media[i];
     InstDev& d = inst[i];
+    d.tf0 = n_tf;
+    d.ntf = (int)c->tfsf[i].size();
+    n_tf += d.ntf;
     d.off = c->off[i];
     d.nz = (int)c->nz[i];
     d.nz_pad = (int)((c->nz[i] + 31) / 32 * 32);
@@ -661,7 +665,7 @@ static gfdtd_status enqueue_fold_advance(gfdtd_ctx* c, cudaStream_t st, int nste
 // One chunk of the batched path; returns the number of block launches (for parity).
 static gfdtd_status enqueue_tfsf(gfdtd_ctx* c, cudaStream_t st, int nsteps) {
   if (c->n_tfsf > 0) {
-    CKI(c, tfsf_aux_launch((const TfsfDev*)c->d_tfsf.p, c->n_tfsf, (double*)c->d_tfaux.p,
+    CKI(c, tfsf_aux_launch((const TfsfDev*)c->d_tfsf.p, c->n_tfsf, c->d_tfaux.p, c->prec == GFDTD_F64,
                            (double*)c->d_tfcorr.p, kChunk, (const long long*)c->d_ndone.p, nsteps, st));
     ++c->launches;
   }
@@ -1148,9 +1152,6 @@ gfdtd_status gfdtd_add_tfsf(gfdtd_ctx* c, int inst, int64_t node, double omega0,
   if (!(tau > 0.0) || !std::isfinite(omega0) || !std::isfinite(t0) || !std::isfinite(amp))
     return fail(c, GFDTD_E_ARG, "bad source parameters");
   if (c->tfsf[inst].size() >= 4) return fail(c, GFDTD_E_ARG, "at most 4 one-way sources per instance");
-  int total = 0;
-  for (const auto& v : c->tfsf) total += (int)v.size();
-  if (total >= 32) return fail(c, GFDTD_E_ARG, "at most 32 one-way sources per context");
   TfsfDev t{};
   t.inst = inst;
   t.node = (int)node;

@@ -366,7 +366,7 @@ __device__ __forceinline__ void kahan_add(R& x, R& cmp, R d) {
 }
 
 template <int C, int TB, bool POS, bool MATTER, bool EDGE, typename T, bool KAHAN = false>
-__device__ __forceinline__ void run_tile(const BlockArgs<T>& A, const InstDev& I, int inst, int x0, int W,
+__device__ __forceinline__ void run_tile(const BlockArgs<T>& A, const InstDev& I, int x0, int W,
                                          long long n0) {
   using R = typename Real<T>::type;
   const int lane = threadIdx.x & 31;
@@ -418,15 +418,17 @@ __device__ __forceinline__ void run_tile(const BlockArgs<T>& A, const InstDev& I
   }
   // one-way sources whose correction cells (node - 2 .. node + 1) lie in this window
   unsigned tmask = 0;
-  for (int q = 0; q < A.n_tfsf && q < 32; ++q) {
-    const TfsfDev& tf = A.tfsf[q];
-    if (tf.inst == inst && tf.node + 1 >= base && tf.node - 2 < base + 32 * C) tmask |= 1u << q;
+  if (A.n_tfsf > 0) {
+    for (int q = 0; q < I.ntf && q < 32; ++q) {
+      const int node = A.tfsf[I.tf0 + q].node;
+      if (node + 1 >= base && node - 2 < base + 32 * C) tmask |= 1u << q;
+    }
   }
   // adds the one-way sources' corrections of this step to the cells first .. first + n - 1
   // (corrections j0 .. j0 + n - 1 of the step's record)
   auto tfsf_add = [&](R (&F)[C], int s, int first_off, int j0, int n) {
     for (unsigned m = tmask; m; m &= m - 1) {
-      const int q = __ffs(m) - 1;
+      const int q = I.tf0 + __ffs(m) - 1;
       const int node = A.tfsf[q].node;
       const double* cr = A.tf_corr + ((long long)q * A.chunk_stride + A.s0 + s) * kTfsfCorr + j0;
       for (int j = 0; j < n; ++j) {
@@ -1052,13 +1054,13 @@ __global__ void __launch_bounds__(128) block_kernel(const BlockArgs<T> A) {
     if (I.flags & F_POS) {
       constexpr int W = tile_width(C, TB, true, V);
       const int base = x0 - tile_margin(TB, true, V);
-      if (base < 0 || base + 32 * C > I.nz) run_tile<C, TB, true, MATTER, true, T, KAHAN>(A, I, tl.x, x0, W, n0);
-      else run_tile<C, TB, true, MATTER, false, T, KAHAN>(A, I, tl.x, x0, W, n0);
+      if (base < 0 || base + 32 * C > I.nz) run_tile<C, TB, true, MATTER, true, T, KAHAN>(A, I, x0, W, n0);
+      else run_tile<C, TB, true, MATTER, false, T, KAHAN>(A, I, x0, W, n0);
     } else {
       constexpr int W = tile_width(C, TB, false, V);
       const int base = x0 - tile_margin(TB, false, V);
-      if (base < 0 || base + 32 * C > I.nz) run_tile<C, TB, false, MATTER, true, T, KAHAN>(A, I, tl.x, x0, W, n0);
-      else run_tile<C, TB, false, MATTER, false, T, KAHAN>(A, I, tl.x, x0, W, n0);
+      if (base < 0 || base + 32 * C > I.nz) run_tile<C, TB, false, MATTER, true, T, KAHAN>(A, I, x0, W, n0);
+      else run_tile<C, TB, false, MATTER, false, T, KAHAN>(A, I, x0, W, n0);
     }
   }
 }

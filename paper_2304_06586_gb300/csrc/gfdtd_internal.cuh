@@ -38,7 +38,7 @@ struct InstDev {
   double cb;         // S beta / 2: coupling in the Table 1 averages (moving perturbation)
   float a32, c32, cb32;   // a, c, cb rounded to FP32 (the FP32-arithmetic kernels read these)
   float sm32;              // S / mu of the first layer or knot in FP32: the uniform value when F_MU_CONST
-  int pad0, pad1;
+  int tf0, ntf;             // one-way sources of this instance: records tf0 .. tf0 + ntf - 1
   double abs_sigma;        // absorbing layers at both ends: strength at the outer end
   int abs_w;               // their width in cells (0: none)
   int pad2;
@@ -130,7 +130,7 @@ static_assert(sizeof(TrackTile) % 16 == 0, "TrackTile is copied by TMA in 16-byt
 
 // Arguments of one time-block launch of the batched kernel.
 // One-way (total-field / scattered-field) source: total field at nodes >= node.
-// Its incident wave is computed in an auxiliary FP64 grid of the same scheme in
+// Its incident wave is computed in an auxiliary grid of the same scheme in
 // the uniform background (the material at `node` at t = 0): kTfsfAuxN cells,
 // graded absorbing layers of kTfsfAuxW cells and strength kTfsfAuxSigma at both
 // ends, a soft source with the given waveform at aux node kTfsfAuxSrc and the
@@ -174,8 +174,8 @@ struct BlockArgs {
   TrackTile* track;           // fast kernel: tracker state per tile, kept between launches; NULL: not kept
   T* dseg;                    // general kernel: D after each step s goes to dseg + (s0 + s + 1) dseg_stride
   long long dseg_stride;      // (NULL: not recorded)
-  const TfsfDev* tfsf;        // general kernel: one-way sources (n_tfsf of them; NULL: none)
-  int n_tfsf;
+  const TfsfDev* tfsf;        // general kernel: one-way sources (instance i owns records
+  int n_tfsf;                 //   tf0 .. tf0 + ntf - 1 of its InstDev; NULL or n_tfsf 0: none)
   const double* tf_corr;      // [source][step in chunk (chunk_stride)][kTfsfCorr] additive corrections
 };
 
@@ -256,9 +256,10 @@ struct SourceAdjArgs {
   double* gn;                 // [step][inst]
 };
 int adjoint_step_launch(const AdjArgs& a, cudaStream_t st);
-// Advances the auxiliary grids of n one-way sources by nsteps steps from step
-// *n_done and writes each step's corrections to corr ([source][chunk_stride][kTfsfCorr]).
-int tfsf_aux_launch(const TfsfDev* tf, int n, double* aux, double* corr, int chunk_stride,
+// Advances the auxiliary grids of n one-way sources (FP64 or FP32 state, 2 kTfsfAuxN
+// values each) by nsteps steps from step *n_done and writes each step's corrections
+// to corr ([source][chunk_stride][kTfsfCorr]).
+int tfsf_aux_launch(const TfsfDev* tf, int n, void* aux, bool fp64, double* corr, int chunk_stride,
                     const long long* n_done, int nsteps, cudaStream_t st);
 int sum_copies_launch(const double* copies, long long n_copies, long long stride, long long n, double* out,
                       cudaStream_t st);

@@ -363,7 +363,9 @@ int capture_launch(int prec, int which, const InstDev* inst, int i, Tables tb, c
 // ---------------------------------------------------------------- one-way sources
 
 // One block per one-way source advances its auxiliary grid (the same leapfrog
-// step as the batched kernels, in FP64, uniform background, graded layers at
+// step as the batched kernels, in the arithmetic type R: FP64 for FP64 fields,
+// FP32 otherwise -- GB300's FP64 rate made an FP64 grid per source cost more
+// than the batch it drives; uniform background, graded layers at
 // both ends, soft source at kTfsfAuxSrc) through the chunk's steps in shared
 // memory, and writes for every step the additive corrections that make the
 // main grid's cells node-2 .. node+1 read each neighbour in their own region's
@@ -374,21 +376,25 @@ int capture_launch(int prec, int which, const InstDev* inst, int i, Tables tb, c
 //   D_q += S (im Bn_{q-1} - hb Di_{q-1}) (+ beta S Di_{q-1} for v >= 0),
 // with Bi, Di the incident B^{n-1}, D^{n-1/2} and Bn the incident B^n (aux
 // cell = main cell - q + kTfsfAuxQ).
-__global__ void __launch_bounds__(1024) tfsf_aux_kernel(const TfsfDev* __restrict__ tfs, double* __restrict__ aux,
-                                                        double* __restrict__ corr, int chunk_stride,
-                                                        const long long* __restrict__ n_done, int nsteps) {
+constexpr int kTfsfThreads = 256;   // one block per source: several blocks share an SM
+
+template <typename R>
+__global__ void __launch_bounds__(kTfsfThreads, 4) tfsf_aux_kernel(const TfsfDev* __restrict__ tfs, R* __restrict__ aux,
+                                                                double* __restrict__ corr, int chunk_stride,
+                                                                const long long* __restrict__ n_done, int nsteps) {
   constexpr int N = kTfsfAuxN, Q = kTfsfAuxQ;
-  constexpr int PER = (N + 1023) / 1024;     // cells per thread
-  __shared__ double sB[N], sD[N], sE[N], sH[N];
+  constexpr int PER = (N + kTfsfThreads - 1) / kTfsfThreads;   // cells per thread
+  __shared__ R sB[N], sD[N], sE[N], sH[N];
   const TfsfDev tf = tfs[blockIdx.x];
-  double* gB = aux + (size_t)blockIdx.x * 2 * N;
-  double* gD = gB + N;
-  const int tid = threadIdx.x, nt = blockDim.x;
+  R* gB = aux + (size_t)blockIdx.x * 2 * N;
+  R* gD = gB + N;
+  const int tid = threadIdx.x, nt = kTfsfThreads;
   for (int i = tid; i < N; i += nt) { sB[i] = gB[i]; sD[i] = gD[i]; }
-  const double S = tf.S, beta = tf.beta, ie = tf.ie, im = tf.im, hb = tf.hb;
+  const R S = (R)tf.S, beta = (R)tf.beta, ie = (R)tf.ie, im = (R)tf.im, hb = (R)tf.hb;
   const bool pos = beta >= 0.0;
   // damping factors of this thread's cells: exp(-sigma d^2), d the depth into a layer / its width
-  double fB[PER], fD[PER];
+  R fB[PER], fD[PER];
+#pragma unroll
   for (int j = 0; j < PER; ++j) {
     const int i = tid + j * nt;
     auto f = [&](double x) {
@@ -396,62 +402,66 @@ __global__ void __launch_bounds__(1024) tfsf_aux_kernel(const TfsfDev* __restric
       double d = 0.0;
       if (x < W) d = (W - x) / W;
       else if (x > right) d = (x - right) / W;
-      return exp(-kTfsfAuxSigma * d * d);
+      return (R)exp(-kTfsfAuxSigma * d * d);
     };
     fB[j] = f((double)i + 0.5);
     fD[j] = f((double)i);
   }
-  auto at = [&](const double* a, int i) { return (i < 0 || i >= N) ? 0.0 : a[i]; };
+  auto at = [&](const R* a, int i) { return (i < 0 || i >= N) ? (R)0 : a[i]; };
   const long long n0 = *n_done;
   double* out = corr + (size_t)blockIdx.x * chunk_stride * kTfsfCorr;
   __syncthreads();
   for (int s = 0; s < nsteps; ++s) {
     const long long n = n0 + s + 1;
-    double Bm2 = 0, Bm1 = 0, B0 = 0, Bp1 = 0, Dm1 = 0, D0 = 0;
+    R Bm2 = 0, Bm1 = 0, B0 = 0, Bp1 = 0, Dm1 = 0, D0 = 0;
     if (tid == 0) { Bm2 = sB[Q - 2]; Bm1 = sB[Q - 1]; B0 = sB[Q]; Bp1 = sB[Q + 1]; Dm1 = sD[Q - 1]; D0 = sD[Q]; }
     // E*^{n-1/2} = ie D - 2 hb Bbar (B at level n-1)
     for (int i = tid; i < N; i += nt) {
-      const double bbar = pos ? 0.5 * (at(sB, i - 1) + at(sB, i - 2)) : 0.5 * (at(sB, i + 1) + sB[i]);
-      sE[i] = ie * sD[i] - 2.0 * hb * bbar;
+      const R bbar = pos ? (R)0.5 * (at(sB, i - 1) + at(sB, i - 2)) : (R)0.5 * (at(sB, i + 1) + sB[i]);
+      sE[i] = ie * sD[i] - (R)2 * hb * bbar;
     }
     __syncthreads();
-    double nb[PER];
+    R nb[PER];
+#pragma unroll
     for (int j = 0; j < PER; ++j) {
       const int i = tid + j * nt;
       if (i < N) {
-        const double dB = pos ? sB[i] - at(sB, i - 1) : at(sB, i + 1) - sB[i];
+        const R dB = pos ? sB[i] - at(sB, i - 1) : at(sB, i + 1) - sB[i];
         nb[j] = (sB[i] - S * (at(sE, i + 1) - sE[i]) - beta * S * dB) * fB[j];
       }
     }
     __syncthreads();
+#pragma unroll
     for (int j = 0; j < PER; ++j) { const int i = tid + j * nt; if (i < N) sB[i] = nb[j]; }
     __syncthreads();
     // H*^n = im B^n - hb (D_j + D_{j+1}) (D at level n-1/2)
     for (int i = tid; i < N; i += nt) sH[i] = im * sB[i] - hb * (sD[i] + at(sD, i + 1));
     __syncthreads();
-    double nd[PER];
+    R nd[PER];
+#pragma unroll
     for (int j = 0; j < PER; ++j) {
       const int i = tid + j * nt;
       if (i < N) {
-        const double dD = pos ? sD[i] - at(sD, i - 1) : at(sD, i + 1) - sD[i];
+        const R dD = pos ? sD[i] - at(sD, i - 1) : at(sD, i + 1) - sD[i];
         nd[j] = (sD[i] - S * (sH[i] - at(sH, i - 1)) - beta * S * dD) * fD[j];
       }
     }
     __syncthreads();
+#pragma unroll
     for (int j = 0; j < PER; ++j) {
       const int i = tid + j * nt;
       if (i < N) {
-        double d = nd[j];
-        if (i == kTfsfAuxSrc) {
-          const double u = (double)(2 * n + 1) * S * 0.5 - tf.t0;
-          d += tf.amp * sin(tf.omega0 * u) * exp(-(u / tf.tau) * (u / tf.tau));
+        R d = nd[j];
+        if (i == kTfsfAuxSrc) {   // the source waveform in FP64, as for soft sources
+          const double u = (double)(2 * n + 1) * tf.S * 0.5 - tf.t0;
+          d += (R)(tf.amp * sin(tf.omega0 * u) * exp(-(u / tf.tau) * (u / tf.tau)));
         }
         sD[i] = d;
       }
     }
     __syncthreads();
     if (tid == 0) {
-      const double Bn = sB[Q - 1];
+      const R Bn = sB[Q - 1];
       double* c = out + (size_t)s * kTfsfCorr;
       if (pos) {
         c[0] = 0.0;
@@ -473,10 +483,13 @@ __global__ void __launch_bounds__(1024) tfsf_aux_kernel(const TfsfDev* __restric
   for (int i = tid; i < N; i += nt) { gB[i] = sB[i]; gD[i] = sD[i]; }
 }
 
-int tfsf_aux_launch(const TfsfDev* tf, int n, double* aux, double* corr, int chunk_stride,
+int tfsf_aux_launch(const TfsfDev* tf, int n, void* aux, bool fp64, double* corr, int chunk_stride,
                     const long long* n_done, int nsteps, cudaStream_t st) {
   if (n == 0 || nsteps == 0) return 0;
-  tfsf_aux_kernel<<<n, 1024, 0, st>>>(tf, aux, corr, chunk_stride, n_done, nsteps);
+  if (fp64)
+    tfsf_aux_kernel<double><<<n, kTfsfThreads, 0, st>>>(tf, (double*)aux, corr, chunk_stride, n_done, nsteps);
+  else
+    tfsf_aux_kernel<float><<<n, kTfsfThreads, 0, st>>>(tf, (float*)aux, corr, chunk_stride, n_done, nsteps);
   return (int)cudaGetLastError();
 }
 
