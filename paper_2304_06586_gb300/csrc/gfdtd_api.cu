@@ -1549,7 +1549,7 @@ void gfdtd_destroy(gfdtd_ctx* c) {
                     &c->d_ckB, &c->d_ckD, &c->d_dseg, &c->d_wB[0], &c->d_wB[1], &c->d_lB[0],
                     &c->d_lB[1], &c->d_lD[0], &c->d_lD[1], &c->d_grad, &c->d_gn, &c->d_adjn,
                     &c->d_Xre, &c->d_Xim, &c->d_bin0, &c->d_pnode, &c->d_acc0_re, &c->d_acc0_im,
-                    &c->d_adj_tiles};
+                    &c->d_adj_tiles, &c->d_tfsf, &c->d_tfaux, &c->d_tfcorr};
   for (DevBuf* b : bufs) dfree(c, *b);
   if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
   delete c;
