@@ -217,12 +217,13 @@ def example_measurements(gb, torch):
     return out
 
 
-CASES = ["adjoint", "interface", "slab"] + ["gradient-" + t for t in ("F32", "F32_KAHAN", "BF16", "F16", "F64")]
+CASES = ["adjoint", "interface", "slab", "tfsf"] + ["gradient-" + t for t in ("F32", "F32_KAHAN", "BF16", "F16", "F64")]
 
 
 def run_case(args):
     """One side workload alone (for profiling it): `adjoint` (256 x 2^14 PWL
-    profiles, gfdtd_adjoint over --time-steps steps), `interface` (FP64),
+    profiles, gfdtd_adjoint over --time-steps steps), `tfsf` (the crystal of
+    --instances instances with one-way sources), `interface` (FP64),
     `slab` (moving matter, FP32) or `gradient-<tier>` (2^20-cell ramp), through
     gfdtd_step with the tile shape of --tile if given.  Prints one JSON line."""
     import torch
@@ -237,6 +238,24 @@ def run_case(args):
         sim.adjoint(64, 0, 0, 16, nv)
         t0 = time.perf_counter()
         sim.adjoint(T, 0, 0, 16, nv)
+        dt = time.perf_counter() - t0
+    elif args.case == "tfsf":
+        # the batched crystal (--instances of them) with a one-way source in place of each soft source
+        wl = w.config3(n_inst=args.instances, n_steps=T)
+        sim = gb.Simulation([i.nz for i in wl.instances], wl.S, gb.F32)
+        for k, I in enumerate(wl.instances):
+            sim.set_medium(k, I.kind, I.beta, I.interp, I.z, I.eps, I.mu, allow_unstable=True)
+            for src in I.sources:
+                sim.add_tfsf(k, *src)
+            for p in I.probes:
+                sim.add_probe(k, p[0], p[1])
+        if args.tile:
+            sim.set_tuning(*[int(x) for x in args.tile.split(",")])
+        sim.step(64)
+        sim.synchronize()
+        t0 = time.perf_counter()
+        sim.step(T)
+        sim.synchronize()
         dt = time.perf_counter() - t0
     else:
         if args.case == "interface":

@@ -162,7 +162,7 @@ gfdtd_status gfdtd_add_source(gfdtd_ctx* ctx, int inst, int64_t node, double ome
  * wave that a soft source with this waveform emits in an auxiliary grid of
  * the same scheme (FP64 for FP64 fields, FP32 otherwise) filled with the
  * uniform background, taken as the
- * material at `node` at t = 0 (1064 cells, graded layers of 512 cells and
+ * material at `node` at t = 0 (1088 cells, graded layers of 524 cells and
  * strength 0.05 at both ends, the auxiliary soft source 12 cells left of the
  * boundary).  Each step, the updates of B at node-2 .. node+1 and of D at
  * node-1 .. node that read a neighbour across the boundary get that

@@ -67,9 +67,9 @@
  *   and the scattered-field region (k < q).  The incident wave is the
  *   right-going wave that a soft source with the given waveform emits in an
  *   auxiliary grid of the same scheme filled with the uniform background (the
- *   material at node q at t = 0): AUX_N = 1064 cells, graded absorbing layers
- *   of AUX_W = 512 cells and strength 0.05 at both ends, the soft source at
- *   aux node 520 and the boundary at aux node 532 (aux index = k - q + 532).
+ *   material at node q at t = 0): AUX_N = 1088 cells, graded absorbing layers
+ *   of AUX_W = 524 cells and strength 0.05 at both ends, the soft source at
+ *   aux node 532 and the boundary at aux node 544 (aux index = k - q + 544).
  *   (What the auxiliary layers reflect, about 1e-6 of the incident amplitude
  *   for |beta| <= 0.6, reaches the scattered-field region.)
  *   Every update that reads a value across the boundary reads it in the
@@ -127,10 +127,10 @@ typedef struct {
     double* aux_D;
 } orc_tfsf;
 
-#define AUX_N 1064
-#define AUX_W 512
-#define AUX_SRC 520
-#define AUX_Q 532
+#define AUX_N 1088
+#define AUX_W 524
+#define AUX_SRC 532
+#define AUX_Q 544
 
 typedef struct {
     int64_t node;

@@ -142,7 +142,7 @@ struct TfsfDev {
   double beta, S;
   double omega0, tau, t0, amp;  // waveform of the auxiliary soft source
 };
-constexpr int kTfsfAuxN = 1064, kTfsfAuxW = 512, kTfsfAuxSrc = 520, kTfsfAuxQ = 532;
+constexpr int kTfsfAuxN = 1088, kTfsfAuxW = 524, kTfsfAuxSrc = 532, kTfsfAuxQ = 544;
 constexpr double kTfsfAuxSigma = 0.05;
 constexpr int kTfsfCorr = 6;    // corrections per step: B at node-2 .. node+1, D at node-1 .. node
 

@@ -483,13 +483,156 @@ __global__ void __launch_bounds__(kTfsfThreads, 4) tfsf_aux_kernel(const TfsfDev
   for (int i = tid; i < N; i += nt) { gB[i] = sB[i]; gD[i] = sD[i]; }
 }
 
+// The FP32 auxiliary grid with one warp per source: every lane keeps 34
+// consecutive cells of B and D in registers through the chunk, neighbours move
+// by shuffles, and no block barrier is taken inside the time loop (the
+// shared-memory form above, with six barriers a step, made the sources' grids
+// cost as much as the batch they drive).  The damping factors, the same for
+// every source, sit in shared memory.
+constexpr int kAuxCPL = kTfsfAuxN / 32;
+static_assert(kTfsfAuxN % 32 == 0, "aux grid spread over the lanes of one warp");
+
+template <int K> struct AuxCell { static constexpr int lane = K / kAuxCPL, c = K % kAuxCPL; };
+
+__global__ void __launch_bounds__(128, 4) tfsf_aux_warp_kernel(const TfsfDev* __restrict__ tfs, int n_src,
+                                                            float* __restrict__ aux, double* __restrict__ corr,
+                                                            int chunk_stride, const long long* __restrict__ n_done,
+                                                            int nsteps) {
+  constexpr int N = kTfsfAuxN, CPL = kAuxCPL;
+  using Qm2 = AuxCell<kTfsfAuxQ - 2>;
+  using Qm1 = AuxCell<kTfsfAuxQ - 1>;
+  using Q0 = AuxCell<kTfsfAuxQ>;
+  using Qp1 = AuxCell<kTfsfAuxQ + 1>;
+  using Src = AuxCell<kTfsfAuxSrc>;
+  __shared__ float sfB[N], sfD[N];
+  for (int i = threadIdx.x; i < N; i += blockDim.x) {
+    auto f = [](double x) {
+      const double W = (double)kTfsfAuxW, right = (double)(N - 1) - W;
+      double d = 0.0;
+      if (x < W) d = (W - x) / W;
+      else if (x > right) d = (x - right) / W;
+      return (float)exp(-kTfsfAuxSigma * d * d);
+    };
+    sfB[i] = f((double)i + 0.5);
+    sfD[i] = f((double)i);
+  }
+  __syncthreads();
+  const int w = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  if (w >= n_src) return;                    // whole warps; no barrier follows
+  const int lane = threadIdx.x & 31, k0 = lane * CPL;
+  const TfsfDev tf = tfs[w];
+  float* gB = aux + (size_t)w * 2 * N;
+  float* gD = gB + N;
+  float B[CPL], D[CPL];
+#pragma unroll
+  for (int c = 0; c < CPL; ++c) { B[c] = gB[k0 + c]; D[c] = gD[k0 + c]; }
+  const float S = (float)tf.S, ie = (float)tf.ie, im = (float)tf.im, hb = (float)tf.hb;
+  const float uS = (float)(tf.beta * tf.S);
+  const bool pos = tf.beta >= 0.0, first = lane == 0, last = lane == 31;
+  const long long n0 = *n_done;
+  double* out = corr + (size_t)w * chunk_stride * kTfsfCorr;
+  for (int s = 0; s < nsteps; ++s) {
+    const long long n = n0 + s + 1;
+    // incident values before the step
+    const float Bm2 = __shfl_sync(FULL, B[Qm2::c], Qm2::lane), Bm1 = __shfl_sync(FULL, B[Qm1::c], Qm1::lane);
+    const float B0 = __shfl_sync(FULL, B[Q0::c], Q0::lane), Bp1 = __shfl_sync(FULL, B[Qp1::c], Qp1::lane);
+    const float Dm1 = __shfl_sync(FULL, D[Qm1::c], Qm1::lane), D0 = __shfl_sync(FULL, D[Q0::c], Q0::lane);
+    // E* = ie D - hb (two B of the Table 1 average), then B^n (old B throughout)
+    if (pos) {
+      const float t1 = __shfl_up_sync(FULL, B[CPL - 1], 1), t2 = __shfl_up_sync(FULL, B[CPL - 2], 1);
+      const float bl1 = first ? 0.0f : t1, bl2 = first ? 0.0f : t2;
+      const float e0 = ie * D[0] - hb * (bl1 + bl2);
+      const float te = __shfl_down_sync(FULL, e0, 1);
+      float en = last ? 0.0f : te;            // E* one cell to the right
+#pragma unroll
+      for (int c = CPL - 1; c >= 0; --c) {
+        const float b1 = c >= 1 ? B[c - 1] : bl1;
+        const float b2 = c >= 2 ? B[c - 2] : (c == 1 ? bl1 : bl2);
+        const float ec = ie * D[c] - hb * (b1 + b2);
+        B[c] = (B[c] - S * (en - ec) - uS * (B[c] - b1)) * sfB[k0 + c];
+        en = ec;
+      }
+    } else {
+      const float t1 = __shfl_down_sync(FULL, B[0], 1);
+      const float br1 = last ? 0.0f : t1;
+      const float e0 = ie * D[0] - hb * (B[1] + B[0]);
+      const float te = __shfl_down_sync(FULL, e0, 1);
+      const float er = last ? 0.0f : te;
+      float ec = e0;
+#pragma unroll
+      for (int c = 0; c < CPL; ++c) {
+        const float b1 = c + 1 < CPL ? B[c + 1] : br1;
+        const float b2 = c + 2 < CPL ? B[c + 2] : br1;          // used only for c + 2 == CPL
+        const float en = c + 1 < CPL ? ie * D[c + 1] - hb * (b2 + b1) : er;
+        B[c] = (B[c] - S * (en - ec) - uS * (b1 - B[c])) * sfB[k0 + c];
+        ec = en;
+      }
+    }
+    // H* = im B^n - hb (D_j + D_{j+1}), then D^{n+1/2} (old D throughout)
+    {
+      const float t1 = __shfl_down_sync(FULL, D[0], 1);
+      const float dr = last ? 0.0f : t1;
+      const float hlast = im * B[CPL - 1] - hb * (D[CPL - 1] + dr);
+      const float th = __shfl_up_sync(FULL, hlast, 1);
+      const float hl = first ? 0.0f : th;
+      if (pos) {
+        const float t2 = __shfl_up_sync(FULL, D[CPL - 1], 1);
+        const float dl = first ? 0.0f : t2;
+        float hc = hlast;
+#pragma unroll
+        for (int c = CPL - 1; c >= 0; --c) {
+          const float dp = c >= 1 ? D[c - 1] : dl;
+          const float hp = c >= 1 ? im * B[c - 1] - hb * (D[c - 1] + D[c]) : hl;
+          D[c] = (D[c] - S * (hc - hp) - uS * (D[c] - dp)) * sfD[k0 + c];
+          hc = hp;
+        }
+      } else {
+        float hp = hl;
+#pragma unroll
+        for (int c = 0; c < CPL; ++c) {
+          const float dn = c + 1 < CPL ? D[c + 1] : dr;
+          const float hc = im * B[c] - hb * (D[c] + dn);
+          D[c] = (D[c] - S * (hc - hp) - uS * (dn - D[c])) * sfD[k0 + c];
+          hp = hc;
+        }
+      }
+    }
+    if (lane == Src::lane) {   // the source waveform in FP64, as for soft sources
+      const double u = (double)(2 * n + 1) * tf.S * 0.5 - tf.t0;
+      D[Src::c] += (float)(tf.amp * sin(tf.omega0 * u) * exp(-(u / tf.tau) * (u / tf.tau)));
+    }
+    const float Bn = __shfl_sync(FULL, B[Qm1::c], Qm1::lane);
+    if (first) {
+      const double S_ = S, ie_ = ie, im_ = im, hb_ = hb, uS_ = uS;
+      double* c = out + (size_t)s * kTfsfCorr;
+      if (pos) {
+        c[0] = 0.0;
+        c[1] = S_ * ie_ * D0;
+        c[2] = -S_ * hb_ * Bm2 + uS_ * Bm1;
+        c[3] = -S_ * hb_ * Bm1;
+        c[4] = -S_ * hb_ * D0;
+        c[5] = S_ * (im_ * Bn - hb_ * Dm1) + uS_ * Dm1;
+      } else {
+        c[0] = -S_ * hb_ * B0;
+        c[1] = S_ * ie_ * D0 - S_ * hb_ * Bp1 + uS_ * B0;
+        c[2] = 0.0;
+        c[3] = 0.0;
+        c[4] = -S_ * hb_ * D0 + uS_ * D0;
+        c[5] = S_ * (im_ * Bn - hb_ * Dm1);
+      }
+    }
+  }
+#pragma unroll
+  for (int c = 0; c < CPL; ++c) { gB[k0 + c] = B[c]; gD[k0 + c] = D[c]; }
+}
+
 int tfsf_aux_launch(const TfsfDev* tf, int n, void* aux, bool fp64, double* corr, int chunk_stride,
                     const long long* n_done, int nsteps, cudaStream_t st) {
   if (n == 0 || nsteps == 0) return 0;
   if (fp64)
     tfsf_aux_kernel<double><<<n, kTfsfThreads, 0, st>>>(tf, (double*)aux, corr, chunk_stride, n_done, nsteps);
   else
-    tfsf_aux_kernel<float><<<n, kTfsfThreads, 0, st>>>(tf, (float*)aux, corr, chunk_stride, n_done, nsteps);
+    tfsf_aux_warp_kernel<<<(n + 3) / 4, 128, 0, st>>>(tf, n, (float*)aux, corr, chunk_stride, n_done, nsteps);
   return (int)cudaGetLastError();
 }
 
