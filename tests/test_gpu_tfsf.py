@@ -127,3 +127,9 @@ def test_tfsf_arguments_and_rejections():
     sim.add_tfsf(0, 800, w0, tau, t0)
     with pytest.raises(gb.GfdtdError):
         sim.step_plain(2)
+    with pytest.raises(gb.GfdtdError):
+        sim.adjoint(10, 0, 0, 1, [len(I.eps) for I in wl.instances])
+    for _ in range(4):
+        sim.add_tfsf(1, 700, w0, tau, t0)
+    with pytest.raises(gb.GfdtdError):          # at most 4 per instance
+        sim.add_tfsf(1, 701, w0, tau, t0)
