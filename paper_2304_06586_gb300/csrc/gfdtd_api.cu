@@ -582,7 +582,7 @@ static Tables tables_of(gfdtd_ctx* c) {
 
 // Enqueue one time-block launch (both kinds) reading buffer `from`.
 static gfdtd_status enqueue_block(gfdtd_ctx* c, cudaStream_t st, int from, int s0, int nsteps,
-                                  bool record, bool sources, int only = -1) {
+                                  bool record, bool sources, int only = -1, bool keep_track = false) {
   for (int k = 0; k < 3; ++k) {
     if (c->n_tiles[k] == 0 || (only >= 0 && k != only)) continue;
     // BlockArgs<T> has the same layout for every T (pointers), so fill the float version
@@ -607,7 +607,7 @@ static gfdtd_status enqueue_block(gfdtd_ctx* c, cudaStream_t st, int from, int s
     a.n_done = (const long long*)c->d_ndone.p;
     a.err = (int*)((char*)c->d_ndone.p + 8);
     a.ftiles = k == 2 ? (const FastTile*)c->d_ftiles.p : nullptr;
-    a.track = (k == 2 && record) ? (TrackTile*)c->d_track.p : nullptr;   // tuning trials leave it alone
+    a.track = (k == 2 && (record || keep_track)) ? (TrackTile*)c->d_track.p : nullptr;
     a.dseg = nullptr;
     a.dseg_stride = 0;
     a.tfsf = sources && c->n_tfsf > 0 ? (const TfsfDev*)c->d_tfsf.p : nullptr;
@@ -720,7 +720,10 @@ static gfdtd_status run_chunk(gfdtd_ctx* c, int nsteps) {
 }
 
 // Time the candidate tile shapes on the actual batch (reads the current
-// buffer, writes the other, records nothing) and keep the fastest.
+// buffer, writes the other, records nothing) and keep the fastest.  The trial
+// launches of a shape follow one another in time (s0 advances by a time block)
+// so that, as in a real run, each finds the boundary trackers the previous one
+// saved; set_tiles resets them for the shape finally kept.
 static gfdtd_status autotune(gfdtd_ctx* c) {
   int Cs[16], TBs[16], MBs[16];
   const int n = block_shapes(c->prec, Cs, TBs, MBs, 16);
@@ -737,12 +740,12 @@ static gfdtd_status autotune(gfdtd_ctx* c) {
     for (int i = 0; i < n; ++i) {
       gfdtd_status s = set_tiles(c, Cs[i], TBs[i], MBs[i]);
       if (s) return s;
-      s = enqueue_block(c, c->stream, c->cur, 0, TBs[i], false, false);
+      s = enqueue_block(c, c->stream, c->cur, 0, TBs[i], false, false, -1, true);
       if (s) return s;
       CK(c, cudaEventRecord(e0, c->stream));
       const int reps = 3;
-      for (int r = 0; r < reps; ++r) {
-        s = enqueue_block(c, c->stream, c->cur, 0, TBs[i], false, false);
+      for (int r = 1; r <= reps; ++r) {
+        s = enqueue_block(c, c->stream, c->cur, r * TBs[i], TBs[i], false, false, -1, true);
         if (s) return s;
       }
       CK(c, cudaEventRecord(e1, c->stream));
