@@ -462,6 +462,9 @@ def cpu_baseline(wl, n_inst=32, n_steps=100, seed=1, single_core=False):
     return out
 
 
+METRIC = "Gcell-updates/s batched vs plain on 1 GB300 at <=1e-4 L2 vs FP64; % of roofline"
+
+
 def run_reference(args, wl, rank):
     if rank != 0:
         return
@@ -471,7 +474,7 @@ def run_reference(args, wl, rank):
         vals.append(cpu_baseline(wl, n_inst=32, n_steps=60, seed=200 + i))
     v = float(np.mean([x["value"] for x in vals]))
     del per
-    line = {"impl": "reference", "metric": "Gcell-updates/s", "value": v, "unit": "Gcell-updates/s",
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "Gcell-updates/s",
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": wl.description},
@@ -633,7 +636,7 @@ def main():
     if rank != 0:
         return
     clocks = clk.summary()
-    line = {"metric": "Gcell-updates/s batched vs plain on 1 GB300 at <=1e-4 L2 vs FP64; % of roofline",
+    line = {"metric": METRIC,
             "value": value, "unit": "Gcell-updates/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
