@@ -6,7 +6,7 @@
 
 namespace gfdtd {
 
-#define GFDTD_SHAPES(X) X(8,8,4) X(8,16,4) X(8,24,6)
+#define GFDTD_SHAPES(X) X(4,8,4) X(8,8,4) X(8,16,4) X(8,24,6)
 
 int block_launch_f64(int variant, int C, int TB, int MB, const void* a, int grid, int block,
                         cudaStream_t st) {

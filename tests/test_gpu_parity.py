@@ -206,6 +206,20 @@ def test_linear_profiles_f64(kind):
     _compare(wl, sim, orcs, 1e-11)
 
 
+@pytest.mark.parametrize("kind", [w.PERTURBATION, w.MATTER])
+def test_f64_four_cell_lanes(kind):
+    """The FP64 shape with 4 cells per lane and 8-step time blocks (latency
+    shape for small single instances) on ragged layered instances."""
+    wl = _mixed_workload(seed=17, kind=kind)
+    sim = make_sim(wl, prec=gb.F64, tuning=(4, 8, 4))
+    orcs = make_oracle(wl)
+    _seed_fields(wl, sim, orcs)
+    sim.step(45)
+    for o in orcs:
+        o.run(45)
+    _compare(wl, sim, orcs, 1e-11)
+
+
 @pytest.mark.parametrize("prec,tol", [(gb.F64, 1e-11), (gb.F32_KAHAN, TOL32), (gb.BF16, 3e-2),
                                       (gb.F16, 5e-3)])
 def test_precision_tiers(prec, tol):
