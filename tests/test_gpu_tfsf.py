@@ -93,6 +93,21 @@ def test_tfsf_matches_oracle(kind, tuning):
     _compare(wl, sim, orcs, TOL32)
 
 
+def test_tfsf_with_absorbing_layers():
+    """One-way sources and graded absorbing layers together (the layers damp
+    after each update, the corrections are added after the damping, on both
+    sides)."""
+    wl, tf = _workload()
+    sim, orcs = _pair(wl, tf)
+    for k, I in enumerate(wl.instances):
+        sim.set_absorber(k, 48, 0.2)
+        orcs[k].set_absorber(48, 0.2)
+    sim.step(2400)
+    import oracle
+    oracle.run_many(orcs, 2400)
+    _compare(wl, sim, orcs, TOL32)
+
+
 def test_tfsf_fp64_tier():
     wl, tf = _workload()
     sim, orcs = _pair(wl, tf, prec=gb.F64)
