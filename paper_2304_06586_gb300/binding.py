@@ -380,3 +380,55 @@ class Simulation:
 
     def synchronize(self):
         self._check(self._L.gfdtd_synchronize(self._h), "synchronize")
+
+
+# ------------------------------------------------------------- autograd
+
+def _autograd():
+    import torch
+
+    class ProbePower(torch.autograd.Function):
+        """Per-instance probe power L_i = sum_{f = bin_lo}^{bin_hi - 1} |X_f|^2 over
+        n_steps from rest, as a differentiable function of every instance's
+        permittivity profile values (concatenated in instance order).  The forward
+        runs gfdtd_adjoint on a fresh context built by make_sim(eps_per_instance),
+        which returns dL_i / d eps with the loss; backward scales those by the
+        incoming gradient of each L_i."""
+
+        @staticmethod
+        def forward(ctx, eps, make_sim, n_values, n_steps, probe_id, bin_lo, bin_hi):
+            e = eps.detach().to("cpu", torch.float64).numpy()
+            parts = np.split(e, np.cumsum(n_values)[:-1])
+            sim = make_sim(parts)
+            try:
+                loss, grads = sim.adjoint(n_steps, probe_id, bin_lo, bin_hi, list(n_values))
+            finally:
+                sim.close()
+            g = torch.from_numpy(np.concatenate(grads)).to(eps.device, eps.dtype)
+            owner = torch.repeat_interleave(torch.arange(len(n_values)),
+                                            torch.tensor(list(n_values))).to(eps.device)
+            ctx.save_for_backward(g, owner)
+            return torch.from_numpy(loss).to(eps.device, eps.dtype)
+
+        @staticmethod
+        def backward(ctx, grad_loss):
+            g, owner = ctx.saved_tensors
+            return grad_loss[owner] * g, None, None, None, None, None, None
+
+    return ProbePower
+
+
+_probe_power_fn = None
+
+
+def probe_power(eps, make_sim, n_values, n_steps, probe_id=0, bin_lo=0, bin_hi=1):
+    """Differentiable per-instance probe power (see ProbePower above): `eps` is a
+    1-D tensor holding the profile values of all instances (n_values[i] for
+    instance i), `make_sim(list_of_eps_arrays)` returns a configured Simulation
+    (media, sources, probes) at rest.  Returns a tensor of n_inst losses whose
+    backward gives d loss / d eps from the GPU adjoint."""
+    global _probe_power_fn
+    if _probe_power_fn is None:
+        _probe_power_fn = _autograd()
+    return _probe_power_fn.apply(eps, make_sim, tuple(int(n) for n in n_values), int(n_steps),
+                                 int(probe_id), int(bin_lo), int(bin_hi))

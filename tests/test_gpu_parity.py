@@ -376,6 +376,44 @@ def test_adjoint_matches_finite_differences():
         assert abs(g[j] - fd) <= 1e-3 * np.abs(g).max(), (j, g[j], fd)
 
 
+def test_adjoint_through_torch_autograd():
+    """binding.probe_power as a torch.autograd.Function: the losses equal the
+    adjoint's, eps.grad of a weighted sum equals the weighted adjoint
+    gradients, and a central difference of the Function's own forward
+    (h = 1e-3) matches eps.grad on a control point."""
+    torch = pytest.importorskip("torch")
+    wl = _adjoint_workload()
+    nv = [len(I.eps) for I in wl.instances]
+
+    def make(parts):
+        sim = gb.Simulation([I.nz for I in wl.instances], wl.S, gb.F32)
+        for k, (I, e) in enumerate(zip(wl.instances, parts)):
+            sim.set_medium(k, I.kind, I.beta, I.interp, I.z, e, I.mu, False)
+            for s in I.sources:
+                sim.add_source(k, *s)
+            for p in I.probes:
+                sim.add_probe(k, p[0], p[1])
+        return sim
+
+    eps = torch.tensor(np.concatenate([I.eps for I in wl.instances]), dtype=torch.float64, requires_grad=True)
+    loss = gb.probe_power(eps, make, nv, wl.n_steps, 0, 0, 16)
+    ref_loss, ref_grads = make([I.eps for I in wl.instances]).adjoint(wl.n_steps, 0, 0, 16, nv)
+    assert np.allclose(loss.detach().numpy(), ref_loss, rtol=1e-6, atol=0)
+    wts = torch.tensor([1.0, -0.5, 2.0], dtype=torch.float64)
+    (loss * wts).sum().backward()
+    want = np.concatenate([wk * g for wk, g in zip(wts.numpy(), ref_grads)])
+    assert np.allclose(eps.grad.numpy(), want, rtol=1e-6, atol=1e-12 * np.abs(want).max())
+    j, h = nv[0] + 20, 1e-3                  # a control point of instance 1 (FP32 loss: a wide step)
+    with torch.no_grad():
+        ep, em = eps.detach().clone(), eps.detach().clone()
+        ep[j] += h
+        em[j] -= h
+        fd = float(((gb.probe_power(ep, make, nv, wl.n_steps, 0, 0, 16)
+                     - gb.probe_power(em, make, nv, wl.n_steps, 0, 0, 16)) * wts).sum()) / (2 * h)
+    g = eps.grad.numpy()
+    assert abs(g[j] - fd) <= 2e-3 * np.abs(g[nv[0]:nv[0] + nv[1]]).max(), (g[j], fd)
+
+
 def test_profile_kernels_matches_step_and_covers_every_cell():
     """The measurement entry point runs the same launches as step(): identical
     fields and spectra, and its per-kernel cell-updates add up to every cell
