@@ -58,3 +58,31 @@ def test_moving_interface_coefficients_on_gpu(prec):
         T = ex["a_t"] * Xt[j] / Xi[j] / (li * lt)
         assert abs(G / abs(ex["Gamma"]) - 1) < 0.01, (f, G, ex["Gamma"])
         assert abs(T / abs(ex["T"]) - 1) < 0.01, (f, T, ex["T"])
+
+
+@pytest.mark.parametrize("beta", [0.2, -0.2])
+def test_moving_slab_transmission_on_gpu(beta):
+    """|T| of a moving slab (eps 1 | 4 | 1, 450 cells, Eq. coef_slab) at 300
+    cells per vacuum wavelength: the transmitted spectrum over that of the
+    same background without the slab, within 1 % over 0.9-1.1 w0 (the
+    Fabry-Perot phase inside the slab makes |T| sensitive to the scheme's
+    phase error, which falls with the square of the resolution)."""
+    from oracle import exact
+    e1, e2, S, lam0 = 1.0, 4.0, 0.5, 300.0
+    w0 = 2 * np.pi / lam0
+    tau = 6 * lam0 / (2 * np.sqrt(np.log(2)))
+    t0 = 4 * tau
+    q, z0, ell, zt, nz, steps = 2400, 7000.0, 450.0, 17200, 20000, 80000
+    fs = np.array([0.9, 0.95, 1.0, 1.05, 1.1])
+    sim = gb.Simulation([nz, nz], S, gb.F32_KAHAN)
+    sim.set_medium(0, gb.PERTURBATION, beta, gb.LAYERS, [z0, z0 + ell], [e1, e2, e1], [1.0] * 3)
+    sim.set_medium(1, gb.PERTURBATION, beta, gb.LAYERS, [], [e1], [1.0])
+    for k in (0, 1):
+        sim.add_tfsf(k, q, w0, tau, t0)
+        sim.set_absorber(k, 64, 0.2)
+        sim.add_probe(k, zt, fs * w0)
+    sim.step(steps)
+    T = np.abs(sim.read_spectrum(0, 0, len(fs))) / np.abs(sim.read_spectrum(1, 0, len(fs)))
+    for j, f in enumerate(fs):
+        Tex, _ = exact.slab_closed_form(e1, e2, beta, ell, f * w0)
+        assert abs(T[j] / abs(Tex) - 1) < 0.01, (beta, f, T[j], abs(Tex))
