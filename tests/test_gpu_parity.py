@@ -262,6 +262,28 @@ def test_gradient_ramp_reduced(prec, tol):
     _compare(wl, sim, orcs, tol)
 
 
+def test_gradient_ramp_error_per_tier():
+    """The error of every precision tier against the FP64 oracle on the reduced
+    moving-gradient run (fields and the probe spectrum, relative L2), printed
+    per tier; bounds: FP64 1e-11, Kahan 1e-5, FP32 5e-4, FP16 5e-3, BF16 5e-2
+    (measured on GB300: 6e-15, 1.7e-6, 1.8e-4, 1.3e-3, 1.2e-2)."""
+    wl = w.config4("stable", nz=1 << 12, n_steps=8000)
+    orcs = make_oracle(wl)
+    for o in orcs:
+        o.run(wl.n_steps)
+    bounds = {gb.F64: 1e-11, gb.F32_KAHAN: 1e-5, gb.F32: 5e-4, gb.F16: 5e-3, gb.BF16: 5e-2}
+    names = {gb.F64: "F64", gb.F32_KAHAN: "F32_KAHAN", gb.F32: "F32", gb.F16: "F16", gb.BF16: "BF16"}
+    for prec, bound in bounds.items():
+        sim = make_sim(wl, prec=prec)
+        sim.step(wl.n_steps)
+        eD = rel_l2(sim.read_fields(0, gb.FIELD_D), orcs[0].D)
+        eB = rel_l2(sim.read_fields(0, gb.FIELD_B), orcs[0].B)
+        eX = rel_l2(sim.read_spectrum(0, 0, len(wl.instances[0].probes[0][1])), orcs[0].spectrum(0))
+        print("tier %-9s D %.2e  B %.2e  spectrum %.2e" % (names[prec], eD, eB, eX))
+        assert max(eD, eB, eX) <= bound, (names[prec], eD, eB, eX)
+        sim.close()
+
+
 def test_matter_slab_reduced():
     wl = w.config2(velocities=(-0.5, 0.0, 0.5), nz=1 << 13, n_steps=2500)
     sim = make_sim(wl)
