@@ -118,7 +118,8 @@ struct gfdtd_ctx {
   int num_sms = 0;
 
   // adjoint work buffers (allocated on first use)
-  DevBuf d_ckB, d_ckD, d_dseg, d_wB[2], d_lB[2], d_lD[2], d_grad, d_gn, d_adjn, d_Xre, d_Xim,
+  // (two sets of the recomputation buffers: dseg, wB, adjn, amp2, one per segment in flight)
+  DevBuf d_ckB, d_ckD, d_dseg[2], d_wB[2][2], d_amp2[2], d_lB[2], d_lD[2], d_grad, d_gn, d_adjn[2], d_Xre, d_Xim,
       d_bin0, d_pnode, d_acc0_re, d_acc0_im, d_adj_tiles;
   int n_adj_tiles = 0;
 
@@ -790,7 +791,8 @@ static gfdtd_status check_inst(gfdtd_ctx* c, int inst) {
 constexpr int kGradCopies = 64;   // copies of the adjoint's gradient that its blocks spread atomics over
 
 static gfdtd_status enqueue_segment_block(gfdtd_ctx* c, const void* Bin, void* Bout, char* dseg, size_t fb,
-                                          const long long* n_done, int s0, int nsteps) {
+                                          const long long* n_done, int s0, int nsteps, const double* amp,
+                                          cudaStream_t st) {
   for (int k : {0, 2}) {
     if (c->n_tiles[k] == 0) continue;
     BlockArgs<float> a{};
@@ -799,7 +801,7 @@ static gfdtd_status enqueue_segment_block(gfdtd_ctx* c, const void* Bin, void* B
     a.n_tiles = c->n_tiles[k];
     a.tb = tables_of(c);
     a.srcs = (const SrcDev*)c->d_srcs.p;
-    a.src_amp = c->n_src > 0 ? (const double*)c->d_amp.p : nullptr;
+    a.src_amp = c->n_src > 0 ? amp : nullptr;
     a.prbs = (const PrbDev*)c->d_prbs.p;
     a.samples = (double*)c->d_samples.p;
     a.chunk_stride = kChunk;
@@ -815,7 +817,7 @@ static gfdtd_status enqueue_segment_block(gfdtd_ctx* c, const void* Bin, void* B
     a.dseg = (float*)dseg;
     a.dseg_stride = (long long)(fb / sizeof(float));
     const int grid = std::min(c->grid[0] > 0 ? c->grid[0] : c->num_sms, (a.n_tiles + 3) / 4);
-    CKI(c, block_launch(GFDTD_F32, 0, c->C, c->TB, c->MB, &a, std::max(grid, 1), kBlock, c->stream));
+    CKI(c, block_launch(GFDTD_F32, 0, c->C, c->TB, c->MB, &a, std::max(grid, 1), kBlock, st));
     ++c->launches;
   }
   return GFDTD_OK;
@@ -851,18 +853,25 @@ extern "C" gfdtd_status gfdtd_adjoint(gfdtd_ctx* c, int64_t n_steps, int probe_i
   const size_t lb = (size_t)c->total * sizeof(float);
   const int ntab = (int)(c->d_tabE.bytes / sizeof(double2));
   if ((s = dalloc(c, c->d_ckB, fb * nseg)) || (s = dalloc(c, c->d_ckD, fb * nseg)) ||
-      (s = dalloc(c, c->d_dseg, fb * (K + 1))) || (s = dalloc(c, c->d_wB[0], fb)) ||
-      (s = dalloc(c, c->d_wB[1], fb)) || (s = dalloc(c, c->d_lB[0], lb)) ||
+      (s = dalloc(c, c->d_dseg[0], fb * (K + 1))) || (s = dalloc(c, c->d_dseg[1], fb * (K + 1))) ||
+      (s = dalloc(c, c->d_wB[0][0], fb)) || (s = dalloc(c, c->d_wB[0][1], fb)) ||
+      (s = dalloc(c, c->d_wB[1][0], fb)) || (s = dalloc(c, c->d_wB[1][1], fb)) ||
+      (s = dalloc(c, c->d_amp2[0], std::max<size_t>(16, (size_t)c->n_src * kChunk * sizeof(double)))) ||
+      (s = dalloc(c, c->d_amp2[1], std::max<size_t>(16, (size_t)c->n_src * kChunk * sizeof(double)))) ||
+      (s = dalloc(c, c->d_lB[0], lb)) ||
       (s = dalloc(c, c->d_lB[1], lb)) || (s = dalloc(c, c->d_lD[0], lb)) ||
       (s = dalloc(c, c->d_lD[1], lb)) || (s = dalloc(c, c->d_grad, sizeof(double) * ntab * (kGradCopies + 1))) ||
-      (s = dalloc(c, c->d_gn, sizeof(double) * K * c->n_inst)) || (s = dalloc(c, c->d_adjn, 16)) ||
+      (s = dalloc(c, c->d_gn, sizeof(double) * K * c->n_inst)) || (s = dalloc(c, c->d_adjn[0], 16)) ||
+      (s = dalloc(c, c->d_adjn[1], 16)) ||
       (s = dalloc(c, c->d_acc0_re, sizeof(double) * std::max(1, c->n_bins))) ||
       (s = dalloc(c, c->d_acc0_im, sizeof(double) * std::max(1, c->n_bins))))
     return s;
   // padding cells past nz are never written by the step kernels: keep them zero
-  CK(c, cudaMemsetAsync(c->d_dseg.p, 0, fb * (K + 1), st));
-  CK(c, cudaMemsetAsync(c->d_wB[0].p, 0, fb, st));
-  CK(c, cudaMemsetAsync(c->d_wB[1].p, 0, fb, st));
+  for (int b = 0; b < 2; ++b) {
+    CK(c, cudaMemsetAsync(c->d_dseg[b].p, 0, fb * (K + 1), st));
+    CK(c, cudaMemsetAsync(c->d_wB[b][0].p, 0, fb, st));
+    CK(c, cudaMemsetAsync(c->d_wB[b][1].p, 0, fb, st));
+  }
   if (c->n_adj_tiles == 0) {
     std::vector<int2> t;
     for (int i = 0; i < c->n_inst; ++i)
@@ -910,27 +919,62 @@ extern "C" gfdtd_status gfdtd_adjoint(gfdtd_ctx* c, int64_t n_steps, int probe_i
   if ((s = upload(c, c->d_Xre, Xre)) || (s = upload(c, c->d_Xim, Xim)) || (s = upload(c, c->d_bin0, bin0)) ||
       (s = upload(c, c->d_pnode, pnode)))
     return s;
-  // ---- reverse sweep, segment by segment
+  // ---- reverse sweep, segment by segment.  The forward recomputation of a
+  // segment (general kernel, D after every step) runs on a second stream in
+  // one of two buffer sets, one segment ahead of the reverse sweep, which
+  // waits for it by an event; a set is refilled only after the reverse sweep
+  // that read it has finished.
   CK(c, cudaMemsetAsync(c->d_lB[0].p, 0, lb, st));
   CK(c, cudaMemsetAsync(c->d_lD[0].p, 0, lb, st));
   CK(c, cudaMemsetAsync(c->d_grad.p, 0, sizeof(double) * ntab * (kGradCopies + 1), st));
-  int lc = 0;
-  long long host_n = 0;
-  for (long long sg = nseg - 1; sg >= 0; --sg) {
-    const long long ns = n0 + sg * K;                 // steps done at the segment start
-    const int Ks = (int)std::min(K, N - sg * K);
-    host_n = ns;
-    CK(c, cudaMemcpyAsync(c->d_adjn.p, &host_n, sizeof(long long), cudaMemcpyHostToDevice, st));
-    CK(c, cudaMemcpyAsync(c->d_wB[0].p, (char*)c->d_ckB.p + sg * fb, fb, cudaMemcpyDeviceToDevice, st));
-    CK(c, cudaMemcpyAsync(c->d_dseg.p, (char*)c->d_ckD.p + sg * fb, fb, cudaMemcpyDeviceToDevice, st));
-    if (c->n_src > 0)
-      CKI(c, src_amp_launch((const SrcDev*)c->d_srcs.p, c->n_src, (double*)c->d_amp.p, kChunk, Ks,
-                            (const long long*)c->d_adjn.p, c->S, st));
-    for (int m0 = 0, w = 0; m0 < Ks; m0 += c->TB, w ^= 1) {
-      if ((s = enqueue_segment_block(c, c->d_wB[w].p, c->d_wB[w ^ 1].p, (char*)c->d_dseg.p, fb,
-                                     (const long long*)c->d_adjn.p, m0, std::min(c->TB, Ks - m0))))
-        return s;
+  std::vector<long long> seg_n((size_t)nseg);          // steps done at each segment start
+  for (long long sg = 0; sg < nseg; ++sg) seg_n[(size_t)sg] = n0 + sg * K;
+  cudaStream_t st2 = nullptr;
+  cudaEvent_t ev_start = nullptr, ev_rc[2] = {nullptr, nullptr}, ev_rv[2] = {nullptr, nullptr};
+  struct Release {
+    cudaStream_t& s2;
+    cudaEvent_t& e0;
+    cudaEvent_t* a;
+    cudaEvent_t* b;
+    ~Release() {
+      if (s2) { cudaStreamSynchronize(s2); cudaStreamDestroy(s2); }
+      for (cudaEvent_t e : {e0, a[0], a[1], b[0], b[1]}) if (e) cudaEventDestroy(e);
     }
+  } release{st2, ev_start, ev_rc, ev_rv};
+  CK(c, cudaStreamCreateWithFlags(&st2, cudaStreamNonBlocking));
+  CK(c, cudaEventCreateWithFlags(&ev_start, cudaEventDisableTiming));
+  for (int b = 0; b < 2; ++b) {
+    CK(c, cudaEventCreateWithFlags(&ev_rc[b], cudaEventDisableTiming));
+    CK(c, cudaEventCreateWithFlags(&ev_rv[b], cudaEventDisableTiming));
+  }
+  CK(c, cudaEventRecord(ev_start, st));               // checkpoints and buffer clears are done
+  CK(c, cudaStreamWaitEvent(st2, ev_start, 0));
+  auto recompute = [&](long long sg) -> gfdtd_status {
+    const int bs = (int)(sg & 1);
+    const int Ks = (int)std::min(K, N - sg * K);
+    CK(c, cudaMemcpyAsync(c->d_adjn[bs].p, &seg_n[(size_t)sg], sizeof(long long), cudaMemcpyHostToDevice, st2));
+    CK(c, cudaMemcpyAsync(c->d_wB[bs][0].p, (char*)c->d_ckB.p + sg * fb, fb, cudaMemcpyDeviceToDevice, st2));
+    CK(c, cudaMemcpyAsync(c->d_dseg[bs].p, (char*)c->d_ckD.p + sg * fb, fb, cudaMemcpyDeviceToDevice, st2));
+    if (c->n_src > 0) {
+      CKI(c, src_amp_launch((const SrcDev*)c->d_srcs.p, c->n_src, (double*)c->d_amp2[bs].p, kChunk, Ks,
+                            (const long long*)c->d_adjn[bs].p, c->S, st2));
+      ++c->launches;
+    }
+    for (int m0 = 0, w = 0; m0 < Ks; m0 += c->TB, w ^= 1) {
+      gfdtd_status r = enqueue_segment_block(c, c->d_wB[bs][w].p, c->d_wB[bs][w ^ 1].p, (char*)c->d_dseg[bs].p,
+                                             fb, (const long long*)c->d_adjn[bs].p, m0, std::min(c->TB, Ks - m0),
+                                             (const double*)c->d_amp2[bs].p, st2);
+      if (r) return r;
+    }
+    CK(c, cudaEventRecord(ev_rc[bs], st2));
+    return GFDTD_OK;
+  };
+  int lc = 0;
+  auto reverse = [&](long long sg) -> gfdtd_status {
+    const int bs = (int)(sg & 1);
+    const long long ns = seg_n[(size_t)sg];
+    const int Ks = (int)std::min(K, N - sg * K);
+    CK(c, cudaStreamWaitEvent(st, ev_rc[bs], 0));
     SourceAdjArgs sa;
     sa.n_inst = c->n_inst;
     sa.bin0 = (const int*)c->d_bin0.p;
@@ -952,7 +996,7 @@ extern "C" gfdtd_status gfdtd_adjoint(gfdtd_ctx* c, int64_t n_steps, int probe_i
       pa.probe_node = (const int*)c->d_pnode.p;
       pa.gn = (const double*)c->d_gn.p + (long long)(m - 1) * c->n_inst;
       pa.lD = (float*)c->d_lD[lc].p;
-      pa.Dnew = (const float*)((char*)c->d_dseg.p + m * fb);
+      pa.Dnew = (const float*)((char*)c->d_dseg[bs].p + m * fb);
       pa.n = n;
       pa.grad = (double*)c->d_grad.p;
       CKI(c, probe_adjoint_launch(pa, st));
@@ -965,7 +1009,7 @@ extern "C" gfdtd_status gfdtd_adjoint(gfdtd_ctx* c, int64_t n_steps, int probe_i
       aa.lDn = (const float*)c->d_lD[lc].p;
       aa.lB = (float*)c->d_lB[1 - lc].p;
       aa.lD = (float*)c->d_lD[1 - lc].p;
-      aa.Dold = (const float*)((char*)c->d_dseg.p + (m - 1) * fb);
+      aa.Dold = (const float*)((char*)c->d_dseg[bs].p + (m - 1) * fb);
       aa.n = n;
       aa.grad = (double*)c->d_grad.p;       // copies 0 .. kGradCopies-1; the sum goes after them
       aa.grad_copies = kGradCopies;
@@ -974,7 +1018,17 @@ extern "C" gfdtd_status gfdtd_adjoint(gfdtd_ctx* c, int64_t n_steps, int probe_i
       c->launches += 2;
       lc = 1 - lc;
     }
-    CK(c, cudaStreamSynchronize(st));   // host_n is reused by the next segment's copy
+    CK(c, cudaEventRecord(ev_rv[bs], st));
+    return GFDTD_OK;
+  };
+  if ((s = recompute(nseg - 1))) return s;
+  if (nseg >= 2 && (s = recompute(nseg - 2))) return s;
+  for (long long sg = nseg - 1; sg >= 0; --sg) {
+    if ((s = reverse(sg))) return s;
+    if (sg >= 2) {
+      CK(c, cudaStreamWaitEvent(st2, ev_rv[sg & 1], 0));
+      if ((s = recompute(sg - 2))) return s;
+    }
   }
   std::vector<double> g(ntab);
   double* gsum = (double*)c->d_grad.p + (size_t)kGradCopies * ntab;
@@ -1549,8 +1603,9 @@ void gfdtd_destroy(gfdtd_ctx* c) {
                     &c->d_tabE, &c->d_tabH, &c->d_srcs, &c->d_prbs, &c->d_amp, &c->d_samples,
                     &c->d_omega, &c->d_binprb, &c->d_acc_re, &c->d_acc_im, &c->d_tiles[0],
                     &c->d_tiles[1], &c->d_tiles[2], &c->d_tmp, &c->d_tabE32, &c->d_tabH32, &c->d_ftiles, &c->d_track, &c->cap.buf,
-                    &c->d_ckB, &c->d_ckD, &c->d_dseg, &c->d_wB[0], &c->d_wB[1], &c->d_lB[0],
-                    &c->d_lB[1], &c->d_lD[0], &c->d_lD[1], &c->d_grad, &c->d_gn, &c->d_adjn,
+                    &c->d_ckB, &c->d_ckD, &c->d_dseg[0], &c->d_dseg[1], &c->d_wB[0][0], &c->d_wB[0][1],
+                    &c->d_wB[1][0], &c->d_wB[1][1], &c->d_amp2[0], &c->d_amp2[1], &c->d_lB[0],
+                    &c->d_lB[1], &c->d_lD[0], &c->d_lD[1], &c->d_grad, &c->d_gn, &c->d_adjn[0], &c->d_adjn[1],
                     &c->d_Xre, &c->d_Xim, &c->d_bin0, &c->d_pnode, &c->d_acc0_re, &c->d_acc0_im,
                     &c->d_adj_tiles, &c->d_tfsf, &c->d_tfaux, &c->d_tfcorr};
   for (DevBuf* b : bufs) dfree(c, *b);
