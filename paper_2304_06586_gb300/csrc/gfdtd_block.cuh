@@ -386,13 +386,32 @@ __device__ __forceinline__ void run_tile(const BlockArgs<T>& A, const InstDev& I
 
   const R a = (R)I.a, cc = (R)I.c;
   const bool damp = window_absorbs(I, base, 32 * C);   // the tile reaches an absorbing layer
-  const bool eps_const = (I.flags & F_EPS_CONST) != 0;
-  const bool mu_const = (I.flags & F_MU_CONST) != 0;
+  bool eps_const = (I.flags & F_EPS_CONST) != 0;
+  bool mu_const = (I.flags & F_MU_CONST) != 0;
   const long long dq = I.dq;
-  const auto e0 = __ldg(TabOf<R>::get(A.tb, true) + I.tab);
-  const auto h0 = __ldg(TabOf<R>::get(A.tb, false) + I.tab);
-  // (uniform values: LINEAR tables hold raw (eps, mu), LAYERS tables the coefficients)
   const bool lin = (I.flags & F_LINEAR) != 0;
+  // A moving-perturbation tile whose window lies, over the whole launch, before
+  // the first profile position or after the last one sees a single material
+  // value on that side (positions move monotonically, so the launch's first
+  // and last half levels decide): it takes the uniform path with that value.
+  int rE = 0, rH = 0;                                  // table entries of the uniform values
+  const int np = lin ? I.n : I.n - 1;                  // profile positions
+  if (!MATTER && np > 0 && (!eps_const || !mu_const)) {
+    const long long* __restrict__ zq = A.tb.zq + I.tab;
+    const long long zf = __ldg(zq), zl = __ldg(zq + np - 1);
+    const int last = base + 32 * C - 1;
+    auto one_side = [&](long long off_a, long long off_b, int& r) {
+      if (last < node_of(zf, off_a) && last < node_of(zf, off_b)) { r = 0; return true; }
+      if (base >= node_of(zl, off_a) && base >= node_of(zl, off_b)) { r = lin ? np - 1 : np; return true; }
+      return false;
+    };
+    const long long n1 = n0 + 1, n2 = n0 + A.nsteps;
+    if (!eps_const && one_side(dq * (2 * n1 - 1), dq * (2 * n2 - 1), rE)) eps_const = true;
+    if (!mu_const && one_side(dq * (2 * n1) - HALF_CELL, dq * (2 * n2) - HALF_CELL, rH)) mu_const = true;
+  }
+  const auto e0 = __ldg(TabOf<R>::get(A.tb, true) + I.tab + rE);
+  const auto h0 = __ldg(TabOf<R>::get(A.tb, false) + I.tab + rH);
+  // (uniform values: LINEAR tables hold raw (eps, mu), LAYERS tables the coefficients)
   const R se0 = lin ? (R)I.S / e0.x : e0.x, sm0 = lin ? (R)I.S / h0.y : h0.x;
   const R cbe0 = MATTER ? e0.y : (R)I.cb, cbh0 = MATTER ? h0.y : (R)I.cb;
   int liE = 0, liH = 0;
