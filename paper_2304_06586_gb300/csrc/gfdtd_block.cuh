@@ -390,13 +390,15 @@ __device__ __forceinline__ void run_tile(const BlockArgs<T>& A, const InstDev& I
   bool mu_const = (I.flags & F_MU_CONST) != 0;
   const long long dq = I.dq;
   const bool lin = (I.flags & F_LINEAR) != 0;
-  // A moving-perturbation tile whose window lies, over the whole launch, before
-  // the first profile position or after the last one sees a single material
-  // value on that side (positions move monotonically, so the launch's first
-  // and last half levels decide): it takes the uniform path with that value.
+  // A tile whose window lies, over the whole launch, before the first profile
+  // position or after the last one sees a single material value on that side
+  // (positions move monotonically, so the launch's first and last half levels
+  // decide): it takes the uniform path with that value.  (Layers tables hold
+  // the coefficients themselves; a linear moving-matter profile would need
+  // them formed from (eps, mu), so it keeps the general path.)
   int rE = 0, rH = 0;                                  // table entries of the uniform values
   const int np = lin ? I.n : I.n - 1;                  // profile positions
-  if (!MATTER && np > 0 && (!eps_const || !mu_const)) {
+  if ((!MATTER || !lin) && np > 0 && (!eps_const || !mu_const)) {
     const long long* __restrict__ zq = A.tb.zq + I.tab;
     const long long zf = __ldg(zq), zl = __ldg(zq + np - 1);
     const int last = base + 32 * C - 1;
