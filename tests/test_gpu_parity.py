@@ -415,6 +415,7 @@ def test_adjoint_through_torch_autograd():
                 sim.add_source(k, *s)
             for p in I.probes:
                 sim.add_probe(k, p[0], p[1])
+        sim.set_tuning(8, 16, 4)             # the same tiling in every run
         return sim
 
     eps = torch.tensor(np.concatenate([I.eps for I in wl.instances]), dtype=torch.float64, requires_grad=True)
@@ -424,7 +425,8 @@ def test_adjoint_through_torch_autograd():
     wts = torch.tensor([1.0, -0.5, 2.0], dtype=torch.float64)
     (loss * wts).sum().backward()
     want = np.concatenate([wk * g for wk, g in zip(wts.numpy(), ref_grads)])
-    assert np.allclose(eps.grad.numpy(), want, rtol=1e-6, atol=1e-12 * np.abs(want).max())
+    # (separate runs: FP64 atomics add the gradient in a different order)
+    assert rel_l2(eps.grad.numpy(), want) <= 1e-6, rel_l2(eps.grad.numpy(), want)
     j, h = nv[0] + 20, 1e-3                  # a control point of instance 1 (FP32 loss: a wide step)
     with torch.no_grad():
         ep, em = eps.detach().clone(), eps.detach().clone()
