@@ -86,7 +86,7 @@ constexpr int kAdjKeys = 1024;                       // profile values one block
 // shared memory, and added to the FP64 gradient with one atomic per profile
 // value per block.  FP64 arithmetic is kept out of the per-cell work: GB300's
 // FP64 pipe is narrow.
-__global__ void __launch_bounds__(kAdjThreads) adjoint_step_kernel(const AdjArgs A) {
+__global__ void __launch_bounds__(kAdjThreads, 4) adjoint_step_kernel(const AdjArgs A) {
   // cells x0 - 2 .. x0 + kAdjTileCells + 5, zero outside [0, nz)
   __shared__ __align__(16) float s_lb[kAdjTileCells + 8];
   __shared__ __align__(16) float s_ld[kAdjTileCells + 8];
@@ -112,6 +112,19 @@ __global__ void __launch_bounds__(kAdjThreads) adjoint_step_kernel(const AdjArgs
   const long long n = A.n;
   const long long offH = I.dq * (2 * n) - HALF_CELL, offE = I.dq * (2 * n - 1);
   const bool mu_const = (I.flags & F_MU_CONST) != 0;
+  // global loads that need no staged value are issued before the barrier, so
+  // that their latency overlaps the staging: the first cell's position count
+  // and D^{n-1/2} of the thread's cells
+  const long long* __restrict__ zq = A.tb.zq + I.tab;
+  const int np = lin ? I.n : I.n - 1;          // profile positions
+  long long xi = ((long long)k0 << 32) - offE;
+  int idx = 0;
+  float Dold[kAdjCPT] = {0.0f, 0.0f, 0.0f, 0.0f};
+  if (nvalid > 0) {
+    idx = positions_at_or_left(zq, np, xi);
+    const float4 d = *reinterpret_cast<const float4*>(A.Dold + I.off + k0);   // padded to 32 cells
+    Dold[0] = d.x; Dold[1] = d.y; Dold[2] = d.z; Dold[3] = d.w;
+  }
   __syncthreads();
 
   int key0[kAdjCPT], key1[kAdjCPT];
@@ -143,16 +156,7 @@ __global__ void __launch_bounds__(kAdjThreads) adjoint_step_kernel(const AdjArgs
       t[q] = in ? LB[q] + sm * lH[q] : 0.0f;
     }
     // material at level n-1/2 of the four cells
-    const long long* __restrict__ zq = A.tb.zq + I.tab;
     const float2* __restrict__ tv = A.tb.tabE32 + I.tab;
-    const int np = lin ? I.n : I.n - 1;        // profile positions
-    long long xi = ((long long)k0 << 32) - offE;
-    int idx = positions_at_or_left(zq, np, xi);
-    float Dold[kAdjCPT];
-    {
-      const float4 d = *reinterpret_cast<const float4*>(A.Dold + I.off + k0);   // padded to 32 cells
-      Dold[0] = d.x; Dold[1] = d.y; Dold[2] = d.z; Dold[3] = d.w;
-    }
     float oD[kAdjCPT], oB[kAdjCPT];
 #pragma unroll
     for (int q = 0; q < kAdjCPT; ++q) {
