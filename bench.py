@@ -286,14 +286,19 @@ def run_case(args):
 E2E_PARTS = 4
 
 
+def e2e_groups(cells, parts):
+    """Contiguous groups of instance indices of about equal total cells."""
+    cells = np.asarray(cells, dtype=np.int64)
+    bounds = np.searchsorted(np.cumsum(cells), np.linspace(0, cells.sum(), parts + 1)[1:-1])
+    return [g for g in np.split(np.arange(len(cells)), bounds) if len(g)]
+
+
 def e2e_pipelined(gb, torch, wl, T, steps, tile, barrier, pg, world, cu):
     """End-to-end throughput through the public API: every bench step writes
     each part's state (B, D) from pinned host buffers, advances it T steps and
     reads it back; parts sit on their own streams, so copies and kernels of
     different parts overlap (host<->device copies counted in full)."""
-    cells = np.array([i.nz for i in wl.instances], dtype=np.int64)
-    bounds = np.searchsorted(np.cumsum(cells), np.linspace(0, cells.sum(), E2E_PARTS + 1)[1:-1])
-    groups = [g for g in np.split(np.arange(len(cells)), bounds) if len(g)]
+    groups = e2e_groups([i.nz for i in wl.instances], E2E_PARTS)
     parts = []
     for g in groups:
         strm = torch.cuda.Stream()
