@@ -248,11 +248,15 @@ gfdtd_status gfdtd_adjoint(gfdtd_ctx* ctx, int64_t n_steps, int probe_id, int bi
 gfdtd_status gfdtd_stability(double S, double beta, double eps_r, double mu_r,
                              gfdtd_kind kind, double* max_abs_zeta);
 
-/* Tile shape of the batched kernel: cells per lane (8 to 24), steps per time
+/* Tile shape of the batched kernel: cells per lane (4 to 24), steps per time
  * block (8 to 32) and the number of 128-thread blocks per SM the fast
  * kernel's registers are limited to (4 to 8; 0 = first built match).  The
- * shapes built depend on the precision; E_UNSUPPORTED if the shape is not
- * built.  0, 0, 0 selects autotuning at the next step. */
+ * shapes built depend on the precision (FP32: 8x16x4, 16x16x4, 16x24x8,
+ * 20x16x7, 20x24x7, 20x32x7, 24x24x6; FP64 adds 4x8x4); E_UNSUPPORTED if the
+ * shape is not built.  0, 0, 0 selects autotuning at the next step: every
+ * built shape is timed on the batch (two interleaved passes of one warm-up
+ * and three timed time blocks that follow one another in time) and the
+ * fastest kept. */
 gfdtd_status gfdtd_set_tuning(gfdtd_ctx* ctx, int cells_per_lane, int time_block, int blocks_per_sm);
 
 typedef struct {
