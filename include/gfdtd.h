@@ -252,8 +252,9 @@ gfdtd_status gfdtd_stability(double S, double beta, double eps_r, double mu_r,
  * block (8 to 32) and the number of 128-thread blocks per SM the fast
  * kernel's registers are limited to (4 to 8; 0 = first built match).  The
  * shapes built depend on the precision (FP32: 8x16x4, 16x16x4, 16x24x8,
- * 20x16x7, 20x24x7, 20x32x7, 24x24x6; FP64 adds 4x8x4); E_UNSUPPORTED if the
- * shape is not built.  0, 0, 0 selects autotuning at the next step: every
+ * 20x16x7, 20x24x7, 20x32x7, 24x24x6; FP32 with Kahan terms: 16x16x4, 8x16x4;
+ * BF16 and FP16: 16x16x4, 8x16x4, 16x24x8, 24x24x6; FP64: 4x8x4, 8x8x4,
+ * 8x16x4, 8x24x6); E_UNSUPPORTED if the shape is not built.  0, 0, 0 selects autotuning at the next step: every
  * built shape is timed on the batch (two interleaved passes of one warm-up
  * and three timed time blocks that follow one another in time) and the
  * fastest kept. */
