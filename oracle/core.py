@@ -40,7 +40,7 @@ class _Tfsf(C.Structure):
                 ("t0", C.c_double), ("amp", C.c_double), ("aux_B", _dp), ("aux_D", _dp)]
 
 
-AUX_N = 1088   # cells of a one-way source's auxiliary grid (see the C header)
+AUX_N = 1064   # cells of a one-way source's auxiliary grid (see the C header)
 
 _lib = None
 

@@ -67,11 +67,17 @@
  *   and the scattered-field region (k < q).  The incident wave is the
  *   right-going wave that a soft source with the given waveform emits in an
  *   auxiliary grid of the same scheme filled with the uniform background (the
- *   material at node q at t = 0): AUX_N = 1088 cells, graded absorbing layers
- *   of AUX_W = 524 cells and strength 0.05 at both ends, the soft source at
- *   aux node 532 and the boundary at aux node 544 (aux index = k - q + 544).
- *   (What the auxiliary layers reflect, about 1e-6 of the incident amplitude
- *   for |beta| <= 0.6, reaches the scattered-field region.)
+ *   material at node q at t = 0): graded absorbing layers of AUX_W = 512
+ *   cells and strength 0.05 at both ends of an undamped interior of 40 cells
+ *   (one carrier wavelength of the workloads), AUX_N = 1064 cells in all; the
+ *   soft source 8 cells into the interior (aux node 520) and the boundary 12
+ *   cells right of it (aux node 532; aux index = k - q + 532).  The width is
+ *   set by an accuracy criterion: 512 is the smallest power of two for which
+ *   the layers (strength 0.05 or 0.1) reflect less than 1e-6 of the incident
+ *   amplitude in moving vacuum for |beta| <= 0.6 and less than 3e-6 in every
+ *   stable uniform background with n|beta| <= 0.6, for a 40-cell carrier
+ *   with 3- and 10-period envelopes (256 cells reflect up to 1.5e-6 in
+ *   vacuum).  What the layers reflect reaches the scattered-field region.
  *   Every update that reads a value across the boundary reads it in the
  *   other region's convention: a total-field update adds the incident value
  *   of a scattered-field input, a scattered-field update subtracts the
@@ -127,10 +133,10 @@ typedef struct {
     double* aux_D;
 } orc_tfsf;
 
-#define AUX_N 1088
-#define AUX_W 524
-#define AUX_SRC 532
-#define AUX_Q 544
+#define AUX_N 1064
+#define AUX_W 512
+#define AUX_SRC 520
+#define AUX_Q 532
 
 typedef struct {
     int64_t node;

@@ -10,10 +10,12 @@ subtract.
 import numpy as np
 import pytest
 
-from oracle import Instance, exact
+from oracle import Instance, core, exact
 from oracle import vonneumann as vn
+from paper_2304_06586_gb300 import workloads as w
 
 AUX_OFFSET = 12     # the auxiliary soft source sits 12 cells left of the boundary
+AUX_W, AUX_INTERIOR, AUX_SIGMA = 512, 40, 0.05   # the auxiliary grid's layers and interior
 
 
 def _pulse(lam0=40.0, periods=3.0):
@@ -115,3 +117,39 @@ def test_moving_interface_reflection_without_reference_run():
         lr = vn.propagation_loss(S, beta, e1, 1.0, ex["a_r"] * w, zm - zr, -1)
         G = ex["a_r"] * abs(Xr) / abs(Xi) / (li * lr)
         assert abs(G / abs(ex["Gamma"]) - 1) < 0.01, (f, G, ex["Gamma"])
+
+
+def _aux_reflection(width, beta, kind, eps, fwhm):
+    """Largest difference, at the boundary node, between the auxiliary grid's
+    geometry (layers of `width` cells and strength AUX_SIGMA around a
+    40-cell interior, the soft source 8 cells into it, the boundary 12 cells
+    right of the source) and a domain too long for any echo to return within
+    the run, relative to the pulse's peak there: what the layers reflect."""
+    steps, ref_n = (2400, 4000) if fwhm < 5 else (5000, 8000)
+
+    def series(nz, src, layers):
+        o = Instance(nz, 0.5, beta, kind=kind, eps=[eps])
+        o.add_source(*w.gaussian_source(src, 40.0, fwhm))
+        o.add_probe(src + AUX_OFFSET, np.array([0.1]))
+        o.set_absorber(layers, AUX_SIGMA if layers else 0.0)
+        o.run(steps, record=True)
+        return o.series(0)
+
+    ref = series(ref_n, ref_n // 2, 0)
+    got = series(2 * width + AUX_INTERIOR, width + 8, width)
+    return np.abs(got - ref).max() / np.abs(ref).max()
+
+
+def test_aux_grid_size_is_the_stated_criterion():
+    """The auxiliary grid's size follows from an accuracy criterion, not from
+    any kernel layout: its 512-cell layers are the smallest power-of-two width
+    that reflects below 1e-6 of the incident amplitude in moving vacuum
+    (|beta| <= 0.6) and below 3e-6 in stable media with n|beta| <= 0.6, for
+    the workloads' 40-cell carrier; 256-cell layers miss the vacuum bound."""
+    assert core.AUX_N == 2 * AUX_W + AUX_INTERIOR
+    for beta in (0.0, 0.3, -0.6, 0.6):
+        assert _aux_reflection(AUX_W, beta, 0, 1.0, 3.0) < 1e-6, beta
+    assert _aux_reflection(AUX_W, -0.3, 0, 1.0, 10.0) < 1e-6
+    assert _aux_reflection(AUX_W, -0.3, 0, 3.0, 3.0) < 3e-6     # n|beta| = 0.52
+    assert _aux_reflection(AUX_W, 0.6, 1, 2.0, 3.0) < 3e-6      # moving matter
+    assert _aux_reflection(AUX_W // 2, 0.6, 0, 1.0, 3.0) > 1e-6
