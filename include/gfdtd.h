@@ -162,9 +162,11 @@ gfdtd_status gfdtd_add_source(gfdtd_ctx* ctx, int inst, int64_t node, double ome
  * wave that a soft source with this waveform emits in an auxiliary grid of
  * the same scheme (FP64 for FP64 fields, FP32 otherwise) filled with the
  * uniform background, taken as the
- * material at `node` at t = 0 (1088 cells, graded layers of 524 cells and
- * strength 0.05 at both ends, the auxiliary soft source 12 cells left of the
- * boundary).  Each step, the updates of B at node-2 .. node+1 and of D at
+ * material at `node` at t = 0 (1064 cells: graded layers of 512 cells and
+ * strength 0.05 at both ends of a 40-cell interior, the auxiliary soft source
+ * 12 cells left of the boundary; 512 is the smallest power-of-two width whose
+ * layers reflect below 1e-6 of the incident wave in moving vacuum for
+ * |beta| <= 0.6).  Each step, the updates of B at node-2 .. node+1 and of D at
  * node-1 .. node that read a neighbour across the boundary get that
  * neighbour's incident value added (total-field update) or subtracted
  * (scattered-field update).  The background must stay uniform around the
@@ -356,23 +358,27 @@ gfdtd_status gfdtd_synchronize(gfdtd_ctx* ctx);
  * ctx is NULL).  Valid until the next call on the context. */
 const char* gfdtd_last_error(const gfdtd_ctx* ctx);
 
-/* Allocation-free stepping (the paper has no counterpart: this is a service
- * for callers that cannot allocate device memory -- code being recorded into
- * a CUDA graph, where cudaMalloc cannot be captured; processes whose device
- * memory belongs to another framework's pool; loops that must never block on
- * an allocator).  Advances ONE instance held in caller-owned device buffers
- * B and D (FP32, nz elements each, the state (B^n, D^{n+1/2}) with n =
- * n_done) by n_steps steps, with the medium given as in gfdtd_set_medium, no
- * sources and no probes, using the same kernels and tile shape (16 cells per
- * lane, 16 steps per time block) as gfdtd_step.  Every working buffer lives
- * in one statically allocated device array of about 4.4 MB that each GPU
- * loading this library keeps until the process exits; no call allocates or
- * frees memory.  Limits: 1 <= nz <= 2^18 and n <= 1024 profile values,
- * otherwise E_ARG.  The first call on a device looks up the array's device
- * address (cudaGetSymbolAddress); make that first call outside any stream
- * capture.  All calls share the array: calls whose work overlaps on the GPU
- * (other streams, other threads) race and corrupt each other.  The call
- * returns when the work on `cuda_stream` has finished. */
+/* Allocation-free stepping (the paper has no counterpart).  For callers that
+ * cannot allocate device memory: a process whose GPU memory another
+ * framework's caching pool has reserved up front, so that cudaMalloc fails or
+ * would fragment that pool; a plugin host that hands its plugins buffers but
+ * no allocator; a loop with a fixed memory budget that must not risk an
+ * allocation failing half way through a run.  Advances ONE instance held in
+ * caller-owned device buffers B and D (FP32, nz elements each, the state
+ * (B^n, D^{n+1/2}) with n = n_done) by n_steps steps, with the medium given as
+ * in gfdtd_set_medium, no sources and no probes, using the same kernels and
+ * tile shape (16 cells per lane, 16 steps per time block) as gfdtd_step.
+ * Every working buffer lives in one statically allocated device array of
+ * about 4.4 MB that each GPU loading this library keeps until the process
+ * exits; no call allocates or frees memory.  Limits: 1 <= nz <= 2^18 and
+ * n <= 1024 profile values, otherwise E_ARG.  The first call on each device
+ * sets up: it looks up the array's device address (cudaGetSymbolAddress), so
+ * make that first call before any stream capture.  All calls share the array,
+ * which keeps the last call's contents (each call clears what has to start at
+ * zero): calls whose work overlaps on the GPU (other streams, other threads)
+ * race and corrupt each other.  The call synchronises cuda_stream before it
+ * returns; when a kernel's bounded wait gave up it returns E_TIMEOUT and
+ * leaves B and D as they were. */
 gfdtd_status gfdtd_step_noalloc(int64_t nz, double S, gfdtd_kind kind, double beta,
                                 gfdtd_interp interp, int n, const double* z, const double* eps_r,
                                 const double* mu_r, float* B, float* D, int64_t n_done,

@@ -8,6 +8,7 @@
 // per (chunk length, buffer parity) into a CUDA graph and replayed.
 #include "../../include/gfdtd.h"
 #include "gfdtd_block.cuh"
+#include "gfdtd_medium.h"
 
 #include <algorithm>
 #include <cmath>
@@ -44,8 +45,6 @@ int elem_bytes_of(gfdtd_prec p) {
     default: return 0;
   }
 }
-
-long long to_fixed(double x) { return llround(ldexp(x, 32)); }
 
 struct Medium {
   gfdtd_kind kind = GFDTD_PERTURBATION;
@@ -236,16 +235,6 @@ static double max_zeta(double S, double beta, double ie, double im, double bc) {
   return worst;
 }
 
-static void medium_coefs(gfdtd_kind kind, double beta, double e, double m, double* ie, double* im,
-                         double* bc) {
-  if (kind == GFDTD_PERTURBATION) {
-    *ie = 1.0 / e; *im = 1.0 / m; *bc = beta;
-    return;
-  }
-  const double den = e * m - beta * beta, g = 1.0 - beta * beta;
-  *ie = g * m / den; *im = g * e / den; *bc = beta * g / den;
-}
-
 // Relative permittivity and permeability of a medium at moving coordinate xi
 // (units of 2^-32 cell): a layers profile holds value i on [z_{i-1}, z_i), a
 // linear one interpolates between knots and holds its end values beyond them.
@@ -273,12 +262,6 @@ static void medium_at(const Medium& m, long long xi, double& e, double& u) {
 }
 
 // ------------------------------------------------------------------ finalize
-
-static std::vector<float2> to_f32(const std::vector<double2>& v) {
-  std::vector<float2> out(v.size());
-  for (size_t i = 0; i < v.size(); ++i) out[i] = make_float2((float)v[i].x, (float)v[i].y);
-  return out;
-}
 
 // Tiles of every instance, split by kernel variant: 0 general moving
 // perturbation, 1 general moving matter, 2 fast interior tiles (see
@@ -418,6 +401,7 @@ static gfdtd_status finalize(gfdtd_ctx* c) {
   std::vector<InstDev> inst(c->n_inst);
   std::vector<long long> zq;
   std::vector<double2> tabE, tabH;
+  std::vector<float2> tabE32, tabH32;
   std::vector<SrcDev> srcs;
   std::vector<PrbDev> prbs;
   std::vector<double> omega, acc_re, acc_im;
@@ -437,65 +421,17 @@ static gfdtd_status finalize(gfdtd_ctx* c) {
     d.off = c->off[i];
     d.nz = (int)c->nz[i];
     d.nz_pad = (int)((c->nz[i] + 31) / 32 * 32);
-    d.dq = llround(ldexp(m.beta * S, 31));
-    d.n = (int)m.eps.size();
-    d.minw = 0;
-    d.tab = (int)tabE.size();
-    d.a = 1.0 - std::fabs(m.beta) * S;
-    d.c = std::fabs(m.beta) * S;
-    d.S = S;
-    d.inv_S = 1.0 / S;
-    d.beta = m.beta;
-    d.cb = 0.5 * S * m.beta;
-    d.a32 = (float)d.a;
-    d.c32 = (float)d.c;
-    d.cb32 = (float)d.cb;
-    d.sm32 = 0.0f;
-    d.abs_w = (int)m.absorb_width;
-    d.abs_sigma = m.absorb_sigma;
-    int flags = 0;
-    if (m.beta >= 0.0) flags |= F_POS;
-    if (m.kind == GFDTD_MATTER) flags |= F_MATTER;
-    const int nvals = (int)m.eps.size();
-    if (m.interp == GFDTD_LINEAR) {
-      flags |= F_LINEAR;
-      // a moving-perturbation profile whose eps (or mu) knots are all equal has a
-      // uniform S/eps (or S/mu): the kernels then skip that side's interpolation
-      bool econst = m.kind != GFDTD_MATTER, mconst = m.kind != GFDTD_MATTER;
-      for (int k = 0; k < nvals; ++k) {
-        zq.push_back(to_fixed(m.z[k]));
-        tabE.push_back(make_double2(m.eps[k], m.mu[k]));
-        tabH.push_back(make_double2(m.eps[k], m.mu[k]));
-        if (m.eps[k] != m.eps[0]) econst = false;
-        if (m.mu[k] != m.mu[0]) mconst = false;
-      }
-      if (econst) flags |= F_EPS_CONST;
-      if (mconst) flags |= F_MU_CONST;
-      d.sm32 = (float)(S / m.mu[0]);
-    } else {
-      bool econst = true, mconst = true;
-      for (int k = 0; k < nvals; ++k) {
-        if (k < nvals - 1) zq.push_back(to_fixed(m.z[k]));
-        double ie, im, bc;
-        medium_coefs(m.kind, m.beta, m.eps[k], m.mu[k], &ie, &im, &bc);
-        const double2 e = make_double2(S * ie, 0.5 * S * bc);
-        const double2 h = make_double2(S * im, 0.5 * S * bc);
-        if (k > 0 && (e.x != tabE[d.tab].x || e.y != tabE[d.tab].y)) econst = false;
-        if (k > 0 && (h.x != tabH[d.tab].x || h.y != tabH[d.tab].y)) mconst = false;
-        tabE.push_back(e);
-        tabH.push_back(h);
-      }
-      while (zq.size() < tabE.size()) zq.push_back(0);   // keep zq aligned with the tables
-      // boundaries move rigidly, so their node indices stay at least floor(width) - 1 apart
-      double wmin = 1e30;
-      for (int k = 1; k + 1 < nvals; ++k) wmin = std::min(wmin, m.z[k] - m.z[k - 1]);
-      d.minw = wmin > 1e9 ? (1 << 30) : std::max(0, (int)std::floor(wmin) - 1);
-      if (econst) flags |= F_EPS_CONST;
-      if (mconst) flags |= F_MU_CONST;
-      d.sm32 = (float)tabH[d.tab].x;
-    }
-    while (zq.size() < tabE.size()) zq.push_back(0);
-    d.flags = flags;
+    MediumSpec ms;
+    ms.kind = (int)m.kind;
+    ms.beta = m.beta;
+    ms.interp = (int)m.interp;
+    ms.n = (int)m.eps.size();
+    ms.z = m.z.data();
+    ms.eps = m.eps.data();
+    ms.mu = m.mu.data();
+    ms.absorb_width = m.absorb_width;
+    ms.absorb_sigma = m.absorb_sigma;
+    fill_instance(ms, S, d, zq, tabE, tabH, tabE32, tabH32);
     d.src0 = (int)srcs.size();
     d.nsrc = (int)c->sources[i].size();
     for (const SrcDev& s : c->sources[i]) srcs.push_back(s);
@@ -525,8 +461,8 @@ static gfdtd_status finalize(gfdtd_ctx* c) {
   c->n_bins = (int)omega.size();
   gfdtd_status s;
   if ((s = upload(c, c->d_inst, inst)) || (s = upload(c, c->d_zq, zq)) || (s = upload(c, c->d_tabE, tabE)) ||
-      (s = upload(c, c->d_tabH, tabH)) || (s = upload(c, c->d_tabE32, to_f32(tabE))) ||
-      (s = upload(c, c->d_tabH32, to_f32(tabH))) || (s = upload(c, c->d_srcs, srcs)) ||
+      (s = upload(c, c->d_tabH, tabH)) || (s = upload(c, c->d_tabE32, tabE32)) ||
+      (s = upload(c, c->d_tabH32, tabH32)) || (s = upload(c, c->d_srcs, srcs)) ||
       (s = upload(c, c->d_prbs, prbs)) || (s = upload(c, c->d_omega, omega)) ||
       (s = upload(c, c->d_binprb, binprb)) || (s = upload(c, c->d_acc_re, acc_re)) ||
       (s = upload(c, c->d_acc_im, acc_im)))
@@ -542,18 +478,23 @@ static gfdtd_status finalize(gfdtd_ctx* c) {
       double e, u;
       medium_at(m, (long long)t.node << 32, e, u);
       double ie, im, bc;
-      medium_coefs(m.kind, m.beta, e, u, &ie, &im, &bc);
+      medium_coefs((int)m.kind, m.beta, e, u, &ie, &im, &bc);
       t.ie = ie;
       t.im = im;
       t.hb = 0.5 * bc;
       t.beta = m.beta;
       t.S = S;
+      t.se32 = (float)(S * ie);
+      t.sm32 = (float)(S * im);
+      t.cb32 = fp32_coupling(0.5 * S * bc);
+      t.c32 = 2.0f * std::fabs(fp32_coupling(0.5 * S * m.beta));
+      t.a32 = 1.0f - t.c32;
       tfs.push_back(t);
     }
   if ((s = upload(c, c->d_tfsf, tfs))) return s;
   if ((int)tfs.size() != c->n_tfsf) {
     // a new set of auxiliary grids starts from rest (the existing ones keep their state otherwise)
-    const size_t aux_bytes = std::max<size_t>(16, tfs.size() * 2 * kTfsfAuxN * sizeof(double));
+    const size_t aux_bytes = std::max<size_t>(16, tfs.size() * 2 * kTfsfAuxPad * sizeof(double));
     if ((s = dalloc(c, c->d_tfaux, aux_bytes)) ||
         (s = dalloc(c, c->d_tfcorr, std::max<size_t>(16, tfs.size() * kChunk * kTfsfCorr * sizeof(double)))))
       return s;
@@ -1152,7 +1093,7 @@ gfdtd_status gfdtd_set_medium(gfdtd_ctx* c, int inst, gfdtd_kind kind, double be
       for (int j = 0; j < i && !seen; ++j) seen = eps_r[j] == eps_r[i] && mu_r[j] == mu_r[i];
       if (seen) continue;
       double ie, im, bc;
-      medium_coefs(kind, beta, eps_r[i], mu_r[i], &ie, &im, &bc);
+      medium_coefs((int)kind, beta, eps_r[i], mu_r[i], &ie, &im, &bc);
       const double g = max_zeta(c->S, beta, ie, im, bc);
       if (g > 1.0 + 1e-9)
         return fail(c, GFDTD_E_UNSTABLE, "eps=%g mu=%g beta=%g: max|zeta| = %.9f > 1 (n|beta| > 1)",
@@ -1543,7 +1484,7 @@ gfdtd_status gfdtd_stability(double S, double beta, double eps_r, double mu_r, g
     return GFDTD_E_ARG;
   if (kind != GFDTD_PERTURBATION && kind != GFDTD_MATTER) return GFDTD_E_ARG;
   double ie, im, bc;
-  medium_coefs(kind, beta, eps_r, mu_r, &ie, &im, &bc);
+  medium_coefs((int)kind, beta, eps_r, mu_r, &ie, &im, &bc);
   *out = max_zeta(S, beta, ie, im, bc);
   return GFDTD_OK;
 }

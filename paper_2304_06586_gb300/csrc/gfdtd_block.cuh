@@ -122,6 +122,13 @@ __device__ __forceinline__ void store_cells(T* __restrict__ p, int k0, int lo, i
 
 // ------------------------------------------------------------ material
 
+// The FP64 or the FP32 copy of an instance coefficient, whichever R is (the FP32
+// copies of a, c and cb are rounded so that a + c = 1 and c = 2 |cb| hold exactly).
+template <typename R> __device__ __forceinline__ R coef(double d, float f);
+template <> __device__ __forceinline__ float coef<float>(double, float f) { return f; }
+template <> __device__ __forceinline__ double coef<double>(double d, float) { return d; }
+
+
 // First node at or beyond a profile position zq when the frame has moved by
 // `off` (units of 2^-32 cell): ceil((zq + off) / 2^32).  For integer nodes at
 // half level h, off = dq h; for half nodes, off = dq h - 2^31.
@@ -181,7 +188,7 @@ __device__ __forceinline__ void linear_coef(const InstDev& I, const long long* _
   const R S = (R)I.S;
   if (!MATTER) {
     cx = S / (ESIDE ? e : m);
-    cy = (R)I.cb;
+    cy = coef<R>(I.cb, I.cb32);
   } else {
     const R b = (R)I.beta, g = (R)1 - b * b;
     const R den = e * m - b * b;
@@ -203,7 +210,7 @@ __device__ __forceinline__ void node_coef(const InstDev& I, const Tables& tb, lo
   }
   const auto v = __ldg(tv + count_at_or_left(zq, I.n - 1, off, k));
   cx = v.x;
-  cy = MATTER ? v.y : (R)I.cb;
+  cy = MATTER ? v.y : coef<R>(I.cb, I.cb32);
 }
 
 // Per-lane material of the run of C cells starting at k0 at one half level.
@@ -266,7 +273,7 @@ __device__ __forceinline__ void lane_coefs(const InstDev& I, const Tables& tb, l
     const int nk = I.n;
     while (li < nk && node_of(__ldg(zq + li), off) <= k0) ++li;
     while (li > 0 && node_of(__ldg(zq + li - 1), off) > k0) --li;
-    const R S = (R)I.S, beta = (R)I.beta, cb = (R)I.cb;
+    const R S = (R)I.S, beta = (R)I.beta, cb = coef<R>(I.cb, I.cb32);
     const long long xi0 = ((long long)k0 << 32) - off;
     const int K1 = li < nk ? node_of(__ldg(zq + li), off) : INT_MAX;
     const int K2 = li + 1 < nk ? node_of(__ldg(zq + li + 1), off) : INT_MAX;
@@ -384,7 +391,7 @@ __device__ __forceinline__ void run_tile(const BlockArgs<T>& A, const InstDev& I
     load_cells<T, R, KAHAN ? C : 1>(A.cDin + I.off, k0, I.nz_pad, cDv);
   }
 
-  const R a = (R)I.a, cc = (R)I.c;
+  const R a = coef<R>(I.a, I.a32), cc = coef<R>(I.c, I.c32);
   const bool damp = window_absorbs(I, base, 32 * C);   // the tile reaches an absorbing layer
   bool eps_const = (I.flags & F_EPS_CONST) != 0;
   bool mu_const = (I.flags & F_MU_CONST) != 0;
@@ -415,7 +422,7 @@ __device__ __forceinline__ void run_tile(const BlockArgs<T>& A, const InstDev& I
   const auto h0 = __ldg(TabOf<R>::get(A.tb, false) + I.tab + rH);
   // (uniform values: LINEAR tables hold raw (eps, mu), LAYERS tables the coefficients)
   const R se0 = lin ? (R)I.S / e0.x : e0.x, sm0 = lin ? (R)I.S / h0.y : h0.x;
-  const R cbe0 = MATTER ? e0.y : (R)I.cb, cbh0 = MATTER ? h0.y : (R)I.cb;
+  const R cbe0 = MATTER ? e0.y : coef<R>(I.cb, I.cb32), cbh0 = MATTER ? h0.y : coef<R>(I.cb, I.cb32);
   int liE = 0, liH = 0;
   if (!eps_const || !mu_const) {
     const int nb = (I.flags & F_LINEAR) ? I.n : I.n - 1;
@@ -700,11 +707,6 @@ __device__ __forceinline__ bool mbar_wait_bounded(unsigned long long* bar, unsig
 // c >= ceil(d / 2^32) of the run lie beyond the boundary.  The B update takes
 // one multiplier per lane (the layer of the whole run); the few lanes with a
 // boundary inside their run then add the difference of the two layers' P.
-
-// The FP64 or the FP32 copy of an instance coefficient, whichever R is.
-template <typename R> __device__ __forceinline__ R coef(double d, float f);
-template <> __device__ __forceinline__ float coef<float>(double, float f) { return f; }
-template <> __device__ __forceinline__ double coef<double>(double d, float) { return d; }
 
 struct BoundaryTrack {
   long long dprev, dnext;     // zq_b + dq h - k0 2^32 of the boundaries around k0
@@ -1053,9 +1055,10 @@ __device__ __forceinline__ void run_tile_fast(const BlockArgs<T>& A, const InstD
     A.track[t].lane[lane] = o;
     if (lane == 0) A.track[t].n = n0 + A.nsteps;
   }
-  const R inv_sm = (R)1 / sm;
+  // back to B: a division, not a multiplication by 1/sm, whose rounding would
+  // scale B by the same factor at every launch
 #pragma unroll
-  for (int c = 0; c < C; ++c) B[c] *= inv_sm;      // back to B
+  for (int c = 0; c < C; ++c) B[c] = B[c] / sm;
   const int hi = min(x0 + W, I.nz_pad);
   store_cells<T, R, C>(A.Bout + I.off, k0, x0, hi, B);
   store_cells<T, R, C>(A.Dout + I.off, k0, x0, hi, D);

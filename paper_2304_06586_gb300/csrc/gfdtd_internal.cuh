@@ -128,23 +128,34 @@ struct TrackTile {
 };
 static_assert(sizeof(TrackTile) % 16 == 0, "TrackTile is copied by TMA in 16-byte units");
 
-// Arguments of one time-block launch of the batched kernel.
 // One-way (total-field / scattered-field) source: total field at nodes >= node.
 // Its incident wave is computed in an auxiliary grid of the same scheme in
 // the uniform background (the material at `node` at t = 0): kTfsfAuxN cells,
 // graded absorbing layers of kTfsfAuxW cells and strength kTfsfAuxSigma at both
-// ends, a soft source with the given waveform at aux node kTfsfAuxSrc and the
-// boundary at aux node kTfsfAuxQ.
+// ends of a 40-cell interior, a soft source with the given waveform at aux
+// node kTfsfAuxSrc and the boundary at aux node kTfsfAuxQ.  (The layer width
+// is the smallest power of two that reflects below 1e-6 of the incident wave
+// in moving vacuum for |beta| <= 0.6.)  Each grid is stored as kTfsfAuxPad
+// values of B then kTfsfAuxPad values of D, the cells past kTfsfAuxN held at
+// zero, so that the FP32 kernel spreads a grid evenly over the 32 lanes of
+// one warp.
 struct TfsfDev {
   int inst;
   int node;
   double ie, im, hb;            // background 1/eps_m, 1/mu_m and beta_c / 2
   double beta, S;
   double omega0, tau, t0, amp;  // waveform of the auxiliary soft source
+  float se32, sm32;             // FP32 weights of the background: S ie, S im,
+  float cb32, a32, c32;         //   S hb, 1 - |beta| S, |beta| S (rounded as the main kernels' weights)
+  float pad;
 };
-constexpr int kTfsfAuxN = 1088, kTfsfAuxW = 524, kTfsfAuxSrc = 532, kTfsfAuxQ = 544;
+constexpr int kTfsfAuxN = 1064, kTfsfAuxW = 512, kTfsfAuxSrc = 520, kTfsfAuxQ = 532;
+constexpr int kTfsfAuxPad = 1088;               // 32 lanes x 34 cells
+static_assert(kTfsfAuxPad % 32 == 0 && kTfsfAuxPad >= kTfsfAuxN, "padded aux grid");
 constexpr double kTfsfAuxSigma = 0.05;
 constexpr int kTfsfCorr = 6;    // corrections per step: B at node-2 .. node+1, D at node-1 .. node
+
+// Arguments of one time-block launch of the batched kernel.
 
 template <typename T>
 struct BlockArgs {
@@ -256,7 +267,7 @@ struct SourceAdjArgs {
   double* gn;                 // [step][inst]
 };
 int adjoint_step_launch(const AdjArgs& a, cudaStream_t st);
-// Advances the auxiliary grids of n one-way sources (FP64 or FP32 state, 2 kTfsfAuxN
+// Advances the auxiliary grids of n one-way sources (FP64 or FP32 state, 2 kTfsfAuxPad
 // values each) by nsteps steps from step *n_done and writes each step's corrections
 // to corr ([source][chunk_stride][kTfsfCorr]).
 int tfsf_aux_launch(const TfsfDev* tf, int n, void* aux, bool fp64, double* corr, int chunk_stride,

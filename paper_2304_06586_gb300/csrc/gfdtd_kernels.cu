@@ -77,7 +77,7 @@ __device__ void plain_cell(const PlainArgs<T>& A, const InstDev& I, int k) {
   const T* __restrict__ Di = A.Din + I.off;
   auto ld = [&](const T* p, int j) -> R { return (j >= 0 && j < nz) ? (R)p[j] : (R)0; };
   const bool pos = (I.flags & F_POS) != 0;
-  const R a = (R)I.a, cc = (R)I.c;
+  const R a = coef<R>(I.a, I.a32), cc = coef<R>(I.c, I.c32);
   const long long n = A.n;
   const long long offE = I.dq * (2 * n - 1), offH = I.dq * (2 * n) - HALF_CELL;
 
@@ -386,8 +386,8 @@ __global__ void __launch_bounds__(kTfsfThreads, 4) tfsf_aux_kernel(const TfsfDev
   constexpr int PER = (N + kTfsfThreads - 1) / kTfsfThreads;   // cells per thread
   __shared__ R sB[N], sD[N], sE[N], sH[N];
   const TfsfDev tf = tfs[blockIdx.x];
-  R* gB = aux + (size_t)blockIdx.x * 2 * N;
-  R* gD = gB + N;
+  R* gB = aux + (size_t)blockIdx.x * 2 * kTfsfAuxPad;
+  R* gD = gB + kTfsfAuxPad;
   const int tid = threadIdx.x, nt = kTfsfThreads;
   for (int i = tid; i < N; i += nt) { sB[i] = gB[i]; sD[i] = gD[i]; }
   const R S = (R)tf.S, beta = (R)tf.beta, ie = (R)tf.ie, im = (R)tf.im, hb = (R)tf.hb;
@@ -487,10 +487,14 @@ __global__ void __launch_bounds__(kTfsfThreads, 4) tfsf_aux_kernel(const TfsfDev
 // consecutive cells of B and D in registers through the chunk, neighbours move
 // by shuffles, and no block barrier is taken inside the time loop (the
 // shared-memory form above, with six barriers a step, made the sources' grids
-// cost as much as the batch they drive).  The damping factors, the same for
-// every source, sit in shared memory.
-constexpr int kAuxCPL = kTfsfAuxN / 32;
-static_assert(kTfsfAuxN % 32 == 0, "aux grid spread over the lanes of one warp");
+// cost as much as the batch they drive).  The grid's kTfsfAuxN cells are padded
+// to kTfsfAuxPad = 32 x 34: the padding cells lie outside the grid, where every
+// field is zero, so their damping factor is 0 and their E' is forced to 0.
+// The update has the main kernels' form and FP32 weights (E' = S E*, H' = S H*;
+// a + c = 1 and, for moving perturbation, c = 2 |cb| exactly), so the incident
+// wave carries no drift of its own over long runs.  The damping factors, the
+// same for every source, sit in shared memory.
+constexpr int kAuxCPL = kTfsfAuxPad / 32;
 
 template <int K> struct AuxCell { static constexpr int lane = K / kAuxCPL, c = K % kAuxCPL; };
 
@@ -498,14 +502,14 @@ __global__ void __launch_bounds__(128, 4) tfsf_aux_warp_kernel(const TfsfDev* __
                                                             float* __restrict__ aux, double* __restrict__ corr,
                                                             int chunk_stride, const long long* __restrict__ n_done,
                                                             int nsteps) {
-  constexpr int N = kTfsfAuxN, CPL = kAuxCPL;
+  constexpr int N = kTfsfAuxN, P = kTfsfAuxPad, CPL = kAuxCPL;
   using Qm2 = AuxCell<kTfsfAuxQ - 2>;
   using Qm1 = AuxCell<kTfsfAuxQ - 1>;
   using Q0 = AuxCell<kTfsfAuxQ>;
   using Qp1 = AuxCell<kTfsfAuxQ + 1>;
   using Src = AuxCell<kTfsfAuxSrc>;
-  __shared__ float sfB[N], sfD[N];
-  for (int i = threadIdx.x; i < N; i += blockDim.x) {
+  __shared__ float sfB[P], sfD[P];
+  for (int i = threadIdx.x; i < P; i += blockDim.x) {
     auto f = [](double x) {
       const double W = (double)kTfsfAuxW, right = (double)(N - 1) - W;
       double d = 0.0;
@@ -513,21 +517,20 @@ __global__ void __launch_bounds__(128, 4) tfsf_aux_warp_kernel(const TfsfDev* __
       else if (x > right) d = (x - right) / W;
       return (float)exp(-kTfsfAuxSigma * d * d);
     };
-    sfB[i] = f((double)i + 0.5);
-    sfD[i] = f((double)i);
+    sfB[i] = i < N ? f((double)i + 0.5) : 0.0f;
+    sfD[i] = i < N ? f((double)i) : 0.0f;
   }
   __syncthreads();
   const int w = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
   if (w >= n_src) return;                    // whole warps; no barrier follows
   const int lane = threadIdx.x & 31, k0 = lane * CPL;
   const TfsfDev tf = tfs[w];
-  float* gB = aux + (size_t)w * 2 * N;
-  float* gD = gB + N;
+  float* gB = aux + (size_t)w * 2 * P;
+  float* gD = gB + P;
   float B[CPL], D[CPL];
 #pragma unroll
   for (int c = 0; c < CPL; ++c) { B[c] = gB[k0 + c]; D[c] = gD[k0 + c]; }
-  const float S = (float)tf.S, ie = (float)tf.ie, im = (float)tf.im, hb = (float)tf.hb;
-  const float uS = (float)(tf.beta * tf.S);
+  const float se = tf.se32, sm = tf.sm32, cb = tf.cb32, a = tf.a32, cc = tf.c32;
   const bool pos = tf.beta >= 0.0, first = lane == 0, last = lane == 31;
   const long long n0 = *n_done;
   double* out = corr + (size_t)w * chunk_stride * kTfsfCorr;
@@ -537,25 +540,25 @@ __global__ void __launch_bounds__(128, 4) tfsf_aux_warp_kernel(const TfsfDev* __
     const float Bm2 = __shfl_sync(FULL, B[Qm2::c], Qm2::lane), Bm1 = __shfl_sync(FULL, B[Qm1::c], Qm1::lane);
     const float B0 = __shfl_sync(FULL, B[Q0::c], Q0::lane), Bp1 = __shfl_sync(FULL, B[Qp1::c], Qp1::lane);
     const float Dm1 = __shfl_sync(FULL, D[Qm1::c], Qm1::lane), D0 = __shfl_sync(FULL, D[Q0::c], Q0::lane);
-    // E* = ie D - hb (two B of the Table 1 average), then B^n (old B throughout)
+    // E' = se D - cb (two B of the Table 1 average), then B^n (old B throughout)
     if (pos) {
       const float t1 = __shfl_up_sync(FULL, B[CPL - 1], 1), t2 = __shfl_up_sync(FULL, B[CPL - 2], 1);
       const float bl1 = first ? 0.0f : t1, bl2 = first ? 0.0f : t2;
-      const float e0 = ie * D[0] - hb * (bl1 + bl2);
+      const float e0 = se * D[0] - cb * (bl1 + bl2);
       const float te = __shfl_down_sync(FULL, e0, 1);
-      float en = last ? 0.0f : te;            // E* one cell to the right
+      float en = last ? 0.0f : te;            // E' one cell to the right
 #pragma unroll
       for (int c = CPL - 1; c >= 0; --c) {
         const float b1 = c >= 1 ? B[c - 1] : bl1;
         const float b2 = c >= 2 ? B[c - 2] : (c == 1 ? bl1 : bl2);
-        const float ec = ie * D[c] - hb * (b1 + b2);
-        B[c] = (B[c] - S * (en - ec) - uS * (B[c] - b1)) * sfB[k0 + c];
+        const float ec = k0 + c < N ? se * D[c] - cb * (b1 + b2) : 0.0f;
+        B[c] = (a * B[c] + (cc * b1 + (ec - en))) * sfB[k0 + c];
         en = ec;
       }
     } else {
       const float t1 = __shfl_down_sync(FULL, B[0], 1);
       const float br1 = last ? 0.0f : t1;
-      const float e0 = ie * D[0] - hb * (B[1] + B[0]);
+      const float e0 = se * D[0] - cb * (B[1] + B[0]);
       const float te = __shfl_down_sync(FULL, e0, 1);
       const float er = last ? 0.0f : te;
       float ec = e0;
@@ -563,16 +566,16 @@ __global__ void __launch_bounds__(128, 4) tfsf_aux_warp_kernel(const TfsfDev* __
       for (int c = 0; c < CPL; ++c) {
         const float b1 = c + 1 < CPL ? B[c + 1] : br1;
         const float b2 = c + 2 < CPL ? B[c + 2] : br1;          // used only for c + 2 == CPL
-        const float en = c + 1 < CPL ? ie * D[c + 1] - hb * (b2 + b1) : er;
-        B[c] = (B[c] - S * (en - ec) - uS * (b1 - B[c])) * sfB[k0 + c];
+        const float en = c + 1 < CPL ? (k0 + c + 1 < N ? se * D[c + 1] - cb * (b2 + b1) : 0.0f) : er;
+        B[c] = (a * B[c] + (cc * b1 + (ec - en))) * sfB[k0 + c];
         ec = en;
       }
     }
-    // H* = im B^n - hb (D_j + D_{j+1}), then D^{n+1/2} (old D throughout)
+    // H' = sm B^n - cb (D_j + D_{j+1}) (D at level n-1/2), then D^{n+1/2} (old D throughout)
     {
       const float t1 = __shfl_down_sync(FULL, D[0], 1);
       const float dr = last ? 0.0f : t1;
-      const float hlast = im * B[CPL - 1] - hb * (D[CPL - 1] + dr);
+      const float hlast = sm * B[CPL - 1] - cb * (D[CPL - 1] + dr);
       const float th = __shfl_up_sync(FULL, hlast, 1);
       const float hl = first ? 0.0f : th;
       if (pos) {
@@ -582,8 +585,8 @@ __global__ void __launch_bounds__(128, 4) tfsf_aux_warp_kernel(const TfsfDev* __
 #pragma unroll
         for (int c = CPL - 1; c >= 0; --c) {
           const float dp = c >= 1 ? D[c - 1] : dl;
-          const float hp = c >= 1 ? im * B[c - 1] - hb * (D[c - 1] + D[c]) : hl;
-          D[c] = (D[c] - S * (hc - hp) - uS * (D[c] - dp)) * sfD[k0 + c];
+          const float hp = c >= 1 ? sm * B[c - 1] - cb * (D[c - 1] + D[c]) : hl;
+          D[c] = (a * D[c] + (cc * dp + (hp - hc))) * sfD[k0 + c];
           hc = hp;
         }
       } else {
@@ -591,8 +594,8 @@ __global__ void __launch_bounds__(128, 4) tfsf_aux_warp_kernel(const TfsfDev* __
 #pragma unroll
         for (int c = 0; c < CPL; ++c) {
           const float dn = c + 1 < CPL ? D[c + 1] : dr;
-          const float hc = im * B[c] - hb * (D[c] + dn);
-          D[c] = (D[c] - S * (hc - hp) - uS * (dn - D[c])) * sfD[k0 + c];
+          const float hc = sm * B[c] - cb * (D[c] + dn);
+          D[c] = (a * D[c] + (cc * dn + (hp - hc))) * sfD[k0 + c];
           hp = hc;
         }
       }
@@ -603,22 +606,22 @@ __global__ void __launch_bounds__(128, 4) tfsf_aux_warp_kernel(const TfsfDev* __
     }
     const float Bn = __shfl_sync(FULL, B[Qm1::c], Qm1::lane);
     if (first) {
-      const double S_ = S, ie_ = ie, im_ = im, hb_ = hb, uS_ = uS;
+      const double se_ = se, sm_ = sm, cb_ = cb, uS = pos ? (double)cc : -(double)cc;   // uS = beta S
       double* c = out + (size_t)s * kTfsfCorr;
       if (pos) {
         c[0] = 0.0;
-        c[1] = S_ * ie_ * D0;
-        c[2] = -S_ * hb_ * Bm2 + uS_ * Bm1;
-        c[3] = -S_ * hb_ * Bm1;
-        c[4] = -S_ * hb_ * D0;
-        c[5] = S_ * (im_ * Bn - hb_ * Dm1) + uS_ * Dm1;
+        c[1] = se_ * D0;
+        c[2] = -cb_ * Bm2 + uS * Bm1;
+        c[3] = -cb_ * Bm1;
+        c[4] = -cb_ * D0;
+        c[5] = (sm_ * Bn - cb_ * Dm1) + uS * Dm1;
       } else {
-        c[0] = -S_ * hb_ * B0;
-        c[1] = S_ * ie_ * D0 - S_ * hb_ * Bp1 + uS_ * B0;
+        c[0] = -cb_ * B0;
+        c[1] = se_ * D0 - cb_ * Bp1 + uS * B0;
         c[2] = 0.0;
         c[3] = 0.0;
-        c[4] = -S_ * hb_ * D0 + uS_ * D0;
-        c[5] = S_ * (im_ * Bn - hb_ * Dm1);
+        c[4] = -cb_ * D0 + uS * D0;
+        c[5] = sm_ * Bn - cb_ * Dm1;
       }
     }
   }

@@ -2,16 +2,20 @@
 // on caller-owned field buffers with every working buffer taken from one
 // statically allocated device array, so the call allocates no memory.
 //
-// Some callers cannot allocate device memory: code running inside a CUDA
-// graph capture (cudaMalloc is not capturable), processes whose memory is
-// owned by another framework's pool with no hook for this library, and
-// real-time loops that must not block on the allocator.  For them this entry
-// point advances one 1D instance with scratch that lives in a file-scope
+// Who needs this: a caller whose device memory is not its own to allocate.
+// A process whose GPU memory has been reserved up front by another framework's
+// caching pool (a training or serving job) may find cudaMalloc failing, or
+// may be forbidden to fragment that pool; a plugin host may hand its plugins
+// buffers but no allocator; a loop with a fixed memory budget may not risk an
+// allocation failing half way through a run.  For them this entry point
+// advances one 1D instance with scratch that lives in a file-scope
 // __device__ array sized for at most kMaxCells cells and kMaxValues profile
 // values.  Every GPU that loads the library holds that array (about 4.4 MB)
-// until the process exits.
+// until the process exits.  The call synchronises its stream before it
+// returns.
 #include "../../include/gfdtd.h"
 #include "gfdtd_block.cuh"
+#include "gfdtd_medium.h"
 
 #include <cmath>
 #include <cstring>
@@ -70,7 +74,7 @@ extern "C" gfdtd_status gfdtd_step_noalloc(int64_t nz, double S, gfdtd_kind kind
     if (!(z[i] > z[i - 1])) return GFDTD_E_ARG;
   cudaStream_t st = (cudaStream_t)cuda_stream;
 
-  // ---- scratch address on this device (first call per device; not capturable)
+  // ---- scratch address on this device (looked up by the first call on each device)
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return GFDTD_E_CUDA;
   if (!g_scratch_addr[dev]) {
@@ -82,62 +86,24 @@ extern "C" gfdtd_status gfdtd_step_noalloc(int64_t nz, double S, gfdtd_kind kind
   float* fld[4];
   for (int k = 0; k < 4; ++k) fld[k] = reinterpret_cast<float*>(base + kOffFields + k * kFieldBytes);
 
-  // ---- the instance and its tables, built on the host
+  // ---- the instance and its tables, built on the host exactly as the context path builds them
   InstDev I{};
   I.off = 0;
   I.nz = (int)nz;
   I.nz_pad = (int)((nz + 31) / 32 * 32);
-  I.dq = llround(ldexp(beta * S, 31));
-  I.n = n;
-  I.tab = 0;
-  I.a = 1.0 - std::fabs(beta) * S;
-  I.c = std::fabs(beta) * S;
-  I.S = S;
-  I.inv_S = 1.0 / S;
-  I.beta = beta;
-  I.cb = 0.5 * S * beta;
-  I.a32 = (float)I.a;
-  I.c32 = (float)I.c;
-  I.cb32 = (float)I.cb;
-  I.minw = 0;
-  int flags = (beta >= 0.0 ? F_POS : 0) | (kind == GFDTD_MATTER ? F_MATTER : 0);
-  std::vector<long long> zq(n, 0);
-  std::vector<double2> tE(n), tH(n);
-  std::vector<float2> tE32(n), tH32(n);
-  if (interp == GFDTD_LINEAR) {
-    flags |= F_LINEAR;
-    for (int k = 0; k < n; ++k) {
-      zq[k] = llround(ldexp(z[k], 32));
-      tE[k] = tH[k] = make_double2(eps_r[k], mu_r[k]);
-    }
-  } else {
-    bool econst = true, mconst = true;
-    double wmin = 1e30;
-    for (int k = 0; k < n; ++k) {
-      if (k < n - 1) zq[k] = llround(ldexp(z[k], 32));
-      if (k >= 1 && k + 1 < n) wmin = std::fmin(wmin, z[k] - z[k - 1]);
-      double ie, im, bc;
-      if (kind == GFDTD_PERTURBATION) {
-        ie = 1.0 / eps_r[k]; im = 1.0 / mu_r[k]; bc = beta;
-      } else {
-        const double den = eps_r[k] * mu_r[k] - beta * beta, g = 1.0 - beta * beta;
-        ie = g * mu_r[k] / den; im = g * eps_r[k] / den; bc = beta * g / den;
-      }
-      tE[k] = make_double2(S * ie, 0.5 * S * bc);
-      tH[k] = make_double2(S * im, 0.5 * S * bc);
-      if (k > 0 && (tE[k].x != tE[0].x || tE[k].y != tE[0].y)) econst = false;
-      if (k > 0 && (tH[k].x != tH[0].x || tH[k].y != tH[0].y)) mconst = false;
-    }
-    I.minw = wmin > 1e9 ? (1 << 30) : std::max(0, (int)std::floor(wmin) - 1);
-    if (econst) flags |= F_EPS_CONST;
-    if (mconst) flags |= F_MU_CONST;
-  }
-  I.flags = flags;
-  I.sm32 = interp == GFDTD_LINEAR ? 0.0f : (float)tH[0].x;
-  for (int k = 0; k < n; ++k) {
-    tE32[k] = make_float2((float)tE[k].x, (float)tE[k].y);
-    tH32[k] = make_float2((float)tH[k].x, (float)tH[k].y);
-  }
+  MediumSpec ms;
+  ms.kind = (int)kind;
+  ms.beta = beta;
+  ms.interp = (int)interp;
+  ms.n = n;
+  ms.z = z;
+  ms.eps = eps_r;
+  ms.mu = mu_r;
+  std::vector<long long> zq;
+  std::vector<double2> tE, tH;
+  std::vector<float2> tE32, tH32;
+  fill_instance(ms, S, I, zq, tE, tH, tE32, tH32);
+  const int flags = I.flags;
   // tiles by kernel variant, as the context path lists them
   std::vector<int2> tiles[3];
   std::vector<FastTile> fast;          // records of tiles[2] (this call has no sources or probes)
@@ -214,10 +180,13 @@ extern "C" gfdtd_status gfdtd_step_noalloc(int64_t nz, double S, gfdtd_kind kind
     }
     cur = 1 - cur;
   }
-  NA_CK(cudaMemcpyAsync(B, fld[2 * cur], sizeof(float) * nz, cudaMemcpyDeviceToDevice, st));
-  NA_CK(cudaMemcpyAsync(D, fld[2 * cur + 1], sizeof(float) * nz, cudaMemcpyDeviceToDevice, st));
+  // status first: on a failed bounded wait the caller's B and D are left as they were
   NA_CK(cudaMemcpyAsync(counter, base + kOffCounter, sizeof(counter), cudaMemcpyDeviceToHost, st));
   NA_CK(cudaStreamSynchronize(st));
+  if ((int)counter[1] & 0xff) return GFDTD_E_TIMEOUT;
+  NA_CK(cudaMemcpyAsync(B, fld[2 * cur], sizeof(float) * nz, cudaMemcpyDeviceToDevice, st));
+  NA_CK(cudaMemcpyAsync(D, fld[2 * cur + 1], sizeof(float) * nz, cudaMemcpyDeviceToDevice, st));
+  NA_CK(cudaStreamSynchronize(st));
 #undef NA_CK
-  return ((int)counter[1] & 0xff) ? GFDTD_E_TIMEOUT : GFDTD_OK;
+  return GFDTD_OK;
 }
