@@ -537,6 +537,16 @@ def main():
             barrier()
         ms = max_over_ranks(e0.elapsed_time(e1), pg, "cuda")
         st = sim.stats()
+        # runtime watchdog over the warm-up and timed steps: instances whose fields
+        # overflowed (non-finite) or passed 1e30, against the host's von Neumann count
+        # of instances with max|zeta| > 1 (n|v| > 1 in their eps = 4 layers, Sec. 5)
+        wflags, _ = sim.watchdog(limit=1e30)
+        unstable_vn = sum(1 for I in wl.instances
+                          if gb.stability(wl.S, I.beta, float(np.max(I.eps)), 1.0, gb.PERTURBATION) > 1 + 1e-9)
+        watchdog = {"instances": len(wl.instances), "non_finite": int(np.sum(wflags & 1)),
+                    "above_1e30_or_non_finite": int(np.sum((wflags & 2) != 0)),
+                    "flagged": int(np.sum(wflags != 0)), "unstable_by_von_neumann": unstable_vn,
+                    "steps_recorded": T * (args.steps + args.warmup)}
         launches = st["kernel_launches"] - l0
         cells = st["cells"]
         cu = cells * T * args.steps
@@ -649,7 +659,7 @@ def main():
                        "time_steps_per_step": T, "tile": [st["cells_per_lane"], st["time_block"], st["blocks_per_sm"]],
                        "l2": "inputs larger than L2 (%.2f GB of fields)" % (cells * 16 / 1e9),
                        "parallelism": "instances sharded per rank" if world > 1 else "1 GPU"},
-            "e2e": e2e, "gpu_launches": launches, "roofline": roofline, "plain": plain,
+            "e2e": e2e, "gpu_launches": launches, "roofline": roofline, "plain": plain, "watchdog": watchdog,
             "clocks": clocks, "sweeps": sweeps, "capture": capture, "absorber": absorber, "adjoint": adjoint,
             "tfsf": tfsf, "examples": examples}
     if not args.no_cpu:

@@ -349,6 +349,32 @@ gfdtd_status gfdtd_star_tmm(int64_t n_stacks, const int64_t* layer_off, const do
                             const double* mu_r, const double* thick, const double* beta, int64_t n_freq,
                             const double* omega, double* T, double* Gamma, void* cuda_stream);
 
+/* Runtime stability watchdog.  The scheme is unstable where n|beta| > 1
+ * (Sec. 5, App. A: the amplification factor of some mode exceeds one), and
+ * an instance run there (allow_unstable) grows until it overflows.  At the
+ * end of every chunk of at most 1024 steps of gfdtd_step, gfdtd_step_plain
+ * and gfdtd_profile_kernels, a scan of the state records, per instance, the
+ * largest |B| and |D| (rounded to FP32) and whether any value is not finite;
+ * gfdtd_adjoint and the autotuner's trial launches record nothing.  This call
+ * synchronises the
+ * stream and writes, for each instance i, flags[i] (bit 0: a non-finite value
+ * was written; bit 1: the largest magnitude exceeded `limit` > 0, a
+ * non-finite value counting as infinite) and amax[i] (the largest magnitude,
+ * +inf once a non-finite value was written); either array may be NULL
+ * (n_inst entries each); with reset != 0 the record then starts again from
+ * zero.  The record covers every time block since the context was created or
+ * last reset.  Returns E_UNSTABLE when some instance is flagged, else OK. */
+gfdtd_status gfdtd_watchdog(gfdtd_ctx* ctx, double limit, int reset, int* flags, double* amax);
+
+/* Test hook for the bounded waits (no counterpart in the paper).  With on != 0
+ * the fast kernel's warps arm the barrier of each tile copy but start no copy,
+ * so each wait gives up after its limit (about one second of device time per
+ * warp); the step then reports E_TIMEOUT through gfdtd_synchronize and the
+ * affected steps are not valid.  No copy is ever in flight, so nothing lands
+ * after a block has exited.  on = 0 restores normal operation.  Takes effect
+ * at the next step. */
+gfdtd_status gfdtd_test_stall(gfdtd_ctx* ctx, int on);
+
 /* Wait for all work queued on the context's stream; returns E_TIMEOUT (once)
  * if a kernel reported that a bounded wait gave up since the last check.
  * gfdtd_read_fields and gfdtd_read_spectrum report it the same way. */

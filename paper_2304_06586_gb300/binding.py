@@ -79,6 +79,8 @@ SIGNATURES = {
     "gfdtd_read_capture": (C.c_int, [C.c_void_p, _dp, C.c_int64]),
     "gfdtd_profile_kernels": (C.c_int, [C.c_void_p, C.c_int64, C.POINTER(KernelTimes)]),
     "gfdtd_synchronize": (C.c_int, [C.c_void_p]),
+    "gfdtd_watchdog": (C.c_int, [C.c_void_p, C.c_double, C.c_int, C.POINTER(C.c_int), _dp]),
+    "gfdtd_test_stall": (C.c_int, [C.c_void_p, C.c_int]),
     "gfdtd_last_error": (C.c_char_p, [C.c_void_p]),
     "gfdtd_destroy": (None, [C.c_void_p]),
     "gfdtd_step_noalloc": (C.c_int, [C.c_int64, C.c_double, C.c_int, C.c_double, C.c_int, C.c_int, _dp,
@@ -380,6 +382,23 @@ class Simulation:
 
     def synchronize(self):
         self._check(self._L.gfdtd_synchronize(self._h), "synchronize")
+
+    def watchdog(self, limit=1e30, reset=False):
+        """gfdtd_watchdog: per-instance flags (bit 0 non-finite, bit 1 above
+        `limit`) and largest |B|, |D| written since creation or the last reset.
+        Returns (flags, amax); an E_UNSTABLE status is the flags themselves."""
+        n = len(self.nz)
+        flags = np.zeros(n, dtype=np.int32)
+        amax = np.zeros(n)
+        rc = self._L.gfdtd_watchdog(self._h, float(limit), int(bool(reset)),
+                                    flags.ctypes.data_as(C.POINTER(C.c_int)), _ptr(amax))
+        if rc not in (OK, E_UNSTABLE):
+            self._check(rc, "watchdog")
+        return flags, amax
+
+    def test_stall(self, on):
+        """gfdtd_test_stall: make the fast kernel's bounded waits run out (test hook)."""
+        self._check(self._L.gfdtd_test_stall(self._h, int(bool(on))), "test_stall")
 
 
 # ------------------------------------------------------------- autograd

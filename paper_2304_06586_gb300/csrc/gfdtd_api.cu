@@ -94,6 +94,10 @@ struct gfdtd_ctx {
   int cur = 0;                          // buffer holding the current state
   DevBuf d_ndone;
   long long n_done = 0;
+  DevBuf d_watch;                       // watchdog: one word per instance (see watch_launch)
+  DevBuf d_watchblk;                    // the watchdog scan's blocks (WatchBlock)
+  int n_watchblk = 0;
+  int stall = 0;                        // test hook: fast-kernel tile copies are not started
 
   // device tables (rebuilt by finalize)
   bool dirty = true;
@@ -467,6 +471,21 @@ static gfdtd_status finalize(gfdtd_ctx* c) {
       (s = upload(c, c->d_binprb, binprb)) || (s = upload(c, c->d_acc_re, acc_re)) ||
       (s = upload(c, c->d_acc_im, acc_im)))
     return s;
+  if (c->n_watchblk == 0) {   // the watchdog scan's blocks depend on the grid sizes only
+    std::vector<WatchBlock> wb;
+    for (int i = 0; i < c->n_inst; ++i) {
+      const long long end = c->off[i] + (c->nz[i] + 31) / 32 * 32;
+      for (long long b = c->off[i]; b < end; b += kWatchCells) {
+        WatchBlock w{};
+        w.start = b;
+        w.end = std::min(end, b + kWatchCells);
+        w.inst = i;
+        wb.push_back(w);
+      }
+    }
+    if ((s = upload(c, c->d_watchblk, wb))) return s;
+    c->n_watchblk = (int)wb.size();
+  }
   if ((s = dalloc(c, c->d_amp, std::max<size_t>(16, (size_t)c->n_src * kChunk * sizeof(double)))) ||
       (s = dalloc(c, c->d_samples, std::max<size_t>(16, (size_t)c->n_prb * kChunk * sizeof(double)))))
     return s;
@@ -558,6 +577,7 @@ static gfdtd_status enqueue_block(gfdtd_ctx* c, cudaStream_t st, int from, int s
     a.s0 = s0;
     a.nsteps = nsteps;
     a.record = record ? 1 : 0;
+    a.stall = c->stall;
     if (k == 2 && c->n_fast_damped > 0) {
       // the tiles that reach an absorbing layer, at the end of the list, get their own launch
       const int nd = c->n_fast_damped, nn = c->n_tiles[2] - nd;
@@ -581,7 +601,14 @@ static gfdtd_status enqueue_block(gfdtd_ctx* c, cudaStream_t st, int from, int s
   return GFDTD_OK;
 }
 
-static gfdtd_status enqueue_fold_advance(gfdtd_ctx* c, cudaStream_t st, int nsteps) {
+// End of a chunk: fold the probes' samples into their DFTs, scan the state
+// (buffer state_buf) for the watchdog, advance the device step counter.
+static gfdtd_status enqueue_fold_advance(gfdtd_ctx* c, cudaStream_t st, int nsteps, int state_buf) {
+  if (c->n_watchblk > 0) {
+    CKI(c, watch_launch(c->prec, (const WatchBlock*)c->d_watchblk.p, c->n_watchblk, c->B[state_buf].p,
+                        c->D[state_buf].p, (unsigned*)c->d_watch.p, st));
+    ++c->launches;
+  }
   if (c->n_bins > 0) {
     FoldArgs f;
     f.prbs = (const PrbDev*)c->d_prbs.p;
@@ -630,7 +657,7 @@ static gfdtd_status enqueue_chunk(gfdtd_ctx* c, cudaStream_t st, int from, int n
     ++m;
   }
   *nlaunch = m;
-  return enqueue_fold_advance(c, st, nsteps);
+  return enqueue_fold_advance(c, st, nsteps, b);
 }
 
 static gfdtd_status run_chunk(gfdtd_ctx* c, int nsteps) {
@@ -655,7 +682,8 @@ static gfdtd_status run_chunk(gfdtd_ctx* c, int nsteps) {
   CK(c, cudaGraphLaunch(it->second, c->stream));
   const int kinds = (c->n_tiles[0] > 0) + (c->n_tiles[1] > 0) + (c->n_tiles[2] > c->n_fast_damped) +
                     (c->n_fast_damped > 0);
-  c->launches += (long long)m * kinds + (c->n_src > 0) + (c->n_tfsf > 0) + (c->n_bins > 0) + 1;
+  c->launches += (long long)m * kinds + (c->n_src > 0) + (c->n_tfsf > 0) + (c->n_bins > 0) +
+                 (c->n_watchblk > 0) + 1;
   if (m & 1) c->cur = 1 - c->cur;
   c->n_done += nsteps;
   return GFDTD_OK;
@@ -1049,7 +1077,9 @@ gfdtd_status gfdtd_create(gfdtd_ctx** out, int n_inst, const int64_t* nz, double
     if (!s && prec == GFDTD_F32_KAHAN) s = dalloc(c, c->cD[k], bytes);
   }
   if (!s) s = dalloc(c, c->d_ndone, 16);
+  if (!s) s = dalloc(c, c->d_watch, sizeof(unsigned) * (size_t)n_inst);
   if (!s) {
+    cudaMemsetAsync(c->d_watch.p, 0, sizeof(unsigned) * (size_t)n_inst, c->stream);
     for (int k = 0; k < 2; ++k) {
       cudaMemsetAsync(c->B[k].p, 0, bytes, c->stream);
       cudaMemsetAsync(c->D[k].p, 0, bytes, c->stream);
@@ -1321,7 +1351,7 @@ gfdtd_status gfdtd_profile_kernels(gfdtd_ctx* c, int64_t n_steps, gfdtd_kernel_t
       ++m;
     }
     if (s) break;
-    s = enqueue_fold_advance(c, c->stream, ch);
+    s = enqueue_fold_advance(c, c->stream, ch, b);
     if (s) break;
     if (m & 1) c->cur = 1 - c->cur;
     c->n_done += ch;
@@ -1378,7 +1408,7 @@ gfdtd_status gfdtd_step_plain(gfdtd_ctx* c, int64_t n_steps) {
       }
       c->cur = 1 - c->cur;
     }
-    s = enqueue_fold_advance(c, c->stream, ch);
+    s = enqueue_fold_advance(c, c->stream, ch, c->cur);
     if (s) return s;
     c->n_done += ch;
     n_steps -= ch;
@@ -1525,6 +1555,36 @@ gfdtd_status gfdtd_get_stats(const gfdtd_ctx* c, gfdtd_stats* out) {
   return GFDTD_OK;
 }
 
+gfdtd_status gfdtd_watchdog(gfdtd_ctx* c, double limit, int reset, int* flags, double* amax) {
+  if (!c) return GFDTD_E_ARG;
+  if (!(limit > 0.0)) return fail(c, GFDTD_E_ARG, "limit must be > 0");
+  std::vector<unsigned> w((size_t)c->n_inst);
+  CK(c, cudaMemcpyAsync(w.data(), c->d_watch.p, w.size() * sizeof(unsigned), cudaMemcpyDeviceToHost,
+                        c->stream));
+  CK(c, cudaStreamSynchronize(c->stream));
+  if (reset) CK(c, cudaMemsetAsync(c->d_watch.p, 0, w.size() * sizeof(unsigned), c->stream));
+  int flagged = 0;
+  for (int i = 0; i < c->n_inst; ++i) {
+    // bits of an FP32 magnitude: above 0x7f800000 a NaN was written, at it an infinity
+    const bool non_finite = w[i] >= 0x7f800000u;
+    float m;
+    const unsigned b = non_finite ? 0x7f800000u : w[i];
+    std::memcpy(&m, &b, sizeof(float));
+    const int f = (non_finite ? 1 : 0) | ((double)m > limit ? 2 : 0);
+    if (flags) flags[i] = f;
+    if (amax) amax[i] = (double)m;
+    flagged += f != 0;
+  }
+  return flagged ? fail(c, GFDTD_E_UNSTABLE, "%d instance(s) flagged by the watchdog", flagged) : GFDTD_OK;
+}
+
+gfdtd_status gfdtd_test_stall(gfdtd_ctx* c, int on) {
+  if (!c) return GFDTD_E_ARG;
+  c->stall = on ? 1 : 0;
+  drop_graphs(c);   // the flag is part of every captured launch
+  return GFDTD_OK;
+}
+
 gfdtd_status gfdtd_synchronize(gfdtd_ctx* c) {
   if (!c) return GFDTD_E_ARG;
   CK(c, cudaStreamSynchronize(c->stream));
@@ -1548,7 +1608,7 @@ void gfdtd_destroy(gfdtd_ctx* c) {
                     &c->d_wB[1][0], &c->d_wB[1][1], &c->d_amp2[0], &c->d_amp2[1], &c->d_lB[0],
                     &c->d_lB[1], &c->d_lD[0], &c->d_lD[1], &c->d_grad, &c->d_gn, &c->d_adjn[0], &c->d_adjn[1],
                     &c->d_Xre, &c->d_Xim, &c->d_bin0, &c->d_pnode, &c->d_acc0_re, &c->d_acc0_im,
-                    &c->d_adj_tiles, &c->d_tfsf, &c->d_tfaux, &c->d_tfcorr};
+                    &c->d_adj_tiles, &c->d_tfsf, &c->d_tfaux, &c->d_tfcorr, &c->d_watch, &c->d_watchblk};
   for (DevBuf* b : bufs) dfree(c, *b);
   if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
   delete c;

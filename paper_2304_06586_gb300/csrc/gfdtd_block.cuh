@@ -645,7 +645,11 @@ __device__ __forceinline__ void run_tile(const BlockArgs<T>& A, const InstDev& I
 
 // ------------------------------------------------ TMA bulk copies + mbarrier
 
-constexpr long long kWaitLimit = 1LL << 22;   // try_wait polls before a wait is declared failed
+// A bounded wait gives up after one second of device time (or kWaitLimit
+// polls, a backstop that does not depend on the timer), far beyond any real
+// tile copy.
+constexpr long long kWaitLimit = 1LL << 24;
+constexpr unsigned long long kWaitNs = 1000000000ull;
 constexpr int kErrTimeout = 1;
 
 __device__ __forceinline__ unsigned smem_u32(const void* p) {
@@ -682,10 +686,20 @@ __device__ __forceinline__ bool mbar_try_wait(unsigned long long* bar, unsigned 
       : "memory");
   return ok != 0;
 }
-// Wait for phase `phase` of `bar`, giving up after kWaitLimit polls.
+__device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+// Wait for phase `phase` of `bar`, giving up after kWaitNs of device time or
+// kWaitLimit polls.
 __device__ __forceinline__ bool mbar_wait_bounded(unsigned long long* bar, unsigned phase) {
-  for (long long it = 0; it < kWaitLimit; ++it)
+  if (mbar_try_wait(bar, phase)) return true;
+  const unsigned long long t0 = global_ns();
+  for (long long it = 1; it < kWaitLimit; ++it) {
     if (mbar_try_wait(bar, phase)) return true;
+    if ((it & 255) == 0 && global_ns() - t0 > kWaitNs) return false;
+  }
   return false;
 }
 
@@ -1055,10 +1069,19 @@ __device__ __forceinline__ void run_tile_fast(const BlockArgs<T>& A, const InstD
     A.track[t].lane[lane] = o;
     if (lane == 0) A.track[t].n = n0 + A.nsteps;
   }
-  // back to B: a division, not a multiplication by 1/sm, whose rounding would
-  // scale B by the same factor at every launch
+  // back to B.  A plain multiplication by the rounded 1/sm would scale B by
+  // the same factor sm fl(1/sm) = 1 - e at every launch; the residual e,
+  // exact in one FMA, corrects that (a division per cell would be exact too,
+  // but costs a quarter of the kernel's time on the crystal).
+  {
+    const R r = (R)1 / sm;
+    const R e = fma(-sm, r, (R)1);
 #pragma unroll
-  for (int c = 0; c < C; ++c) B[c] = B[c] / sm;
+    for (int c = 0; c < C; ++c) {
+      const R p = B[c] * r;
+      B[c] = fma(p, e, p);
+    }
+  }
   const int hi = min(x0 + W, I.nz_pad);
   store_cells<T, R, C>(A.Bout + I.off, k0, x0, hi, B);
   store_cells<T, R, C>(A.Dout + I.off, k0, x0, hi, D);
@@ -1134,6 +1157,7 @@ __global__ void __launch_bounds__(128, MB) fast_kernel(const BlockArgs<T> A) {
     if (lane == 0 && t < A.n_tiles) {
       fence_proxy_async();
       mbar_expect_tx(&sbar[wib], tx);
+      if (A.stall) return;   // test hook: no copy is started, so the wait for it runs out
       bulk_g2s(&sbuf[wib][0][0], A.Bin + fe, BYTES, &sbar[wib]);
       bulk_g2s(&sbuf[wib][1][0], A.Din + fe, BYTES, &sbar[wib]);
       bulk_g2s(&sinst[wib], A.inst + fi, sizeof(InstDev), &sbar[wib]);

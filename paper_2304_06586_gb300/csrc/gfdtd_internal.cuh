@@ -188,6 +188,8 @@ struct BlockArgs {
   const TfsfDev* tfsf;        // general kernel: one-way sources (instance i owns records
   int n_tfsf;                 //   tf0 .. tf0 + ntf - 1 of its InstDev; NULL or n_tfsf 0: none)
   const double* tf_corr;      // [source][step in chunk (chunk_stride)][kTfsfCorr] additive corrections
+  int stall;                  // fast kernel, test hook: arm each tile barrier but start no copy,
+                              //   so that every bounded wait runs out (0 in normal operation)
 };
 
 // Arguments of the plain kernel (one instance, one step).
@@ -289,6 +291,18 @@ int plain_launch(int prec, const void* args, int nz, cudaStream_t st);
 int src_amp_launch(const SrcDev* srcs, int nsrc, double* amp, int stride, int nsteps,
                    const long long* n_done, double S, cudaStream_t st);
 int fold_launch(const FoldArgs& a, cudaStream_t st);
+// Runtime stability watchdog: block j of the scan covers the state elements
+// [start, end) of instance inst (at most kWatchCells, 16-byte aligned).
+struct WatchBlock {
+  long long start, end;
+  int inst, pad;
+};
+constexpr int kWatchCells = 8192;
+// Merges, per instance, the largest |B| and |D| of the state (B, D in storage
+// precision prec) into watch[inst] as the bits of its FP32 magnitude (NaNs above
+// infinities above every finite value), by atomicMax.
+int watch_launch(int prec, const WatchBlock* blocks, int n_blocks, const void* B, const void* D,
+                 unsigned* watch, cudaStream_t st);
 int advance_launch(long long* n_done, long long by, cudaStream_t st);
 int convert_launch(int prec, int to_double, const void* src, void* dst, long long n, cudaStream_t st);
 int capture_launch(int prec, int which, const InstDev* inst, int i, Tables tb, const void* B, const void* D,

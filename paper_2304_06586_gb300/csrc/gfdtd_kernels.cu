@@ -213,6 +213,69 @@ int fold_launch(const FoldArgs& a, cudaStream_t st) {
   return (int)cudaGetLastError();
 }
 
+// ------------------------------------------------------------ watchdog
+//
+// The scheme is unstable where n|beta| > 1 (Sec. 5); an instance run there
+// grows until it overflows.  Once per chunk this scan reads the state (B, D) and
+// merges, per instance, the largest magnitude into one word: the bits of
+// |x| rounded to FP32, which order like the values and put infinities
+// (0x7f800000) and NaNs above every finite value, so one integer maximum also
+// records a non-finite value.  A separate pass, not a step inside the tile
+// kernels: it reads 2 values per cell once per chunk (under 1 % of the
+// batched kernel's traffic), where the same reduction inside the fast kernel's
+// tiles cost it 13 % on the crystal.
+constexpr int kWatchThreads = 256;
+
+template <typename T>
+__global__ void __launch_bounds__(kWatchThreads) watch_kernel(const WatchBlock* __restrict__ blocks,
+                                                              const T* __restrict__ B, const T* __restrict__ D,
+                                                              unsigned* __restrict__ watch) {
+  using R = typename Real<T>::type;
+  constexpr int V = 16 / sizeof(T);
+  const WatchBlock wb = blocks[blockIdx.x];
+  unsigned m = 0u;
+  for (long long e = wb.start + (long long)threadIdx.x * V; e < wb.end; e += (long long)kWatchThreads * V) {
+    R x[V];
+    unpack(__ldg(reinterpret_cast<const uint4*>(B + e)), x, T());
+#pragma unroll
+    for (int j = 0; j < V; ++j) m = max(m, __float_as_uint((float)x[j]) & 0x7fffffffu);
+    unpack(__ldg(reinterpret_cast<const uint4*>(D + e)), x, T());
+#pragma unroll
+    for (int j = 0; j < V; ++j) m = max(m, __float_as_uint((float)x[j]) & 0x7fffffffu);
+  }
+  m = __reduce_max_sync(FULL, m);
+  __shared__ unsigned sm[kWatchThreads / 32];
+  if ((threadIdx.x & 31) == 0) sm[threadIdx.x >> 5] = m;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int w = 1; w < kWatchThreads / 32; ++w) m = max(m, sm[w]);
+    if (m != 0u) atomicMax(watch + wb.inst, m);
+  }
+}
+
+int watch_launch(int prec, const WatchBlock* blocks, int n_blocks, const void* B, const void* D,
+                 unsigned* watch, cudaStream_t st) {
+  if (n_blocks == 0) return 0;
+  switch (prec) {
+    case 0: case 1:
+      watch_kernel<float><<<n_blocks, kWatchThreads, 0, st>>>(blocks, (const float*)B, (const float*)D, watch);
+      break;
+    case 2:
+      watch_kernel<__nv_bfloat16><<<n_blocks, kWatchThreads, 0, st>>>(blocks, (const __nv_bfloat16*)B,
+                                                                       (const __nv_bfloat16*)D, watch);
+      break;
+    case 3:
+      watch_kernel<__half><<<n_blocks, kWatchThreads, 0, st>>>(blocks, (const __half*)B, (const __half*)D, watch);
+      break;
+    case 4:
+      watch_kernel<double><<<n_blocks, kWatchThreads, 0, st>>>(blocks, (const double*)B, (const double*)D, watch);
+      break;
+    default:
+      return (int)cudaErrorInvalidValue;
+  }
+  return (int)cudaGetLastError();
+}
+
 __global__ void advance_kernel(long long* n_done, long long by) {
   if (threadIdx.x == 0 && blockIdx.x == 0) *n_done += by;
 }
