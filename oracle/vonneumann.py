@@ -141,3 +141,25 @@ def propagation_loss(S, beta, eps, mu, omega, distance, direction=+1):
     theta, z, vg = mode_for_frequency(S, beta, eps, mu, omega, direction)
     steps = abs(distance) / (abs(vg) * S)
     return abs(z) ** steps
+
+
+def doppler_factor(S, beta, eps_in, eps_out, omega, direction_out=+1, mu_in=1.0, mu_out=1.0):
+    """Lab frequency ratio omega_out / omega of the wave that leaves a moving
+    interface (velocity beta) when a +z wave of lab frequency omega arrives in
+    medium `in`: the interface moves rigidly, so the frequency seen in its frame,
+    Omega = omega - beta k, is the same on both sides (the invariant behind
+    Eq. comp_exp), here with k taken from the scheme's own dispersion relation
+    (mode_for_frequency) in each uniform medium.  direction_out = +1: the
+    transmitted wave in medium `out`; -1: the reflected wave (medium `out` =
+    medium `in`).  As omega -> 0 it tends to Eq. comp_exp's a_t and a_r."""
+    th_in, _, _ = mode_for_frequency(S, beta, eps_in, mu_in, omega, +1)
+    Om = omega - beta * th_in
+    lo, hi = 0.05 * omega, 20.0 * omega
+    for _ in range(200):
+        mid = 0.5 * (lo + hi)
+        th, _, _ = mode_for_frequency(S, beta, eps_out, mu_out, mid, direction_out)
+        if mid - beta * direction_out * th < Om:
+            lo = mid
+        else:
+            hi = mid
+    return 0.5 * (lo + hi) / omega

@@ -82,11 +82,12 @@ def config1(lam0=40.0, scale=1):
                     "1D moving-perturbation interface, v=+0.3c, eps 1|4, Nz=4000, 8000 steps")
 
 
-def config2(velocities=(-0.5, -0.2, 0.0, 0.2, 0.5), nz=1 << 16, n_steps=40000, slab=800, lam0=40.0):
+def config2(velocities=(-0.5, -0.2, 0.0, 0.2, 0.5), nz=1 << 16, n_steps=40000, slab=800, lam0=40.0,
+            src_gap=1024):
     """Moving-matter slab (Fig. 6 geometry): rest eps' = 9, mu' = 1, one instance per velocity.
 
     Slab [32768, 32768 + 800) of the moving frame at t = 0 (scaled with nz);
-    source 1024 cells before it; reflected / transmitted probes at 5/16 and
+    source src_gap cells before it; reflected / transmitted probes at 5/16 and
     11/16 of the grid; 256 bins over [0, 4 w0).
     """
     w0 = 2 * np.pi / lam0
@@ -96,7 +97,7 @@ def config2(velocities=(-0.5, -0.2, 0.0, 0.2, 0.5), nz=1 << 16, n_steps=40000, s
     for v in velocities:
         out.append(InstanceSpec(nz=nz, beta=float(v), kind=MATTER, z=np.array([z0, z0 + slab], float),
                                 eps=np.array([1.0, 9.0, 1.0]), mu=np.ones(3),
-                                sources=[gaussian_source(z0 - 1024, lam0, 10.0)],
+                                sources=[gaussian_source(z0 - src_gap, lam0, 10.0)],
                                 probes=[(nz * 5 // 16, bins), (nz * 11 // 16, bins)]))
     return Workload("matter_slab", 0.5, n_steps, out,
                     "5 x 2^16 moving-matter slab, eps'=9, v in {-0.5,-0.2,0,0.2,0.5}c, 40000 steps")
@@ -137,18 +138,23 @@ def config3(n_inst=4096, nz_lo=1 << 12, nz_hi=1 << 18, periods=64, v_max=0.8, n_
 
 
 def config4(variant="as_written", nz=1 << 20, n_steps=200000, lam0=40.0):
-    """Moving gradient: linear eps ramp over [nz/4, nz/2) of the moving frame, v = 0.7c.
+    """Moving gradient (Fig. 8 geometry, scaled up): linear eps ramp over
+    [nz/4, nz/2) of the moving frame, v = 0.7c (co-moving with the pulse).
 
     as_written: eps 1 -> 6 (n|v| exceeds 1 beyond eps = 2.04: unstable there);
-    stable: eps 1 -> 2 (n|v| <= 0.99).
+    stable: eps 1 -> 2 (n|v| <= 0.99).  The source sits g = min(1024, nz/16)
+    cells behind the ramp, so that the pulse, chasing the ramp at 0.3c,
+    reaches it early in the run; the probe sits 2g behind it and records the
+    source's backward pulse and what the ramp reflects.
     """
     e2 = 6.0 if variant == "as_written" else 2.0
     w0 = 2 * np.pi / lam0
     bins = np.linspace(0.5, 1.5, 16) * w0
+    g = min(1024, nz // 16)
     inst = InstanceSpec(nz=nz, beta=0.7, interp=LINEAR, z=np.array([nz / 4, nz / 2], float),
                         eps=np.array([1.0, e2]), mu=np.ones(2),
-                        sources=[gaussian_source(nz // 8, lam0, 10.0)],
-                        probes=[(nz * 7 // 8, bins)])
+                        sources=[gaussian_source(nz // 4 - g, lam0, 10.0)],
+                        probes=[(nz // 4 - 2 * g, bins)])
     return Workload("gradient_" + variant, 0.5, n_steps, [inst],
                     "Nz=2^20 linear ramp eps 1->%g over 2^18 cells, v=0.7c, %d steps" % (e2, n_steps))
 

@@ -1,12 +1,25 @@
-"""GPU results against the exact solutions the paper gives (App. B): the
-moving-interface reflection and transmission coefficients of Eq.
-coef_interface within 1 % at 150 cells per wavelength (Fig. 5 parameters),
-measured with a one-way source so that the scattered-field probe records the
-reflected pulse alone, and the Doppler factors of Eq. comp_exp."""
+"""GPU results against the exact solutions the paper gives (App. B).
+
+* The moving-interface workload as stated (v = +0.3c, eps 1 | 4, 40 cells per
+  carrier wavelength, soft source, FP64 and FP32): |Gamma| of Eq.
+  coef_interface within 1 %, the Doppler factors of Eq. comp_exp from the
+  spectral peaks, and |T| equal to the oracle's value on the same run (the
+  transmitted wave has 11.4 cells per wavelength there, where the scheme's own
+  error in |T| is 4 %: the convergence table below is the stated limit).
+* Convergence of |Gamma| and |T| with the mesh (20 to 150 cells per carrier
+  wavelength), GPU and oracle side by side.
+* Fig. 5 parameters with a one-way source at 150 cells per wavelength, and a
+  moving slab (Eq. coef_slab) at 40 to 300 cells per wavelength.
+* The moving-matter slab workload (n' = 3, 800 cells, v in +-0.5c): first-pass
+  reflection and transmission against the Lorentz transformation of the
+  rest-frame Fresnel coefficients, time-gated between the slab's echoes.
+"""
 import numpy as np
 import pytest
 
+from exactness import Interface
 from paper_2304_06586_gb300 import binding as gb
+from paper_2304_06586_gb300 import workloads as w
 
 pytestmark = pytest.mark.gpu
 
@@ -17,6 +30,58 @@ def _gpu():
     if not torch.cuda.is_available():
         pytest.skip("no GPU")
     gb.load()
+
+
+@pytest.fixture(scope="module")
+def interface_oracle():
+    """The oracle's coefficients on the stated moving-interface workload."""
+    return Interface(1.0).run_oracle()
+
+
+@pytest.mark.parametrize("prec", [gb.F64, gb.F32])
+def test_interface_workload_as_stated(prec, interface_oracle):
+    geo = Interface(1.0)
+    res = geo.run_gpu(prec)
+    orc = interface_oracle
+    print("interface as stated, prec %d: Gamma %s, T %s, a_r %.5f (Eq. comp_exp %.5f, scheme %.5f), "
+          "a_t %.5f (Eq. comp_exp %.5f, scheme %.5f)"
+          % (prec, np.round(res["Gamma"], 5), np.round(res["T"], 5), res["a_r"], geo.ex["a_r"],
+             res["a_r_scheme"], res["a_t"], geo.ex["a_t"], res["a_t_scheme"]))
+    assert np.all(np.abs(res["Gamma"]) < 0.01), res["Gamma"]
+    # the same run on both sides: GPU and oracle measure the same coefficients
+    tol = 1e-6 if prec == gb.F64 else 1e-4
+    for key in ("Gamma", "T"):
+        assert np.all(np.abs((1 + res[key]) / (1 + orc[key]) - 1) < tol), (key, res[key], orc[key])
+    # Doppler factors: the reflected peak at Eq. comp_exp's a_r; the transmitted one
+    # at the scheme's own factor (w - v k conserved with the scheme's k), within the
+    # shift that the frequency-dependent loss over the path gives the peak
+    assert abs(res["a_r"] / geo.ex["a_r"] - 1) < 1e-3, res["a_r"]
+    assert abs(res["a_t"] / res["a_t_scheme"] - 1) < 1e-2, (res["a_t"], res["a_t_scheme"])
+    assert abs(res["a_t"] / geo.ex["a_t"] - 1) < 0.04, res["a_t"]
+    # |T| at 11.4 cells per transmitted wavelength: the scheme's limit, 4 %
+    assert np.all(np.abs(res["T"]) < 0.05), res["T"]
+
+
+def test_interface_convergence_table():
+    """|Gamma| and |T| errors against Eq. coef_interface at 20, 40, 80 and 150
+    cells per carrier wavelength, GPU (FP32) and oracle side by side: |Gamma|
+    within 1 % at every mesh, |T| converging to within 1 % (the transmitted
+    wave has 1 / (2 a_t) of the carrier's cells per wavelength)."""
+    rows = []
+    for scale in (0.5, 1.0, 2.0, 3.75):
+        geo = Interface(scale)
+        g = geo.run_gpu(gb.F32)
+        o = geo.run_oracle()
+        rows.append((geo.lam0, g, o))
+        print("cells/lambda %5.1f (transmitted %5.1f): GPU Gamma %+.4f T %+.4f | oracle Gamma %+.4f T %+.4f"
+              % (geo.lam0, g["cells_per_transmitted_wavelength"], g["Gamma"][1], g["T"][1], o["Gamma"][1],
+                 o["T"][1]))
+        assert np.all(np.abs(g["Gamma"]) < 0.01)
+        for key in ("Gamma", "T"):
+            assert np.all(np.abs((1 + g[key]) / (1 + o[key]) - 1) < 1e-4), (scale, key, g[key], o[key])
+    errs = [abs(r[1]["T"][1]) for r in rows]
+    assert errs[1] > errs[2] > errs[3], errs
+    assert np.all(np.abs(rows[-1][1]["T"]) < 0.01), rows[-1][1]["T"]
 
 
 @pytest.mark.parametrize("prec", [gb.F32, gb.F32_KAHAN])
@@ -86,3 +151,150 @@ def test_moving_slab_transmission_on_gpu(beta):
     for j, f in enumerate(fs):
         Tex, _ = exact.slab_closed_form(e1, e2, beta, ell, f * w0)
         assert abs(T[j] / abs(Tex) - 1) < 0.01, (beta, f, T[j], abs(Tex))
+
+
+def _slab_T(lam0, beta, runner, prec=None):
+    """|T| of a moving slab (eps 1 | 4 | 1, 1.5 carrier wavelengths thick) over
+    0.9-1.1 w0: the transmitted spectrum over that of the same background
+    without the slab, one-way sources and absorbing layers (the geometry of
+    the 300-cell test below, scaled to lam0 cells per carrier wavelength)."""
+    from oracle import exact
+    s = lam0 / 300.0
+    e1, e2, S = 1.0, 4.0, 0.5
+    w0 = 2 * np.pi / lam0
+    tau = 6 * lam0 / (2 * np.sqrt(np.log(2)))
+    t0 = 4 * tau
+    q, z0, ell, zt, nz, steps = int(2400 * s), 7000.0 * s, 450.0 * s, int(17200 * s), int(20000 * s), int(80000 * s)
+    fs = np.array([0.9, 0.95, 1.0, 1.05, 1.1])
+    aw = max(64, int(64 * s))
+    media = (([z0, z0 + ell], [e1, e2, e1]), ([], [e1]))
+    if runner == "gpu":
+        sim = gb.Simulation([nz, nz], S, prec)
+        for k, (z, e) in enumerate(media):
+            sim.set_medium(k, gb.PERTURBATION, beta, gb.LAYERS, z, e, [1.0] * len(e))
+            sim.add_tfsf(k, q, w0, tau, t0)
+            sim.set_absorber(k, aw, 0.2)
+            sim.add_probe(k, zt, fs * w0)
+        sim.step(steps)
+        X = [sim.read_spectrum(k, 0, len(fs)) for k in (0, 1)]
+        sim.close()
+    else:
+        import oracle
+        insts = []
+        for z, e in media:
+            o = oracle.Instance(nz, S, beta, z=z, eps=e)
+            o.add_tfsf(q, w0, tau, t0)
+            o.set_absorber(aw, 0.2)
+            o.add_probe(zt, fs * w0)
+            insts.append(o)
+        oracle.run_many(insts, steps)
+        X = [o.spectrum(0) for o in insts]
+    T = np.abs(X[0]) / np.abs(X[1])
+    Tex = np.array([abs(exact.slab_closed_form(e1, e2, beta, ell, f * w0)[0]) for f in fs])
+    return T / Tex - 1
+
+
+@pytest.mark.parametrize("beta", [0.2, -0.2])
+def test_moving_slab_convergence_table(beta):
+    """|T| of the moving slab against Eq. coef_slab at 40, 80 and 150 cells
+    per carrier wavelength, GPU (FP32) and oracle side by side (the 300-cell
+    case is the test below).  The Fabry-Perot phase inside the slab amplifies
+    the scheme's phase error, so the slab needs finer cells than the interface
+    for the same accuracy."""
+    errs = []
+    for lam0 in (40.0, 80.0, 150.0):
+        g = _slab_T(lam0, beta, "gpu", gb.F32)
+        o = _slab_T(lam0, beta, "oracle")
+        print("slab beta %+.1f, cells/lambda %5.1f: GPU max |T| error %.4f, oracle %.4f"
+              % (beta, lam0, np.abs(g).max(), np.abs(o).max()))
+        assert np.all(np.abs((1 + g) / (1 + o) - 1) < 1e-4), (lam0, g, o)
+        errs.append(np.abs(o).max())
+    assert errs[0] > errs[1] > errs[2], errs
+
+
+def _gated_dft(series, t, lo, hi, omega):
+    m = (t >= lo) & (t < hi)
+    return np.array([np.sum(series[m] * np.exp(1j * om * t[m])) for om in np.atleast_1d(omega)])
+
+
+# measured bound per case: the reflected wave has lam0 (1 + v)/(1 - v) cells per
+# wavelength, so the contra-moving case needs the finest mesh (first order in the
+# mesh: -22 % at 13 cells per reflected wavelength, -2.8 % at 53, -0.7 % at 213)
+MATTER_BOUNDS = {(1, -0.5): 0.25, (1, -0.2): 0.04, (1, 0.0): 0.03, (1, 0.2): 0.02, (1, 0.5): 0.07,
+                 (4, -0.5): 0.035, (4, 0.5): 0.01, (16, -0.5): 0.01}
+
+
+@pytest.mark.parametrize("scale,beta", sorted(MATTER_BOUNDS))
+def test_matter_slab_first_pass_lorentz(scale, beta):
+    """The moving-matter slab workload (n' = 3, 800 cells, 2^16 cells, 40000
+    steps; scale 4 and 16: every length and the step count x4, x16): the
+    first reflection off the slab's front face, time-gated before the back
+    face's echo arrives, against the Lorentz transformation of the rest-frame
+    Fresnel coefficient (test oracle exact): |r1| = |(1 - n')/(1 + n')|
+    (1 - beta)/(1 + beta), at the Doppler-shifted frequency; and, at rest, the
+    first transmission |t1| = 1 - r'^2.  The reflected and incident pulses are
+    recorded 256 cells either side of the source (A - R: the slab run minus a
+    moving-vacuum run with the same source, so the source's direct pulses
+    cancel); the scheme's propagation loss in the moving vacuum over the short
+    paths to the meeting point is removed (Sec. 5), and the reflected frequency
+    is the scheme's own Doppler factor.  Inside moving matter the reading of
+    the scheme damps the forward wave at |zeta| = 0.9967 per step at v = 0.2c
+    (60 internal wavelengths: 2e-8 over the crossing), so the transmission is
+    checked at rest only."""
+    from oracle import exact
+    from oracle import vonneumann as vn
+    wl = w.config2(velocities=(beta,), nz=(1 << 16) * scale, n_steps=40000 * scale, slab=800 * scale,
+                   lam0=40.0 * scale, src_gap=1024 * scale)
+    I = wl.instances[0]
+    S, n_rest = wl.S, 3.0
+    src = I.sources[0]
+    node, w0, tau, t0 = src[0], src[1], src[2], src[3]
+    zr, zi, zt = node - 256 * scale, node + 256 * scale, I.probes[1][0]
+    ts = 2 * scale                              # steps between frames
+    frames = wl.n_steps // ts
+    runs = {}
+    for tag, (z, e) in (("A", (I.z, I.eps)), ("R", ([], [1.0]))):
+        for pair in ((zr, zi), (zt,)) if beta == 0.0 else ((zr, zi),):
+            sim = gb.Simulation([I.nz], S, gb.F32)
+            sim.set_medium(0, gb.MATTER, beta, gb.LAYERS, z, e, [1.0] * len(e))
+            sim.add_source(0, *src)
+            stride = pair[1] - pair[0] if len(pair) == 2 else 1
+            sim.set_capture(0, gb.FIELD_E, pair[0], pair[-1] + 1, stride, ts, max_frames=frames, half=False)
+            sim.step(wl.n_steps)
+            cap, dropped = sim.capture()
+            assert dropped == 0 and cap.shape == (frames, len(pair))
+            for j, zz in enumerate(pair):
+                runs[tag, zz] = cap[:, j]
+            sim.close()
+    t = (np.arange(1, frames + 1) * ts + 0.5) * S
+    z_front, L = I.z[0], I.z[1] - I.z[0]
+    t_meet = (z_front - node + t0) / (1 - beta)          # pulse centre meets the front face
+    zm = z_front + beta * t_meet
+    u_b = (-1 / n_rest + beta) / (1 - beta / n_rest)      # Fizeau speeds inside the slab
+    u_f = (1 / n_rest + beta) / (1 + beta / n_rest)
+    t_cross = L / (u_f - beta)
+    t_round = t_cross + L / (beta - u_b)                 # one internal round trip
+    a = (1 - beta) / (1 + beta)
+    half = 5 * tau
+    res = []
+    for f in (0.95, 1.0, 1.05):
+        om = f * w0
+        ar = vn.doppler_factor(S, beta, 1.0, 1.0, om, -1)
+        Xi = _gated_dft(runs["R", zi], t, 0, t[-1] + 1, om)[0]
+        tr = t_meet + (zm - zr)
+        Xr = _gated_dft(runs["A", zr] - runs["R", zr], t, tr - half / a, tr + min(half / a, 0.5 * t_round),
+                        ar * om)[0]
+        li = vn.propagation_loss(S, beta, 1.0, 1.0, om, zm - zi, +1)
+        lr = vn.propagation_loss(S, beta, 1.0, 1.0, ar * om, zm - zr, -1)
+        r1 = ar * abs(Xr) / abs(Xi) / (li * lr)
+        row = [r1 / abs(exact.matter_interface_reflection(n_rest, beta)) - 1]
+        if beta == 0.0:
+            tt = t_meet + t_cross + (zt - (zm + L))
+            Xt = _gated_dft(runs["A", zt], t, tt - half, tt + min(half, 0.5 * t_round), om)[0]
+            Xd = _gated_dft(runs["R", zt], t, 0, t[-1] + 1, om)[0]
+            row.append(abs(Xt) / abs(Xd) / (1 - ((1 - n_rest) / (1 + n_rest)) ** 2) - 1)
+        res.append(row)
+    res = np.array(res)
+    print("matter slab x%d beta %+.1f: first-pass |r1| error %s%s" % (
+        scale, beta, np.round(res[:, 0], 4), ", |t1| error %s" % np.round(res[:, 1], 4) if beta == 0.0 else ""))
+    assert np.all(np.abs(res) < MATTER_BOUNDS[scale, beta]), res
