@@ -217,7 +217,44 @@ def example_measurements(gb, torch):
     return out
 
 
-CASES = ["adjoint", "interface", "slab", "tfsf"] + ["gradient-" + t for t in ("F32", "F32_KAHAN", "BF16", "F16", "F64")]
+def gradient_as_written(gb, window=4000):
+    """The moving-gradient workload as written: linear eps ramp 1 -> 6 over 2^18
+    of 2^20 cells, v = 0.7c, 2 x 10^5 steps, FP32, from rest with its source.
+    Beyond eps = 1/0.49 the ramp has n|v| > 1, where the scheme is unstable
+    (Sec. 5); the watchdog's largest |B|, |D| over each `window` steps gives the
+    measured growth per step, compared with the von Neumann max|zeta| of the
+    ramp's densest medium (App. A).  The watchdog reads (one synchronisation
+    per window) are inside the timed run."""
+    from paper_2304_06586_gb300 import workloads as w
+    wl = w.config4("as_written")
+    T = wl.n_steps
+    sim = gb.Simulation([i.nz for i in wl.instances], wl.S, gb.F32)
+    configure(sim, wl, gb)
+    sim.step(256)
+    sim.watchdog(reset=True)
+    amax, first_flag = [], None
+    t0 = time.perf_counter()
+    for k in range(T // window):
+        sim.step(window)
+        flags, a = sim.watchdog(limit=1e30, reset=True)
+        amax.append(float(a[0]))
+        if flags[0] and first_flag is None:
+            first_flag = (k + 1) * window + 256
+    dt = time.perf_counter() - t0
+    sim.close()
+    rates = [(b / a) ** (1.0 / window) for a, b in zip(amax, amax[1:])
+             if 0 < a < float("inf") and 0 < b < float("inf")]
+    zeta = gb.stability(wl.S, 0.7, 6.0, 1.0, gb.PERTURBATION)
+    return {"value": wl.cells * (T // window) * window / dt / 1e9, "unit": "Gcell-updates/s",
+            "steps": (T // window) * window, "seconds": dt, "config": wl.description,
+            "growth_per_step_max": max(rates) if rates else None,
+            "growth_per_step_last": rates[-1] if rates else None,
+            "von_neumann_max_abs_zeta_eps6": zeta,
+            "flagged_at_step": first_flag, "largest_field_per_window": amax[::5]}
+
+
+CASES = ["adjoint", "interface", "slab", "tfsf", "gradient-written"] + \
+    ["gradient-" + t for t in ("F32", "F32_KAHAN", "BF16", "F16", "F64")]
 
 
 def run_case(args):
@@ -230,6 +267,9 @@ def run_case(args):
     from paper_2304_06586_gb300 import binding as gb
     from paper_2304_06586_gb300 import workloads as w
     T = args.time_steps
+    if args.case == "gradient-written":
+        print(json.dumps({"case": args.case, **gradient_as_written(gb)}), flush=True)
+        return
     if args.case == "adjoint":
         wl = w.config5(n_steps=T)
         sim = gb.Simulation([i.nz for i in wl.instances], wl.S, gb.F32)
@@ -647,6 +687,9 @@ def main():
         sweeps = None if args.no_sweeps else sweep_measurements(torch, gb, stream)
         adjoint = None if args.no_sweeps else adjoint_measurement(gb)
         examples = None if args.no_sweeps else example_measurements(gb, torch)
+        if examples is not None:
+            examples["gradient as written (eps 1->6, 2^20 cells, v=0.7c, 2e5 steps, FP32)"] = \
+                gradient_as_written(gb)
 
     if rank != 0:
         return
