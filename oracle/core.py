@@ -35,6 +35,22 @@ class _Probe(C.Structure):
                 ("omega", _dp), ("re", _dp), ("im", _dp), ("series", _dp)]
 
 
+class _Problem2(C.Structure):
+    _fields_ = [("nx", C.c_int64), ("nz", C.c_int64), ("dx", C.c_double), ("S", C.c_double),
+                ("beta", C.c_double), ("slope", C.c_double), ("n", C.c_int32), ("reserved", C.c_int32),
+                ("z", _dp), ("eps", _dp), ("mu", _dp)]
+
+
+class _Source2(C.Structure):
+    _fields_ = [("k", C.c_int64), ("kx", C.c_double), ("omega0", C.c_double), ("tau", C.c_double),
+                ("t0", C.c_double), ("amp", C.c_double)]
+
+
+class _Probe2(C.Structure):
+    _fields_ = [("i", C.c_int64), ("k", C.c_int64), ("n_bins", C.c_int32), ("reserved", C.c_int32),
+                ("omega", _dp), ("re", _dp), ("im", _dp)]
+
+
 class _Tfsf(C.Structure):
     _fields_ = [("node", C.c_int64), ("omega0", C.c_double), ("tau", C.c_double),
                 ("t0", C.c_double), ("amp", C.c_double), ("aux_B", _dp), ("aux_D", _dp)]
@@ -61,6 +77,9 @@ def lib():
         L.orc_sample_material.argtypes = [C.POINTER(_Problem), C.c_int, C.c_int, C.c_int64, _dp]
         L.orc_step_transpose.restype = C.c_int
         L.orc_step_transpose.argtypes = [C.POINTER(_Problem), C.c_int64, _dp, _dp, _dp, _dp, _dp, _dp]
+        L.orc2_run.restype = C.c_int
+        L.orc2_run.argtypes = [C.POINTER(_Problem2), C.c_int, C.POINTER(_Source2), C.c_int,
+                               C.POINTER(_Probe2), C.c_int64, C.c_int64, _dp, _dp, _dp]
         L.orc_adjoint.restype = C.c_int
         L.orc_adjoint.argtypes = [C.POINTER(_Problem), C.c_int, C.POINTER(_Source), C.POINTER(_Probe),
                                   C.c_int64, C.c_int64, _dp, _dp, _dp, _dp]
@@ -206,3 +225,54 @@ def run_many(instances, n_steps, threads=None, record=False):
     with ThreadPoolExecutor(max_workers=threads) as ex:
         list(ex.map(lambda inst: inst.run(n_steps, record=record), instances))
     return instances
+
+
+class Instance2D:
+    """The 2D TE generalized scheme (see the C file): nx columns (periodic in x,
+    width dx each), nz cells along the motion (zero fields beyond the ends),
+    moving-perturbation layers whose boundaries are the lines
+    z - beta t - slope x = z_b.  State: Bx, Bz, D as [nx, nz] FP64 arrays
+    (D at (i, k), Bx at (i, k + 1/2), Bz at (i + 1/2, k))."""
+
+    def __init__(self, nx, nz, S, beta, dx=1.0, z=(), eps=(1.0,), mu=None, slope=0.0):
+        self.nx, self.nz, self.S, self.beta, self.dx, self.slope = int(nx), int(nz), float(S), float(beta), \
+            float(dx), float(slope)
+        self.eps = _f64(eps)
+        self.mu = _f64(np.ones_like(self.eps) if mu is None else mu)
+        assert len(z) == len(self.eps) - 1
+        self.z = _f64(z) if len(z) else np.zeros(1)
+        self.Bx = np.zeros((self.nx, self.nz))
+        self.Bz = np.zeros((self.nx, self.nz))
+        self.D = np.zeros((self.nx, self.nz))
+        self.n_done = 0
+        self.sources = []
+        self.probes = []
+
+    def add_source(self, k, kx, omega0, tau, t0, amp=1.0):
+        self.sources.append((int(k), float(kx), float(omega0), float(tau), float(t0), float(amp)))
+
+    def add_probe(self, i, k, omega):
+        omega = _f64(omega)
+        self.probes.append({"i": int(i), "k": int(k), "omega": omega,
+                            "re": np.zeros(len(omega)), "im": np.zeros(len(omega))})
+        return len(self.probes) - 1
+
+    def run(self, n_steps):
+        prob = _Problem2(self.nx, self.nz, self.dx, self.S, self.beta, self.slope, len(self.eps), 0,
+                         _ptr(self.z), _ptr(self.eps), _ptr(self.mu))
+        srcs = (_Source2 * max(1, len(self.sources)))(*[_Source2(*s) for s in self.sources])
+        prbs = (_Probe2 * max(1, len(self.probes)))(*[
+            _Probe2(p["i"], p["k"], len(p["omega"]), 0, _ptr(p["omega"]), _ptr(p["re"]), _ptr(p["im"]))
+            for p in self.probes])
+        for a in (self.Bx, self.Bz, self.D):
+            assert a.flags["C_CONTIGUOUS"] and a.dtype == np.float64
+        rc = lib().orc2_run(C.byref(prob), len(self.sources), srcs, len(self.probes), prbs, self.n_done,
+                            int(n_steps), _ptr(self.Bx), _ptr(self.Bz), _ptr(self.D))
+        if rc != 0:
+            raise ValueError("oracle rejected the 2D problem")
+        self.n_done += int(n_steps)
+        return self
+
+    def spectrum(self, probe_id):
+        p = self.probes[probe_id]
+        return p["re"] + 1j * p["im"]

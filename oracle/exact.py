@@ -118,3 +118,73 @@ def fizeau_velocity(n_rest, beta, forward=True):
     """Lab-frame phase velocity in matter moving at beta (relativistic velocity addition)."""
     u = 1.0 / n_rest if forward else -1.0 / n_rest
     return (u + beta) / (1 + u * beta)
+
+
+def oblique_interface(eps1, eps2, beta, kx, omega, mu1=1.0, mu2=1.0):
+    """TE (E along y) plane wave of lab frequency omega and transverse
+    wavenumber kx arriving from medium 1 on a moving-perturbation interface
+    z = z0 + beta t (normal along the motion, oblique incidence).  Derived
+    from Eq. cont and Eq. star: in each uniform medium the wave is an ordinary
+    plane wave (kx^2 + kz^2 = omega^2 n^2, B = k x E / omega), all waves share kx
+    and the frequency seen by the interface, Omega = omega - beta kz, and the
+    tangential star fields E*_y = E_y (1 - beta kz/omega) and
+    H*_x = E_y (-kz/(omega mu) + beta eps) are continuous.  Returns
+    (Gamma, T, omega_r, omega_t, domega_r/domega): reflection and transmission
+    as ratios of E_y amplitudes, the reflected and transmitted lab frequencies
+    and the slope of omega_r(omega) at fixed kx (the spectral compression of
+    the reflected pulse).  kx = 0 gives Eq. coef_interface and Eq. comp_exp;
+    beta = 0 the TE Fresnel coefficients."""
+    n1, n2 = np.sqrt(eps1 * mu1), np.sqrt(eps2 * mu2)
+
+    def kz(w, n, sign):
+        return sign * np.sqrt(w * w * n * n - kx * kx + 0j)
+
+    kz1 = kz(omega, n1, 1).real
+    Om = omega - beta * kz1
+
+    def leaving(n, sign):
+        # omega_out - beta kz_out = Om with kz_out = sign sqrt(omega_out^2 n^2 - kx^2)
+        a = 1 - beta * beta * n * n
+        b = -2 * Om
+        c = Om * Om + beta * beta * kx * kx
+        disc = np.sqrt(b * b - 4 * a * c)
+        for w in ((-b - disc) / (2 * a), (-b + disc) / (2 * a)):
+            if w > 0 and w * n >= abs(kx):
+                k = kz(w, n, sign).real
+                if abs(w - beta * k - Om) < 1e-9 * abs(Om):
+                    return w, k
+        raise ValueError("no propagating wave leaves the interface")
+
+    wr, kzr = leaving(n1, -1)
+    wt, kzt = leaving(n2, +1)
+
+    def star(w, k, eps, mu):
+        return 1 - beta * k / w, -k / (w * mu) + beta * eps
+
+    ei, hi = star(omega, kz1, eps1, mu1)
+    er, hr = star(wr, kzr, eps1, mu1)
+    et, ht = star(wt, kzt, eps2, mu2)
+    M = np.array([[er, -et], [hr, -ht]])
+    G, T = np.linalg.solve(M, -np.array([ei, hi]))
+    dw = 1e-7 * omega
+    wr_p = oblique_interface_frequency(eps1, beta, kx, omega + dw, mu1)
+    wr_m = oblique_interface_frequency(eps1, beta, kx, omega - dw, mu1)
+    return G, T, wr, wt, (wr_p - wr_m) / (2 * dw)
+
+
+def oblique_interface_frequency(eps1, beta, kx, omega, mu1=1.0):
+    """Lab frequency of the wave reflected by the moving interface (see
+    oblique_interface): omega_r - beta kz_r = omega - beta kz_i, kz_r < 0."""
+    n1 = np.sqrt(eps1 * mu1)
+    kz1 = np.sqrt(omega * omega * n1 * n1 - kx * kx)
+    Om = omega - beta * kz1
+    a = 1 - beta * beta * n1 * n1
+    b = -2 * Om
+    c = Om * Om + beta * beta * kx * kx
+    disc = np.sqrt(b * b - 4 * a * c)
+    for w in ((-b - disc) / (2 * a), (-b + disc) / (2 * a)):
+        if w > 0 and w * n1 >= abs(kx):
+            k = -np.sqrt(w * w * n1 * n1 - kx * kx)
+            if abs(w - beta * k - Om) < 1e-9 * abs(Om):
+                return w
+    raise ValueError("no reflected wave")

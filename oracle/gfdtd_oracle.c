@@ -592,3 +592,150 @@ int orc_adjoint(const orc_problem* p, int n_src, const orc_source* src, const or
     free(aB); free(aD); free(aB0); free(aD0); free(geps);
     return 0;
 }
+
+/* ---- 2D TE generalized scheme (test infrastructure) ----------------------
+ *
+ * Sec. 3 and Sec. 4 before the 1D reduction, for moving perturbation in the
+ * x-z plane (d/dy = 0), motion along z, the TE polarisation E = E_y y^,
+ * B = (B_x, 0, B_z), D = D_y y^, H = (H_x, 0, H_z):
+ *   Eq. star:        E*_y = E_y + v B_x,   H*_x = H_x + v D_y,   H*_z = H_z
+ *                    (v x B = v B_x y^,  v x D = -v D_y x^)
+ *   Eq. const_3d:    D_y = eps (E*_y - v B_x),  B_x = mu (H*_x - v D_y),
+ *                    B_z = mu H*_z
+ *   Eq. Maxwell_star with curl(v x B) = -v dB/dz (v uniform, div B = 0) and
+ *   curl(v x D) = -v dD/dz (div D = 0):
+ *     dB_x/dt =  dE*_y/dz - v dB_x/dz
+ *     dB_z/dt = -dE*_y/dx - v dB_z/dz
+ *     dD_y/dt =  dH*_x/dz - dH*_z/dx - v dD_y/dz
+ * Along z the terms are discretized exactly as the 1D scheme (Table 1: the
+ * average of B_x in E*_y, the average of D_y in H*_x, the upwind differences
+ * of every component); along x they are the standard Yee differences.  With
+ * b = -B_x the z-part is the 1D update of Eqs. Farad_discr .. Bconst_discr.
+ *
+ * Grid (dz = 1, dx given, S = dt/dz, Sx = dt/dx): D_y at (i, k), B_x at
+ * (i, k+1/2), B_z at (i+1/2, k); arrays [i * nz + k].  Periodic in x (nx
+ * columns), every field zero outside [0, nz) in z.  Medium: layers of the
+ * moving coordinate xi = z - v t - slope x (boundary b at xi = z_b, slanted
+ * when slope != 0), evaluated exactly in 32.32 fixed point: a node at (x, z)
+ * at half level h has xi = z 2^32 - dq h - round(x slope 2^32), dq as in 1D.
+ * Soft line source: D_y(i, ks) += amp s(t) cos(kx i dx), s as in 1D.
+ * Probes: E_y = D_y / eps at node (i, k), running DFT as in 1D.
+ */
+typedef struct {
+    int64_t nx, nz;
+    double dx, S, beta, slope;
+    int32_t n, reserved;
+    const double* z;      /* n-1 boundaries (moving frame, t = 0, at x = 0) */
+    const double* eps;
+    const double* mu;
+} orc2_problem;
+
+typedef struct {
+    int64_t k;            /* z node of the line source */
+    double kx;            /* transverse wavenumber of its cos(kx x) weight */
+    double omega0, tau, t0, amp;
+} orc2_source;
+
+typedef struct {
+    int64_t i, k;
+    int32_t n_bins, reserved;
+    const double* omega;
+    double* re;
+    double* im;
+} orc2_probe;
+
+static double orc2_material(const orc2_problem* p, const int64_t* zq, const double* val,
+                            double x, int64_t zpos, int64_t dq, int64_t h)
+{
+    const int64_t xi = zpos - dq * h - llround(ldexp(x * p->slope, 32));
+    int i = last_at_or_below(zq, p->n - 1, xi) + 1;
+    return val[i];
+}
+
+static double at2(const double* a, int64_t nx, int64_t nz, int64_t i, int64_t k)
+{
+    if (k < 0 || k >= nz) return 0.0;
+    i = ((i % nx) + nx) % nx;
+    return a[i * nz + k];
+}
+
+int orc2_run(const orc2_problem* p, int n_src, const orc2_source* src, int n_probe, orc2_probe* probes,
+             int64_t n_done, int64_t n_steps, double* Bx, double* Bz, double* D)
+{
+    const int64_t nx = p->nx, nz = p->nz, N = nx * nz;
+    const double beta = p->beta, S = p->S, Sx = p->S / p->dx;
+    const int pos = beta >= 0.0;
+    if (nx < 1 || nz < 1 || p->n < 1 || !(p->dx > 0.0)) return -1;
+    int64_t* zq = (int64_t*)malloc(sizeof(int64_t) * (size_t)(p->n > 1 ? p->n - 1 : 1));
+    for (int i = 0; i + 1 < p->n; ++i) zq[i] = to_fixed(p->z[i]);
+    const int64_t dq = llround(ldexp(beta * S, 31));
+    double* Es = (double*)malloc(sizeof(double) * (size_t)N);
+    double* Hx = (double*)malloc(sizeof(double) * (size_t)N);
+    double* Hz = (double*)malloc(sizeof(double) * (size_t)N);
+    double* Bxo = (double*)malloc(sizeof(double) * (size_t)N);
+    double* Bzo = (double*)malloc(sizeof(double) * (size_t)N);
+    double* Do = (double*)malloc(sizeof(double) * (size_t)N);
+    for (int64_t s = 0; s < n_steps; ++s) {
+        const int64_t n = n_done + s + 1;
+        memcpy(Bxo, Bx, sizeof(double) * (size_t)N);
+        memcpy(Bzo, Bz, sizeof(double) * (size_t)N);
+        memcpy(Do, D, sizeof(double) * (size_t)N);
+        /* E*_y^{n-1/2} = D/eps + v Bbar_x (Table 1 Ba/Bb along z, B_x at level n-1) */
+        for (int64_t i = 0; i < nx; ++i)
+            for (int64_t k = 0; k < nz; ++k) {
+                const double e = orc2_material(p, zq, p->eps, (double)i * p->dx, node_pos(k), dq, 2 * n - 1);
+                const double bbar = pos ? 0.5 * (at2(Bxo, nx, nz, i, k - 1) + at2(Bxo, nx, nz, i, k - 2))
+                                        : 0.5 * (at2(Bxo, nx, nz, i, k + 1) + at2(Bxo, nx, nz, i, k));
+                Es[i * nz + k] = Do[i * nz + k] / e + beta * bbar;
+            }
+        /* B_x^n, B_z^n */
+        for (int64_t i = 0; i < nx; ++i)
+            for (int64_t k = 0; k < nz; ++k) {
+                const int64_t c = i * nz + k;
+                const double dbx = pos ? Bxo[c] - at2(Bxo, nx, nz, i, k - 1) : at2(Bxo, nx, nz, i, k + 1) - Bxo[c];
+                Bx[c] = Bxo[c] + S * (at2(Es, nx, nz, i, k + 1) - Es[c]) - beta * S * dbx;
+                const double dbz = pos ? Bzo[c] - at2(Bzo, nx, nz, i, k - 1) : at2(Bzo, nx, nz, i, k + 1) - Bzo[c];
+                Bz[c] = Bzo[c] - Sx * (at2(Es, nx, nz, i + 1, k) - Es[c]) - beta * S * dbz;
+            }
+        /* H*_x^n = B_x/mu + v Dbar (Table 1 Da/Db, D at level n-1/2); H*_z^n = B_z/mu */
+        for (int64_t i = 0; i < nx; ++i)
+            for (int64_t k = 0; k < nz; ++k) {
+                const int64_t c = i * nz + k;
+                const double mx = orc2_material(p, zq, p->mu, (double)i * p->dx, half_pos(k), dq, 2 * n);
+                const double mz = orc2_material(p, zq, p->mu, ((double)i + 0.5) * p->dx, node_pos(k), dq, 2 * n);
+                const double dbar = 0.5 * (Do[c] + at2(Do, nx, nz, i, k + 1));
+                Hx[c] = Bx[c] / mx + beta * dbar;
+                Hz[c] = Bz[c] / mz;
+            }
+        /* D_y^{n+1/2} */
+        for (int64_t i = 0; i < nx; ++i)
+            for (int64_t k = 0; k < nz; ++k) {
+                const int64_t c = i * nz + k;
+                const double dd = pos ? Do[c] - at2(Do, nx, nz, i, k - 1) : at2(Do, nx, nz, i, k + 1) - Do[c];
+                D[c] = Do[c] + S * (Hx[c] - at2(Hx, nx, nz, i, k - 1)) - Sx * (Hz[c] - at2(Hz, nx, nz, i - 1, k))
+                       - beta * S * dd;
+            }
+        /* line sources at t_{n+1/2} */
+        const double t = (double)(2 * n + 1) * S * 0.5;
+        for (int q = 0; q < n_src; ++q) {
+            if (src[q].k < 0 || src[q].k >= nz) continue;
+            const double u = t - src[q].t0;
+            const double sv = src[q].amp * sin(src[q].omega0 * u) * exp(-(u / src[q].tau) * (u / src[q].tau));
+            for (int64_t i = 0; i < nx; ++i) D[i * nz + src[q].k] += sv * cos(src[q].kx * (double)i * p->dx);
+        }
+        /* probes: E_y = D_y / eps at level n+1/2 */
+        for (int q = 0; q < n_probe; ++q) {
+            const int64_t i = probes[q].i, k = probes[q].k;
+            if (i < 0 || i >= nx || k < 0 || k >= nz) continue;
+            const double e = orc2_material(p, zq, p->eps, (double)i * p->dx, node_pos(k), dq, 2 * n + 1);
+            const double F = D[i * nz + k] / e;
+            for (int f = 0; f < probes[q].n_bins; ++f) {
+                const double w = probes[q].omega[f];
+                probes[q].re[f] += F * cos(w * t) * S;
+                probes[q].im[f] += F * sin(w * t) * S;
+            }
+        }
+    }
+    free(zq); free(Es); free(Hx); free(Hz); free(Bxo); free(Bzo); free(Do);
+    return 0;
+}
