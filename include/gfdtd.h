@@ -410,6 +410,77 @@ gfdtd_status gfdtd_step_noalloc(int64_t nz, double S, gfdtd_kind kind, double be
                                 const double* mu_r, float* B, float* D, int64_t n_done,
                                 int64_t n_steps, void* cuda_stream);
 
+/* ---- 2D TE generalized scheme (oblique incidence, slanted moving layers) ----
+ *
+ * Sec. 3 and Sec. 4 before their 1D reduction, for moving perturbation in the
+ * x-z plane (d/dy = 0, motion along z, E = E_y y^, B = (B_x, 0, B_z),
+ * D = D_y y^).  Eq. star and Eq. const_3d give E*_y = D_y/eps + v B_x,
+ * H*_x = B_x/mu + v D_y, H*_z = B_z/mu (E*_y is tangential to every boundary
+ * in the x-z plane, Eq. EHstar_comp), and Eq. Maxwell_star, with
+ * curl(v x F) = -v dF/dz for a uniform velocity and divergence-free F, gives
+ *     dB_x/dt = dE*_y/dz - v dB_x/dz,   dB_z/dt = -dE*_y/dx - v dB_z/dz,
+ *     dD_y/dt = dH*_x/dz - dH*_z/dx - v dD_y/dz.
+ * Along z these are discretized exactly as the 1D scheme (Table 1 averages in
+ * E*_y and H*_x, upwind differences of every component; with b = -B_x the
+ * z-part is the 1D update), along x with plain Yee differences.  Grid: D_y at
+ * (i, k), B_x at (i, k + 1/2), B_z at (i + 1/2, k); x spacing dx in units of
+ * the z cell, S = dt/dz; periodic over the nx columns, every field zero
+ * beyond the z ends.  The medium is moving-perturbation layers of the moving
+ * coordinate xi = z - beta t - slope x (boundary j at xi = z_j; slope != 0:
+ * boundaries slanted against the motion, n not parallel to v), sampled per
+ * node exactly in 32.32 fixed point: xi = z 2^32 - round(beta S 2^31) h -
+ * round(x slope 2^32) at half level h.  Fields are stored [i][k] (nx rows of
+ * nz values) in FP32 or FP64.  The GPU holds all nx <= 32 columns of a
+ * z-tile in one block (one warp per column). */
+typedef struct gfdtd2d_ctx gfdtd2d_ctx;
+
+/* Create a 2D context: 1 <= nx <= 32 columns, 1 <= nz <= 2^26 cells along z,
+ * dx > 0, S in (0, 1] with S^2 (1 + 1/dx^2) <= 1 (the 2D Yee limit in vacuum),
+ * prec F32 or F64 (E_UNSUPPORTED otherwise), on cuda_stream.  Vacuum at rest,
+ * fields zero.  Device memory from cudaMalloc. */
+gfdtd_status gfdtd2d_create(gfdtd2d_ctx** out, int nx, int64_t nz, double dx, double S, gfdtd_prec prec,
+                            void* cuda_stream);
+
+/* Moving layers: velocity beta (|beta| S < 1), slope of the boundaries, n >= 1
+ * layers with values eps_r[], mu_r[] > 0 and n - 1 increasing boundaries z[]
+ * (moving frame at t = 0, at x = 0).  E_UNSTABLE when a layer has n|beta| > 1
+ * (the 1D von Neumann limit of the scheme, Sec. 5) unless allow_unstable. */
+gfdtd_status gfdtd2d_set_medium(gfdtd2d_ctx* ctx, double beta, double slope, int n, const double* z,
+                                const double* eps_r, const double* mu_r, int allow_unstable);
+
+/* Soft line source at z node k: after the D update of step n,
+ * D_y(i, k) += amp sin(omega0 (t - t0)) exp(-((t - t0)/tau)^2) cos(kx i dx),
+ * t = (n + 1/2) S (Eq. spectrum_incident with a transverse wavenumber kx:
+ * waves at the angles +-asin(kx / (n omega))). */
+gfdtd_status gfdtd2d_add_source(gfdtd2d_ctx* ctx, int64_t k, double kx, double omega0, double tau, double t0,
+                                double amp);
+
+/* DFT probe of E_y = D_y / eps at node (i, k): every step adds
+ * E_y exp(+i omega t) S to each of its n_bins bins (FP64), t = (n + 1/2) S. */
+gfdtd_status gfdtd2d_add_probe(gfdtd2d_ctx* ctx, int i, int64_t k, int n_bins, const double* omega,
+                               int* probe_id);
+
+/* Tile shape: cells per lane along z and steps per time block; built: FP32
+ * 8x8 and 8x16 (the default), FP64 8x8 (the default); E_UNSUPPORTED
+ * otherwise. */
+gfdtd_status gfdtd2d_set_tuning(gfdtd2d_ctx* ctx, int cells_per_lane, int time_block);
+
+/* Advance n_steps >= 0 steps (asynchronous on the stream). */
+gfdtd_status gfdtd2d_step(gfdtd2d_ctx* ctx, int64_t n_steps);
+
+/* Copy field which (0: D_y, 1: B_x, 2: B_z) to / from host_dst[i * nz + k]
+ * as doubles, n == nx * nz (written fields rounded to the storage precision).
+ * Both synchronise the stream. */
+gfdtd_status gfdtd2d_read_fields(gfdtd2d_ctx* ctx, int which, double* host_dst, int64_t n);
+gfdtd_status gfdtd2d_write_fields(gfdtd2d_ctx* ctx, int which, const double* host_src, int64_t n);
+
+/* FP64 DFT accumulators of probe probe_id; synchronises the stream. */
+gfdtd_status gfdtd2d_read_spectrum(gfdtd2d_ctx* ctx, int probe_id, double* re, double* im);
+
+gfdtd_status gfdtd2d_synchronize(gfdtd2d_ctx* ctx);
+const char* gfdtd2d_last_error(const gfdtd2d_ctx* ctx);
+void gfdtd2d_destroy(gfdtd2d_ctx* ctx);
+
 /* Release the context and all its device memory.  NULL is ignored. */
 void gfdtd_destroy(gfdtd_ctx* ctx);
 

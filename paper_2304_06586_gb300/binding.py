@@ -81,6 +81,20 @@ SIGNATURES = {
     "gfdtd_synchronize": (C.c_int, [C.c_void_p]),
     "gfdtd_watchdog": (C.c_int, [C.c_void_p, C.c_double, C.c_int, C.POINTER(C.c_int), _dp]),
     "gfdtd_test_stall": (C.c_int, [C.c_void_p, C.c_int]),
+    "gfdtd2d_create": (C.c_int, [C.POINTER(C.c_void_p), C.c_int, C.c_int64, C.c_double, C.c_double, C.c_int,
+                                 C.c_void_p]),
+    "gfdtd2d_set_medium": (C.c_int, [C.c_void_p, C.c_double, C.c_double, C.c_int, _dp, _dp, _dp, C.c_int]),
+    "gfdtd2d_add_source": (C.c_int, [C.c_void_p, C.c_int64, C.c_double, C.c_double, C.c_double, C.c_double,
+                                     C.c_double]),
+    "gfdtd2d_add_probe": (C.c_int, [C.c_void_p, C.c_int, C.c_int64, C.c_int, _dp, C.POINTER(C.c_int)]),
+    "gfdtd2d_set_tuning": (C.c_int, [C.c_void_p, C.c_int, C.c_int]),
+    "gfdtd2d_step": (C.c_int, [C.c_void_p, C.c_int64]),
+    "gfdtd2d_read_fields": (C.c_int, [C.c_void_p, C.c_int, _dp, C.c_int64]),
+    "gfdtd2d_write_fields": (C.c_int, [C.c_void_p, C.c_int, _dp, C.c_int64]),
+    "gfdtd2d_read_spectrum": (C.c_int, [C.c_void_p, C.c_int, _dp, _dp]),
+    "gfdtd2d_synchronize": (C.c_int, [C.c_void_p]),
+    "gfdtd2d_last_error": (C.c_char_p, [C.c_void_p]),
+    "gfdtd2d_destroy": (None, [C.c_void_p]),
     "gfdtd_last_error": (C.c_char_p, [C.c_void_p]),
     "gfdtd_destroy": (None, [C.c_void_p]),
     "gfdtd_step_noalloc": (C.c_int, [C.c_int64, C.c_double, C.c_int, C.c_double, C.c_int, C.c_int, _dp,
@@ -399,6 +413,86 @@ class Simulation:
     def test_stall(self, on):
         """gfdtd_test_stall: make the fast kernel's bounded waits run out (test hook)."""
         self._check(self._L.gfdtd_test_stall(self._h, int(bool(on))), "test_stall")
+
+
+# ------------------------------------------------------------- 2D TE
+
+FIELD2D_D, FIELD2D_BX, FIELD2D_BZ = 0, 1, 2
+
+
+class Simulation2D:
+    """A gfdtd2d_ctx: the 2D TE generalized scheme on nx periodic columns (width
+    dx) of nz cells along the motion, on the current CUDA device.  Fields are
+    [nx, nz] arrays: D_y at (i, k), B_x at (i, k + 1/2), B_z at (i + 1/2, k)."""
+
+    def __init__(self, nx, nz, dx, S, prec=F32, stream=None):
+        L = load()
+        self._L = L
+        self.nx, self.nz, self.dx, self.S, self.prec = int(nx), int(nz), float(dx), float(S), prec
+        if stream is None:
+            import torch
+            stream = torch.cuda.current_stream().cuda_stream
+        h = C.c_void_p()
+        rc = L.gfdtd2d_create(C.byref(h), self.nx, self.nz, self.dx, self.S, prec, C.c_void_p(stream))
+        if rc != OK:
+            raise GfdtdError(rc, "gfdtd2d_create")
+        self._h = h
+
+    def _check(self, rc, what):
+        if rc != OK:
+            raise GfdtdError(rc, "%s: %s" % (what, self._L.gfdtd2d_last_error(self._h).decode()))
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._L.gfdtd2d_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_medium(self, beta=0.0, slope=0.0, z=(), eps=(1.0,), mu=None, allow_unstable=False):
+        eps = _f64(eps)
+        mu = _f64(np.ones_like(eps) if mu is None else mu)
+        z = _f64(z) if len(z) else np.zeros(1)
+        self._check(self._L.gfdtd2d_set_medium(self._h, float(beta), float(slope), len(eps), _ptr(z), _ptr(eps),
+                                               _ptr(mu), int(bool(allow_unstable))), "set_medium")
+
+    def add_source(self, k, kx, omega0, tau, t0, amp=1.0):
+        self._check(self._L.gfdtd2d_add_source(self._h, int(k), float(kx), float(omega0), float(tau), float(t0),
+                                               float(amp)), "add_source")
+
+    def add_probe(self, i, k, omega):
+        omega = _f64(np.atleast_1d(omega))
+        pid = C.c_int()
+        self._check(self._L.gfdtd2d_add_probe(self._h, int(i), int(k), len(omega), _ptr(omega), C.byref(pid)),
+                    "add_probe")
+        return pid.value
+
+    def set_tuning(self, cells_per_lane, time_block):
+        self._check(self._L.gfdtd2d_set_tuning(self._h, int(cells_per_lane), int(time_block)), "set_tuning")
+
+    def step(self, n):
+        self._check(self._L.gfdtd2d_step(self._h, int(n)), "step")
+
+    def read_fields(self, which=FIELD2D_D):
+        out = np.empty(self.nx * self.nz)
+        self._check(self._L.gfdtd2d_read_fields(self._h, int(which), _ptr(out), len(out)), "read_fields")
+        return out.reshape(self.nx, self.nz)
+
+    def write_fields(self, which, values):
+        v = _f64(np.asarray(values).reshape(-1))
+        self._check(self._L.gfdtd2d_write_fields(self._h, int(which), _ptr(v), len(v)), "write_fields")
+
+    def read_spectrum(self, probe_id, n_bins):
+        re, im = np.zeros(n_bins), np.zeros(n_bins)
+        self._check(self._L.gfdtd2d_read_spectrum(self._h, int(probe_id), _ptr(re), _ptr(im)), "read_spectrum")
+        return re + 1j * im
+
+    def synchronize(self):
+        self._check(self._L.gfdtd2d_synchronize(self._h), "synchronize")
 
 
 # ------------------------------------------------------------- autograd
