@@ -253,7 +253,51 @@ def gradient_as_written(gb, window=4000):
             "flagged_at_step": first_flag, "largest_field_per_window": amax[::5]}
 
 
-CASES = ["adjoint", "interface", "slab", "tfsf", "gradient-written"] + \
+FLOPS_PER_CELL_UPDATE_2D = 19    # FP32 operations of one 2D TE update (E', B_x, B_z, H'x, H'z, D)
+
+
+def te2d_measurement(gb, torch, n_steps=2000):
+    """The 2D TE scheme: 32 periodic columns (dx = 2) x 2^20 cells along the
+    motion, slanted moving layers (eps 1 / 4, 20-120 cells, slope 0.3,
+    v = 0.3c), an oblique line source and a probe, FP32, tile 8 x 16; CUDA
+    events on the context's stream around gfdtd2d_step after a warm-up call."""
+    rng = np.random.default_rng(20230413 + 11)
+    nx, nz, dx = 32, 1 << 20, 2.0
+    widths = rng.integers(20, 121, size=4000)
+    z = nz / 8 + np.cumsum(widths)
+    z = z[z < 7 * nz / 8]
+    eps = np.array([1.0] + [4.0 if i % 2 == 0 else 1.0 for i in range(len(z))])
+    stream = torch.cuda.Stream()
+    sim = gb.Simulation2D(nx, nz, dx, 0.5, gb.F32, stream=stream.cuda_stream)
+    sim.set_medium(0.3, 0.3, z, eps, np.ones(len(eps)))
+    w0 = 2 * np.pi / 40.0
+    tau = 10 * 40.0 / (2 * np.sqrt(np.log(2)))
+    sim.add_source(nz // 16, w0 * 0.5, w0, tau, 4 * tau)
+    sim.add_probe(0, nz * 15 // 16, np.linspace(0.75, 1.25, 16) * w0)
+    sim.set_tuning(8, 16)
+    sim.step(64)
+    sim.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    sim.step(n_steps)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    sec = e0.elapsed_time(e1) / 1e3
+    sim.close()
+    cu = nx * nz * n_steps
+    achieved = FLOPS_PER_CELL_UPDATE_2D * cu / sec / 1e12
+    peak = 2 * FP32_LANES_PER_SM * SM_COUNT * SM_MAX_MHZ * 1e6 / 1e12
+    return {"value": cu / sec / 1e9, "unit": "Gcell-updates/s", "steps": n_steps, "seconds": sec,
+            "config": "%d columns x 2^20 cells, slanted moving layers (slope 0.3, v = 0.3c), FP32, tile 8x16"
+                      % nx,
+            "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                         "frac": achieved / peak, "traffic": None,
+                         "note": "FP32 pipe: %d flops per 2D cell-update (algorithmic), peak derived as for the "
+                                 "1D kernel; whole gfdtd2d_step time (tile kernel, sources, probe folds)"
+                                 % FLOPS_PER_CELL_UPDATE_2D}}
+
+
+CASES = ["adjoint", "interface", "slab", "tfsf", "gradient-written", "te2d"] + \
     ["gradient-" + t for t in ("F32", "F32_KAHAN", "BF16", "F16", "F64")]
 
 
@@ -269,6 +313,9 @@ def run_case(args):
     T = args.time_steps
     if args.case == "gradient-written":
         print(json.dumps({"case": args.case, **gradient_as_written(gb)}), flush=True)
+        return
+    if args.case == "te2d":
+        print(json.dumps({"case": args.case, **te2d_measurement(gb, torch)}), flush=True)
         return
     if args.case == "adjoint":
         wl = w.config5(n_steps=T)
@@ -690,6 +737,7 @@ def main():
         if examples is not None:
             examples["gradient as written (eps 1->6, 2^20 cells, v=0.7c, 2e5 steps, FP32)"] = \
                 gradient_as_written(gb)
+        te2d = None if args.no_sweeps else te2d_measurement(gb, torch)
 
     if rank != 0:
         return
@@ -704,7 +752,7 @@ def main():
                        "parallelism": "instances sharded per rank" if world > 1 else "1 GPU"},
             "e2e": e2e, "gpu_launches": launches, "roofline": roofline, "plain": plain, "watchdog": watchdog,
             "clocks": clocks, "sweeps": sweeps, "capture": capture, "absorber": absorber, "adjoint": adjoint,
-            "tfsf": tfsf, "examples": examples}
+            "tfsf": tfsf, "examples": examples, "te2d": te2d}
     if not args.no_cpu:
         line["cpu_baseline"] = cpu_baseline(wl, single_core=True)
     print(json.dumps(line), flush=True)

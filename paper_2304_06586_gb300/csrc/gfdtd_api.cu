@@ -96,6 +96,7 @@ struct gfdtd_ctx {
   long long n_done = 0;
   DevBuf d_watch;                       // watchdog: one word per instance (see watch_launch)
   DevBuf d_watchblk;                    // the watchdog scan's blocks (WatchBlock)
+  DevBuf d_plain_s;                     // plain path: step within the chunk (device counter)
   int n_watchblk = 0;
   int stall = 0;                        // test hook: fast-kernel tile copies are not started
 
@@ -1385,27 +1386,55 @@ gfdtd_status gfdtd_step_plain(gfdtd_ctx* c, int64_t n_steps) {
   gfdtd_status s = finalize(c);
   if (s) return s;
   if (c->n_tfsf > 0) return fail(c, GFDTD_E_UNSUPPORTED, "one-way sources run in gfdtd_step only");
+  // One step = one launch per instance, in instance order on the stream, then a
+  // tick of the device step counter; the launches of a step read the step from
+  // device memory, so one captured CUDA graph per buffer parity replays every
+  // step (the launches stay one instance and one step each).
+  if (!c->d_plain_s.p) {
+    s = dalloc(c, c->d_plain_s, 16);
+    if (s) return s;
+  }
   while (n_steps > 0) {
     const int ch = (int)std::min<int64_t>(n_steps, kChunk);
+    CK(c, cudaMemsetAsync(c->d_plain_s.p, 0, sizeof(int), c->stream));
     for (int st = 0; st < ch; ++st) {
-      for (int i = 0; i < c->n_inst; ++i) {
-        PlainArgs<float> a;
-        a.inst = (const InstDev*)c->d_inst.p;
-        a.i = i;
-        a.tb = tables_of(c);
-        a.srcs = (const SrcDev*)c->d_srcs.p;
-        a.prbs = (const PrbDev*)c->d_prbs.p;
-        a.samples = (double*)c->d_samples.p;
-        a.chunk_stride = kChunk;
-        a.s = st;
-        a.n = c->n_done + st + 1;
-        a.Bin = (const float*)c->B[c->cur].p;
-        a.Din = (const float*)c->D[c->cur].p;
-        a.Bout = (float*)c->B[1 - c->cur].p;
-        a.Dout = (float*)c->D[1 - c->cur].p;
-        CKI(c, plain_launch(c->prec, &a, (int)c->nz[i], c->stream));
-        ++c->launches;
+      const auto key = std::make_pair(-1, c->cur);
+      auto it = c->graphs.find(key);
+      if (it == c->graphs.end()) {
+        cudaGraph_t g = nullptr;
+        CK(c, cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal));
+        gfdtd_status cs = GFDTD_OK;
+        for (int i = 0; i < c->n_inst && !cs; ++i) {
+          PlainArgs<float> a;
+          a.inst = (const InstDev*)c->d_inst.p;
+          a.i = i;
+          a.tb = tables_of(c);
+          a.srcs = (const SrcDev*)c->d_srcs.p;
+          a.prbs = (const PrbDev*)c->d_prbs.p;
+          a.samples = (double*)c->d_samples.p;
+          a.chunk_stride = kChunk;
+          a.n_done = (const long long*)c->d_ndone.p;
+          a.s_dev = (const int*)c->d_plain_s.p;
+          a.Bin = (const float*)c->B[c->cur].p;
+          a.Din = (const float*)c->D[c->cur].p;
+          a.Bout = (float*)c->B[1 - c->cur].p;
+          a.Dout = (float*)c->D[1 - c->cur].p;
+          if (plain_launch(c->prec, &a, (int)c->nz[i], c->cap_stream) != 0)
+            cs = fail(c, GFDTD_E_CUDA, "plain launch failed");
+        }
+        if (!cs && plain_tick_launch((int*)c->d_plain_s.p, c->cap_stream) != 0)
+          cs = fail(c, GFDTD_E_CUDA, "step counter launch failed");
+        cudaError_t e = cudaStreamEndCapture(c->cap_stream, &g);
+        if (cs) { if (g) cudaGraphDestroy(g); return cs; }
+        CK(c, e);
+        cudaGraphExec_t ex = nullptr;
+        e = cudaGraphInstantiate(&ex, g, 0);
+        cudaGraphDestroy(g);
+        CK(c, e);
+        it = c->graphs.emplace(key, ex).first;
       }
+      CK(c, cudaGraphLaunch(it->second, c->stream));
+      c->launches += c->n_inst + 1;
       c->cur = 1 - c->cur;
     }
     s = enqueue_fold_advance(c, c->stream, ch, c->cur);
@@ -1608,7 +1637,7 @@ void gfdtd_destroy(gfdtd_ctx* c) {
                     &c->d_wB[1][0], &c->d_wB[1][1], &c->d_amp2[0], &c->d_amp2[1], &c->d_lB[0],
                     &c->d_lB[1], &c->d_lD[0], &c->d_lD[1], &c->d_grad, &c->d_gn, &c->d_adjn[0], &c->d_adjn[1],
                     &c->d_Xre, &c->d_Xim, &c->d_bin0, &c->d_pnode, &c->d_acc0_re, &c->d_acc0_im,
-                    &c->d_adj_tiles, &c->d_tfsf, &c->d_tfaux, &c->d_tfcorr, &c->d_watch, &c->d_watchblk};
+                    &c->d_adj_tiles, &c->d_tfsf, &c->d_tfaux, &c->d_tfcorr, &c->d_watch, &c->d_watchblk, &c->d_plain_s};
   for (DevBuf* b : bufs) dfree(c, *b);
   if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
   delete c;

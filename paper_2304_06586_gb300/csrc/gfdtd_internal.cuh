@@ -202,13 +202,15 @@ struct PlainArgs {
   const PrbDev* prbs;
   double* samples;
   int chunk_stride;
-  int s;                      // step within the chunk
-  long long n;                // the step being taken (1-based)
+  const long long* n_done;    // steps completed at the start of the chunk (device)
+  const int* s_dev;           // step within the chunk (device): the step taken is *n_done + *s_dev + 1
   const T* Bin;
   const T* Din;
   T* Bout;
   T* Dout;
 };
+// Advances the plain path's step-within-chunk counter by one (after a step's launches).
+int plain_tick_launch(int* s_dev, cudaStream_t st);
 
 struct FoldArgs {
   const PrbDev* prbs;

@@ -65,44 +65,111 @@ int block_shapes(int prec, int* C, int* TB, int* MB, int max) {
 
 // ------------------------------------------------------------ plain kernel
 //
-// One thread per cell, one step per launch, one instance per launch.  Every
-// thread recomputes from the old fields in HBM the E', B' and H' values its D
-// update needs, and finds the material of each node by binary search.
+// One step of one instance per launch, fields in HBM: the throughput baseline
+// of the batched kernel.  A block of 256 threads stages the old B and D of its
+// 256 cells and a 4-cell halo on each side in shared memory, then forms each
+// intermediate value once: E' at the 259 nodes its B update reads, B' at 258
+// and H' at 257 half nodes, D' at its own 256 nodes (a barrier between the
+// stages).
+// The material comes from one binary search per block and level (the table
+// index at the block's first node, kept in shared memory) and a short forward
+// walk per node.
+
+// Coefficients (x: S/eps or S/mu, y: coupling) at node k, walking forward from
+// `idx` profile positions at or left of the block's first node.
+template <bool MATTER, bool ESIDE, typename R>
+__device__ __forceinline__ void walk_coef(const InstDev& I, const Tables& tb, long long off, int k, int idx,
+                                          R& cx, R& cy) {
+  const long long* __restrict__ zq = tb.zq + I.tab;
+  const auto* __restrict__ tv = TabOf<R>::get(tb, ESIDE) + I.tab;
+  if (I.flags & F_LINEAR) {
+    while (idx < I.n && node_of(__ldg(zq + idx), off) <= k) ++idx;
+    linear_coef<MATTER, ESIDE>(I, zq, tv, idx, k, off, cx, cy);
+    return;
+  }
+  const int nb = I.n - 1;
+  while (idx < nb && node_of(__ldg(zq + idx), off) <= k) ++idx;
+  const auto v = __ldg(tv + idx);
+  cx = v.x;
+  cy = MATTER ? v.y : coef<R>(I.cb, I.cb32);
+}
 
 template <bool MATTER, typename T>
-__device__ void plain_cell(const PlainArgs<T>& A, const InstDev& I, int k) {
+__device__ void plain_block(const PlainArgs<T>& A, const InstDev& I) {
   using R = typename Real<T>::type;
+  constexpr int NT = 256, H = 4, M = NT + 2 * H;     // staged cells: k0 - 4 .. k0 + 259
+  __shared__ R sB[M], sD[M], sE[M], sBn[M], sH[M];
+  __shared__ int sIdx[2];
   const int nz = I.nz;
-  const T* __restrict__ Bi = A.Bin + I.off;
-  const T* __restrict__ Di = A.Din + I.off;
-  auto ld = [&](const T* p, int j) -> R { return (j >= 0 && j < nz) ? (R)p[j] : (R)0; };
+  const int k0 = blockIdx.x * NT;
   const bool pos = (I.flags & F_POS) != 0;
   const R a = coef<R>(I.a, I.a32), cc = coef<R>(I.c, I.c32);
-  const long long n = A.n;
+  const int sc = *A.s_dev;                 // step within the chunk
+  const long long n = *A.n_done + sc + 1;
   const long long offE = I.dq * (2 * n - 1), offH = I.dq * (2 * n) - HALF_CELL;
+  const T* __restrict__ Bi = A.Bin + I.off;
+  const T* __restrict__ Di = A.Din + I.off;
+  auto cell = [&](int j) { return k0 - H + j; };
+  auto in = [&](int k) { return k >= 0 && k < nz; };
 
-  auto Ep = [&](int j) -> R {   // E' at node j, level n-1/2
-    if (j < 0 || j >= nz) return (R)0;
-    R se, cb;
-    node_coef<MATTER, true>(I, A.tb, offE, j, se, cb);
-    const R bs = pos ? ld(Bi, j - 1) + ld(Bi, j - 2) : ld(Bi, j) + ld(Bi, j + 1);
-    return se * ld(Di, j) - cb * bs;
-  };
-  auto Bn = [&](int j) -> R {   // B^n at half node j (after the absorbing layers' damping)
-    if (j < 0 || j >= nz) return (R)0;
-    const R bu = pos ? ld(Bi, j - 1) : ld(Bi, j + 1);
-    const R b = a * ld(Bi, j) + (cc * bu + (Ep(j) - Ep(j + 1)));
-    return I.abs_w > 0 ? b * absorb_factor<R>(I, (R)j + (R)0.5) : b;
-  };
-  auto Hp = [&](int j, R bn) -> R {   // H' at half node j, level n
-    if (j < 0 || j >= nz) return (R)0;
-    R sm, cb;
-    node_coef<MATTER, false>(I, A.tb, offH, j, sm, cb);
-    return sm * bn - cb * (ld(Di, j) + ld(Di, j + 1));
-  };
-  const R bk = Bn(k), bkm = Bn(k - 1);
-  const R du = pos ? ld(Di, k - 1) : ld(Di, k + 1);
-  R d = a * ld(Di, k) + (cc * du + (Hp(k - 1, bkm) - Hp(k, bk)));
+  for (int j = threadIdx.x; j < M; j += NT) {
+    const int k = cell(j);
+    sB[j] = in(k) ? (R)Bi[k] : (R)0;
+    sD[j] = in(k) ? (R)Di[k] : (R)0;
+  }
+  if (threadIdx.x < 2) {
+    const int nbp = (I.flags & F_LINEAR) ? I.n : I.n - 1;
+    sIdx[threadIdx.x] = count_at_or_left(A.tb.zq + I.tab, nbp, threadIdx.x == 0 ? offE : offH, k0 - H);
+  }
+  __syncthreads();
+
+  // E'^{n-1/2} at cells k0 - 2 .. k0 + 256 (B at level n-1)
+  for (int j = H - 2 + threadIdx.x; j <= H + NT; j += NT) {
+    const int k = cell(j);
+    R e = (R)0;
+    if (in(k)) {
+      R se, cb;
+      walk_coef<MATTER, true>(I, A.tb, offE, k, sIdx[0], se, cb);
+      const R bs = pos ? sB[j - 1] + sB[j - 2] : sB[j] + sB[j + 1];
+      e = se * sD[j] - cb * bs;
+    }
+    sE[j] = e;
+  }
+  __syncthreads();
+
+  // B^n at cells k0 - 2 .. k0 + 255 (absorbing layers damp after the update)
+  for (int j = H - 2 + threadIdx.x; j < H + NT; j += NT) {
+    const int k = cell(j);
+    R b = (R)0;
+    if (in(k)) {
+      const R bu = pos ? sB[j - 1] : sB[j + 1];
+      b = a * sB[j] + (cc * bu + (sE[j] - sE[j + 1]));
+      if (I.abs_w > 0) b *= absorb_factor<R>(I, (R)k + (R)0.5);
+    }
+    sBn[j] = b;
+    if (j >= H && in(k)) A.Bout[I.off + k] = (T)b;
+  }
+  __syncthreads();
+
+  // H'^n at cells k0 - 1 .. k0 + 255 (D at level n-1/2)
+  for (int j = H - 1 + threadIdx.x; j < H + NT; j += NT) {
+    const int k = cell(j);
+    R h = (R)0;
+    if (in(k)) {
+      R sm, cb;
+      walk_coef<MATTER, false>(I, A.tb, offH, k, sIdx[1], sm, cb);
+      h = sm * sBn[j] - cb * (sD[j] + sD[j + 1]);
+    }
+    sH[j] = h;
+  }
+  __syncthreads();
+
+  // D^{n+1/2} at the block's own cells, sources and probes
+  const int j = H + threadIdx.x;
+  const int k = cell(j);
+  if (!in(k)) return;
+  const R du = pos ? sD[j - 1] : sD[j + 1];
+  R d = a * sD[j] + (cc * du + (sH[j - 1] - sH[j]));
   if (I.abs_w > 0) d *= absorb_factor<R>(I, (R)k);
   const double t = (double)(2 * n + 1) * I.S * 0.5;
   for (int q = 0; q < I.nsrc; ++q) {
@@ -118,23 +185,29 @@ __device__ void plain_cell(const PlainArgs<T>& A, const InstDev& I, int k) {
       node_coef<MATTER, true>(I, A.tb, I.dq * (2 * n + 1), k, se, cb);
       R F = d * se;
       if (MATTER) {
-        const R bbar = pos ? (R)0.5 * (bkm + Bn(k - 2)) : (R)0.5 * (bk + Bn(k + 1));
+        const R bbar = pos ? (R)0.5 * (sBn[j - 1] + sBn[j - 2]) : (R)0.5 * (sBn[j] + sBn[j + 1]);
         F += ((R)I.beta * (R)I.S - (R)2 * cb) * bbar;
       }
-      A.samples[(long long)(I.prb0 + q) * A.chunk_stride + A.s] = (double)(F * (R)I.inv_S);
+      A.samples[(long long)(I.prb0 + q) * A.chunk_stride + sc] = (double)(F * (R)I.inv_S);
     }
   }
-  A.Bout[I.off + k] = (T)bk;
   A.Dout[I.off + k] = (T)d;
 }
 
 template <typename T>
 __global__ void __launch_bounds__(256) plain_kernel(const PlainArgs<T> A) {
-  const int k = blockIdx.x * blockDim.x + threadIdx.x;
   const InstDev I = A.inst[A.i];
-  if (k >= I.nz) return;
-  if (I.flags & F_MATTER) plain_cell<true>(A, I, k);
-  else plain_cell<false>(A, I, k);
+  if (I.flags & F_MATTER) plain_block<true>(A, I);
+  else plain_block<false>(A, I);
+}
+
+__global__ void plain_tick_kernel(int* s_dev) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) *s_dev += 1;
+}
+
+int plain_tick_launch(int* s_dev, cudaStream_t st) {
+  plain_tick_kernel<<<1, 32, 0, st>>>(s_dev);
+  return (int)cudaGetLastError();
 }
 
 template <typename T>
