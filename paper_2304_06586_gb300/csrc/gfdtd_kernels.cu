@@ -71,25 +71,47 @@ int block_shapes(int prec, int* C, int* TB, int* MB, int max) {
 // intermediate value once: E' at the 259 nodes its B update reads, B' at 258
 // and H' at 257 half nodes, D' at its own 256 nodes (a barrier between the
 // stages).
-// The material comes from one binary search per block and level (the table
-// index at the block's first node, kept in shared memory) and a short forward
-// walk per node.
+// The material comes from one coalesced pass of the whole block over the
+// profile positions and a short search in shared memory per node.
 
-// Coefficients (x: S/eps or S/mu, y: coupling) at node k, walking forward from
-// `idx` profile positions at or left of the block's first node.
+// The block's profile positions: how many lie at or left of its first staged
+// node at each level (counted by all threads at once, one coalesced pass), and
+// the next kPlainZ positions from the smaller count on, in shared memory, so
+// that each node finds its own count with a short search in shared memory.
+constexpr int kPlainZ = 64;
+
+struct PlainZ {
+  long long z[kPlainZ];   // zq[first .. first + kPlainZ) (FAR_AWAY past the end)
+  int first;              // index of z[0]
+  int cntE, cntH;         // positions at or left of the first staged node (E-side, H-side level)
+};
+
+// Number of profile positions at or left of node k at offset `off`: the block's
+// window in shared memory first, then (past it) a walk in global memory.
+__device__ __forceinline__ int plain_count(const PlainZ& P, const long long* __restrict__ zq, int nbp,
+                                           long long off, int k, int lo) {
+  // positions [lo, first + kPlainZ) are in shared memory; count those <= k
+  int a = lo - P.first, b = kPlainZ;
+  while (a < b) {
+    const int m = (a + b) >> 1;
+    if (node_of(P.z[m], off) <= k) a = m + 1; else b = m;
+  }
+  int idx = P.first + a;
+  if (a == kPlainZ)
+    while (idx < nbp && node_of(__ldg(zq + idx), off) <= k) ++idx;
+  return idx;
+}
+
 template <bool MATTER, bool ESIDE, typename R>
-__device__ __forceinline__ void walk_coef(const InstDev& I, const Tables& tb, long long off, int k, int idx,
-                                          R& cx, R& cy) {
+__device__ __forceinline__ void plain_coef(const InstDev& I, const Tables& tb, const PlainZ& P, long long off, int k,
+                                           int lo, R& cx, R& cy) {
   const long long* __restrict__ zq = tb.zq + I.tab;
   const auto* __restrict__ tv = TabOf<R>::get(tb, ESIDE) + I.tab;
   if (I.flags & F_LINEAR) {
-    while (idx < I.n && node_of(__ldg(zq + idx), off) <= k) ++idx;
-    linear_coef<MATTER, ESIDE>(I, zq, tv, idx, k, off, cx, cy);
+    linear_coef<MATTER, ESIDE>(I, zq, tv, plain_count(P, zq, I.n, off, k, lo), k, off, cx, cy);
     return;
   }
-  const int nb = I.n - 1;
-  while (idx < nb && node_of(__ldg(zq + idx), off) <= k) ++idx;
-  const auto v = __ldg(tv + idx);
+  const auto v = __ldg(tv + plain_count(P, zq, I.n - 1, off, k, lo));
   cx = v.x;
   cy = MATTER ? v.y : coef<R>(I.cb, I.cb32);
 }
@@ -99,7 +121,7 @@ __device__ void plain_block(const PlainArgs<T>& A, const InstDev& I) {
   using R = typename Real<T>::type;
   constexpr int NT = 256, H = 4, M = NT + 2 * H;     // staged cells: k0 - 4 .. k0 + 259
   __shared__ R sB[M], sD[M], sE[M], sBn[M], sH[M];
-  __shared__ int sIdx[2];
+  __shared__ PlainZ P;
   const int nz = I.nz;
   const int k0 = blockIdx.x * NT;
   const bool pos = (I.flags & F_POS) != 0;
@@ -117,9 +139,31 @@ __device__ void plain_block(const PlainArgs<T>& A, const InstDev& I) {
     sB[j] = in(k) ? (R)Bi[k] : (R)0;
     sD[j] = in(k) ? (R)Di[k] : (R)0;
   }
-  if (threadIdx.x < 2) {
+  {
+    const long long* __restrict__ zq = A.tb.zq + I.tab;
     const int nbp = (I.flags & F_LINEAR) ? I.n : I.n - 1;
-    sIdx[threadIdx.x] = count_at_or_left(A.tb.zq + I.tab, nbp, threadIdx.x == 0 ? offE : offH, k0 - H);
+    int cE = 0, cH = 0;
+    for (int j0 = 0; j0 < nbp; j0 += NT) {
+      const int jj = j0 + threadIdx.x;
+      bool pE = false, pH = false;
+      if (jj < nbp) {
+        const long long z = __ldg(zq + jj);
+        pE = node_of(z, offE) <= k0 - H;
+        pH = node_of(z, offH) <= k0 - H;
+      }
+      cE += __syncthreads_count(pE);
+      cH += __syncthreads_count(pH);
+    }
+    const int first = min(cE, cH);
+    if (threadIdx.x < kPlainZ) {
+      const int jj = first + threadIdx.x;
+      P.z[threadIdx.x] = jj < nbp ? __ldg(zq + jj) : FAR_AWAY;
+    }
+    if (threadIdx.x == 0) {
+      P.first = first;
+      P.cntE = cE;
+      P.cntH = cH;
+    }
   }
   __syncthreads();
 
@@ -129,7 +173,7 @@ __device__ void plain_block(const PlainArgs<T>& A, const InstDev& I) {
     R e = (R)0;
     if (in(k)) {
       R se, cb;
-      walk_coef<MATTER, true>(I, A.tb, offE, k, sIdx[0], se, cb);
+      plain_coef<MATTER, true>(I, A.tb, P, offE, k, P.cntE, se, cb);
       const R bs = pos ? sB[j - 1] + sB[j - 2] : sB[j] + sB[j + 1];
       e = se * sD[j] - cb * bs;
     }
@@ -157,7 +201,7 @@ __device__ void plain_block(const PlainArgs<T>& A, const InstDev& I) {
     R h = (R)0;
     if (in(k)) {
       R sm, cb;
-      walk_coef<MATTER, false>(I, A.tb, offH, k, sIdx[1], sm, cb);
+      plain_coef<MATTER, false>(I, A.tb, P, offH, k, P.cntH, sm, cb);
       h = sm * sBn[j] - cb * (sD[j] + sD[j + 1]);
     }
     sH[j] = h;
