@@ -264,6 +264,295 @@ __global__ void __launch_bounds__(kAdjThreads, 4) adjoint_step_kernel(const AdjA
   }
 }
 
+// ------------------------------------------------ time-blocked reverse steps
+//
+// adjoint_block_kernel transposes up to kAdjBlockSteps consecutive steps per
+// launch (n = n_hi, n_hi - 1, ...).  A warp holds the adjoint fields of a
+// window of 32 x kAdjCells cells of one instance in registers (lane l: cells
+// base + 8 l .. base + 8 l + 7) and applies the gathered transpose above one
+// step at a time, trading the ends of each lane's run with its neighbours by
+// shuffles; only the tile's output range is stored at the end, where the
+// margins keep it exact (adj_margin, adj_width).  Cells outside [0, nz) stay
+// zero, as the forward's ghosts are.  D^{n-1/2} of each step comes from the
+// segment's recomputation.  The probe term of step n (F_n = D_p se_p / S at
+// level n+1/2, with dL/dF_n from loss_source_kernel) enters lD' of every
+// window that holds the probe node, before the step, and its permittivity
+// term once, from the tile whose output range holds the node.
+// The permittivity gradient of the output cells adds up per lane over runs of
+// one profile value, then per warp in shared memory over the values the
+// window can meet in the launch, and reaches the FP64 gradient with one
+// atomic per value and tile; a window that stays before the first profile
+// position or after the last one over the whole launch has a single value,
+// summed in registers.
+
+constexpr int kAdjKeysW = 192;     // profile values a warp collects in shared memory
+
+struct GradRun {
+  int key;
+  float acc;
+};
+
+// Hands a lane's run to the warp's accumulators (values kb .. kb + kAdjKeysW - 1)
+// or, outside them, to the FP64 gradient.
+__device__ __forceinline__ void grad_flush(GradRun& r, float* sacc, int kb, double* grad) {
+  if (r.key >= 0 && r.acc != 0.0f) {
+    const int slot = r.key - kb;
+    if (slot >= 0 && slot < kAdjKeysW) atomicAdd(sacc + slot, r.acc);
+    else atomicAdd(grad + r.key, (double)r.acc);
+  }
+  r.acc = 0.0f;
+}
+__device__ __forceinline__ void grad_add(GradRun& r, int key, float v, float* sacc, int kb, double* grad) {
+  if (key != r.key) {
+    grad_flush(r, sacc, kb, grad);
+    r.key = key;
+  }
+  r.acc += v;
+}
+
+template <bool POS>
+__device__ __forceinline__ void adjoint_tile(const AdjBlockArgs& A, const InstDev& I, int inst, int x0,
+                                             float* sacc, double* grad, int lane) {
+  constexpr int C = kAdjCells;
+  const int base = x0 - adj_margin(POS);
+  const int k0 = base + C * lane;
+  const int nz = I.nz;
+  const int out_hi = min(x0 + adj_width(POS), nz);   // output cells [x0, out_hi)
+  float LB[C], LD[C];
+  load_cells<float, float, C>(A.lBn + I.off, k0, I.nz_pad, LB);
+  load_cells<float, float, C>(A.lDn + I.off, k0, I.nz_pad, LD);
+#pragma unroll
+  for (int c = 0; c < C; ++c) {   // (padding cells past nz are not necessarily written)
+    const bool in = (unsigned)(k0 + c) < (unsigned)nz;
+    LB[c] = in ? LB[c] : 0.0f;
+    LD[c] = in ? LD[c] : 0.0f;
+  }
+  const float a = I.a32, cc = I.c32, cb = I.cb32, S = (float)I.S, inv_S = (float)I.inv_S;
+  const bool lin = (I.flags & F_LINEAR) != 0;
+  const bool mu_const = (I.flags & F_MU_CONST) != 0;
+  const long long dq = I.dq;
+  const long long* __restrict__ zq = A.tb.zq + I.tab;
+  const float2* __restrict__ tv = A.tb.tabE32 + I.tab;
+  const int np = lin ? I.n : I.n - 1;                  // profile positions
+  const long long n_hi = A.n_seg + A.m_hi, n_lo = n_hi - A.nsteps + 1;
+
+  // a single permittivity value over the window and the launch (key ku), else ku = -1
+  int ku = -1;
+  float seu = 0.0f;
+  {
+    const int last = base + 32 * C - 1;
+    const long long oa = dq * (2 * n_lo - 1), ob = dq * (2 * n_hi - 1);
+    if (np == 0) {
+      ku = 0;
+    } else {
+      const long long zf = __ldg(zq), zl = __ldg(zq + np - 1);
+      if (last < node_of(zf, oa) && last < node_of(zf, ob)) ku = 0;
+      else if (base >= node_of(zl, oa) && base >= node_of(zl, ob)) ku = lin ? np - 1 : np;
+    }
+    if (ku >= 0) {
+      const float2 v = __ldg(tv + ku);
+      seu = lin ? S / v.x : v.x;
+    }
+  }
+  int kb = 0, li = 0, liH = 0;
+  if (ku < 0) {
+    // the smallest value the window meets in the launch: one below the count at its first cell
+    const long long xa = ((long long)base << 32) - dq * (2 * n_lo - 1);
+    const long long xb = ((long long)base << 32) - dq * (2 * n_hi - 1);
+    kb = max(0, positions_at_or_left(zq, np, min(xa, xb)) - 1);
+    for (int i = lane; i < kAdjKeysW; i += 32) sacc[i] = 0.0f;
+    __syncwarp();
+    li = positions_at_or_left(zq, np, ((long long)k0 << 32) - dq * (2 * n_hi - 1));
+  }
+  if (!mu_const) liH = count_at_or_left(zq, np, dq * (2 * n_hi) - HALF_CELL, k0);
+  // the probe
+  const int kp = A.probe_node[inst];
+  const bool probe_in = kp >= 0 && kp < nz && kp >= base && kp < base + 32 * C;
+  const bool probe_out = probe_in && kp >= x0 && kp < out_hi;
+  const int lp = probe_in ? (kp - base) / C : -1, cp = probe_in ? (kp - base) % C : 0;
+
+  GradRun run{-1, 0.0f};
+  float gu = 0.0f;                                   // the single value's sum (ku >= 0)
+  for (int s = 0; s < A.nsteps; ++s) {
+    const int m = A.m_hi - s;                        // segment step transposed: n = n_seg + m
+    const long long n = A.n_seg + m;
+    float Dv[C];                                     // D^{n-1/2}: the forward's field after step m - 1
+    load_cells<float, float, C>(A.dseg + (long long)(m - 1) * A.dseg_stride + I.off, k0, I.nz_pad, Dv);
+
+    // probe term of step n (level n+1/2) into lD'
+    if (lane == lp) {
+      const double g = A.gn[(long long)(m - 1) * A.n_inst + inst];
+      if (g != 0.0) {
+        const long long off = dq * (2 * n + 1);
+        double se, y;
+        node_coef<false, true>(I, A.tb, off, kp, se, y);
+        const float add = (float)(g * se / I.S);
+#pragma unroll
+        for (int c = 0; c < C; ++c) LD[c] += (c == cp) ? add : 0.0f;
+        if (probe_out) {
+          // F = D / eps: dF/deps = -D / eps^2 = -D se^2 / S^2
+          const double Dp = A.dseg[(long long)m * A.dseg_stride + I.off + kp];
+          const double gE = g * (-Dp * se * se / (I.S * I.S));
+          int i0, i1;
+          double w0, w1;
+          eps_weights(I, zq, ((long long)kp << 32) - off, i0, w0, i1, w1);
+          atomicAdd(grad + i0, gE * w0);
+          if (lin) atomicAdd(grad + i1, gE * w1);
+        }
+      }
+    }
+
+    // lH_j = lD'_{j+1} - lD'_j and lBt_j = lB'_j + sm_j lH_j
+    const float dn1 = __shfl_down_sync(FULL, LD[0], 1);
+    float lH[C], T[C];
+    {
+      float smv[C];
+      if (mu_const) {
+#pragma unroll
+        for (int c = 0; c < C; ++c) smv[c] = I.sm32;
+      } else {
+        float tmp[C];
+        lane_coefs<C, false, false, float>(I, A.tb, dq * (2 * n) - HALF_CELL, k0, liH, smv, tmp);
+      }
+#pragma unroll
+      for (int c = 0; c < C; ++c) {
+        const bool in = (unsigned)(k0 + c) < (unsigned)nz;
+        lH[c] = in ? (c + 1 < C ? LD[c + 1] : dn1) - LD[c] : 0.0f;
+        T[c] = in ? LB[c] + smv[c] * lH[c] : 0.0f;
+      }
+    }
+    // lE_k = lBt_k - lBt_{k-1}
+    const float tl1 = __shfl_up_sync(FULL, T[C - 1], 1);
+    float lE[C];
+#pragma unroll
+    for (int c = 0; c < C; ++c) {
+      const bool in = (unsigned)(k0 + c) < (unsigned)nz;
+      lE[c] = in ? T[c] - (c > 0 ? T[c - 1] : tl1) : 0.0f;
+    }
+    const float hl1 = __shfl_up_sync(FULL, lH[C - 1], 1);
+    const float dl1 = __shfl_up_sync(FULL, LD[C - 1], 1);
+    const float tn1 = __shfl_down_sync(FULL, T[0], 1);
+    const float en1 = __shfl_down_sync(FULL, lE[0], 1);
+    const float en2 = __shfl_down_sync(FULL, lE[1], 1);
+    const float el1 = __shfl_up_sync(FULL, lE[C - 1], 1);
+
+    // the permittivity at level n-1/2 of each cell, with the profile values it weighs
+    const long long offE = dq * (2 * n - 1);
+    const long long xi0 = ((long long)k0 << 32) - offE;
+    if (ku < 0) {
+      while (li < np && __ldg(zq + li) <= xi0) ++li;
+      while (li > 0 && __ldg(zq + li - 1) > xi0) --li;
+    }
+    int idx = li;
+    float nD[C], nB[C];
+#pragma unroll
+    for (int c = 0; c < C; ++c) {
+      const int k = k0 + c;
+      const bool in = (unsigned)k < (unsigned)nz;
+      float se, w1 = 0.0f;
+      int key0 = ku, key1 = ku;
+      if (ku >= 0) {
+        se = seu;
+      } else {
+        const long long xi = xi0 + ((long long)c << 32);
+        while (idx < np && __ldg(zq + idx) <= xi) ++idx;
+        if (lin) {
+          float e;
+          if (idx <= 0) {
+            e = __ldg(tv).x;
+            key0 = key1 = 0;
+          } else if (idx >= np) {
+            e = __ldg(tv + np - 1).x;
+            key0 = key1 = np - 1;
+          } else {
+            const long long z0 = __ldg(zq + idx - 1), z1 = __ldg(zq + idx);
+            w1 = quick_div(i64_to_f32(xi - z0), i64_to_f32(z1 - z0));
+            const float e0 = __ldg(tv + idx - 1).x, e1 = __ldg(tv + idx).x;
+            e = e0 + w1 * (e1 - e0);
+            key0 = idx - 1;
+            key1 = idx;
+          }
+          se = quick_div(S, e);
+        } else {
+          se = __ldg(tv + idx).x;
+          key0 = key1 = idx;
+        }
+      }
+      // lD_k = a lD'_k + c lD'_dn(k) - cb (lH_k + lH_{k-1}) + se_k lE_k
+      const float ldn = POS ? (c + 1 < C ? LD[c + 1] : dn1) : (c > 0 ? LD[c - 1] : dl1);
+      const float hm1 = c > 0 ? lH[c - 1] : hl1;
+      nD[c] = in ? a * LD[c] + cc * ldn - cb * (lH[c] + hm1) + se * lE[c] : 0.0f;
+      // lB_j = a lBt_j + c lBt_dn(j) - cb (lE_{j+1} + lE_{j+2})  (v >= 0)
+      //                                 - cb (lE_j + lE_{j-1})      (v < 0)
+      if (POS) {
+        const float tdn = c + 1 < C ? T[c + 1] : tn1;
+        const float e1 = c + 1 < C ? lE[c + 1] : en1;
+        const float e2 = c + 2 < C ? lE[c + 2] : (c + 2 == C ? en1 : en2);
+        nB[c] = in ? a * T[c] + cc * tdn - cb * (e1 + e2) : 0.0f;
+      } else {
+        const float tdn = c > 0 ? T[c - 1] : tl1;
+        const float em1 = c > 0 ? lE[c - 1] : el1;
+        nB[c] = in ? a * T[c] + cc * tdn - cb * (lE[c] + em1) : 0.0f;
+      }
+      // dL/deps_k = lE_k (-S D_k / eps_k^2) = lE_k (-se^2 D_k / S), output cells only
+      if (k >= x0 && k < out_hi) {
+        const float gE = lE[c] * (-se * se * Dv[c] * inv_S);
+        if (ku >= 0) {
+          gu += gE;
+        } else {
+          grad_add(run, key0, gE * (1.0f - w1), sacc, kb, grad);
+          grad_add(run, key1, gE * w1, sacc, kb, grad);
+        }
+      }
+    }
+#pragma unroll
+    for (int c = 0; c < C; ++c) {
+      LB[c] = nB[c];
+      LD[c] = nD[c];
+    }
+  }
+
+  const int hi = min(x0 + adj_width(POS), I.nz_pad);
+  store_cells<float, float, C>(A.lB + I.off, k0, x0, hi, LB);
+  store_cells<float, float, C>(A.lD + I.off, k0, x0, hi, LD);
+  if (ku >= 0) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) gu += __shfl_xor_sync(FULL, gu, o);
+    if (lane == 0 && gu != 0.0f) atomicAdd(grad + ku, (double)gu);
+  } else {
+    grad_flush(run, sacc, kb, grad);
+    __syncwarp();
+    for (int i = lane; i < kAdjKeysW; i += 32)
+      if (sacc[i] != 0.0f) atomicAdd(grad + kb + i, (double)sacc[i]);
+    __syncwarp();
+  }
+}
+
+__global__ void __launch_bounds__(128, 4) adjoint_block_kernel(const AdjBlockArgs A) {
+  constexpr int WPB = 4;
+  __shared__ float s_acc[WPB][kAdjKeysW];
+  const int wib = __shfl_sync(FULL, (int)(threadIdx.x >> 5), 0), lane = threadIdx.x & 31;
+  const int gw = blockIdx.x * WPB + wib, nw = gridDim.x * WPB;
+  // (blocks add into different copies of the gradient, so that the many warps of one
+  // uniform region do not all queue on the same profile value's atomics)
+  double* gcopy = A.grad + (size_t)(blockIdx.x % A.grad_copies) * A.grad_stride;
+  for (int t = gw; t < A.n_tiles; t += nw) {
+    const int2 tl = A.tiles[t];
+    const InstDev I = A.inst[tl.x];
+    if (I.flags & F_POS) adjoint_tile<true>(A, I, tl.x, tl.y, s_acc[wib], gcopy + I.tab, lane);
+    else adjoint_tile<false>(A, I, tl.x, tl.y, s_acc[wib], gcopy + I.tab, lane);
+  }
+}
+
+int adjoint_block_launch(const AdjBlockArgs& a, int grid, cudaStream_t st) {
+  adjoint_block_kernel<<<grid, 128, 0, st>>>(a);
+  return (int)cudaGetLastError();
+}
+
+int adjoint_block_occupancy(int* blocks_per_sm) {
+  return (int)cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, adjoint_block_kernel, 128, 0);
+}
+
 // The probe term of step n: F_n = D^{n+1/2}_p se_p / S = D_p / eps_p (level
 // n+1/2) with dL/dF_n = g[inst]; adds g se_p / S to lD at the probe node and
 // g dF/deps = g (-D_p / eps_p^2) to dL/deps.  One thread per instance.

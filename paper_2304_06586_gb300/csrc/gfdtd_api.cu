@@ -126,6 +126,7 @@ struct gfdtd_ctx {
   DevBuf d_ckB, d_ckD, d_dseg[2], d_wB[2][2], d_amp2[2], d_lB[2], d_lD[2], d_grad, d_gn, d_adjn[2], d_Xre, d_Xim,
       d_bin0, d_pnode, d_acc0_re, d_acc0_im, d_adj_tiles;
   int n_adj_tiles = 0;
+  int adj_grid = 1;
 
   // space-time capture: frames of one field of one instance every ts steps
   struct Capture {
@@ -461,6 +462,7 @@ static gfdtd_status finalize(gfdtd_ctx* c) {
     }
   }
   c->h_inst = inst;
+  c->n_adj_tiles = 0;   // the adjoint's tiles follow the signs of v
   c->n_src = (int)srcs.size();
   c->n_prb = (int)prbs.size();
   c->n_bins = (int)omega.size();
@@ -843,11 +845,20 @@ extern "C" gfdtd_status gfdtd_adjoint(gfdtd_ctx* c, int64_t n_steps, int probe_i
     CK(c, cudaMemsetAsync(c->d_wB[b][1].p, 0, fb, st));
   }
   if (c->n_adj_tiles == 0) {
+    // tiles of the time-blocked transpose, those of instances with v >= 0 first (warps
+    // running at the same time execute the same code)
     std::vector<int2> t;
-    for (int i = 0; i < c->n_inst; ++i)
-      for (long long x0 = 0; x0 < c->nz[i]; x0 += kAdjTileCells) t.push_back(make_int2(i, (int)x0));
+    for (int side = 0; side < 2; ++side)
+      for (int i = 0; i < c->n_inst; ++i) {
+        const bool pos = (c->h_inst[i].flags & F_POS) != 0;
+        if (pos != (side == 0)) continue;
+        for (long long x0 = 0; x0 < c->nz[i]; x0 += adj_width(pos)) t.push_back(make_int2(i, (int)x0));
+      }
     if ((s = upload(c, c->d_adj_tiles, t))) return s;
     c->n_adj_tiles = (int)t.size();
+    int nb = 0;
+    CKI(c, adjoint_block_occupancy(&nb));
+    c->adj_grid = std::max(1, std::min(c->num_sms * std::max(nb, 1), (c->n_adj_tiles + 3) / 4));
   }
   // ---- forward with checkpoints at every segment start
   const long long n0 = c->n_done;
@@ -957,20 +968,9 @@ extern "C" gfdtd_status gfdtd_adjoint(gfdtd_ctx* c, int64_t n_steps, int probe_i
     sa.S = c->S;
     sa.gn = (double*)c->d_gn.p;
     CKI(c, loss_source_launch(sa, st));
-    for (int m = Ks; m >= 1; --m) {
-      const long long n = ns + m;
-      ProbeAdjArgs pa;
-      pa.inst = (const InstDev*)c->d_inst.p;
-      pa.n_inst = c->n_inst;
-      pa.tb = tables_of(c);
-      pa.probe_node = (const int*)c->d_pnode.p;
-      pa.gn = (const double*)c->d_gn.p + (long long)(m - 1) * c->n_inst;
-      pa.lD = (float*)c->d_lD[lc].p;
-      pa.Dnew = (const float*)((char*)c->d_dseg[bs].p + m * fb);
-      pa.n = n;
-      pa.grad = (double*)c->d_grad.p;
-      CKI(c, probe_adjoint_launch(pa, st));
-      AdjArgs aa;
+    ++c->launches;
+    for (int m_hi = Ks; m_hi >= 1; m_hi -= kAdjBlockSteps) {
+      AdjBlockArgs aa;
       aa.inst = (const InstDev*)c->d_inst.p;
       aa.tiles = (const int2*)c->d_adj_tiles.p;
       aa.n_tiles = c->n_adj_tiles;
@@ -979,13 +979,19 @@ extern "C" gfdtd_status gfdtd_adjoint(gfdtd_ctx* c, int64_t n_steps, int probe_i
       aa.lDn = (const float*)c->d_lD[lc].p;
       aa.lB = (float*)c->d_lB[1 - lc].p;
       aa.lD = (float*)c->d_lD[1 - lc].p;
-      aa.Dold = (const float*)((char*)c->d_dseg[bs].p + (m - 1) * fb);
-      aa.n = n;
+      aa.dseg = (const float*)c->d_dseg[bs].p;
+      aa.dseg_stride = (long long)(fb / sizeof(float));
+      aa.n_seg = ns;
+      aa.m_hi = m_hi;
+      aa.nsteps = std::min(kAdjBlockSteps, m_hi);
+      aa.probe_node = (const int*)c->d_pnode.p;
+      aa.gn = (const double*)c->d_gn.p;
+      aa.n_inst = c->n_inst;
       aa.grad = (double*)c->d_grad.p;       // copies 0 .. kGradCopies-1; the sum goes after them
       aa.grad_copies = kGradCopies;
       aa.grad_stride = ntab;
-      CKI(c, adjoint_step_launch(aa, st));
-      c->launches += 2;
+      CKI(c, adjoint_block_launch(aa, c->adj_grid, st));
+      ++c->launches;
       lc = 1 - lc;
     }
     CK(c, cudaEventRecord(ev_rv[bs], st));
@@ -1397,6 +1403,11 @@ gfdtd_status gfdtd_step_plain(gfdtd_ctx* c, int64_t n_steps) {
   while (n_steps > 0) {
     const int ch = (int)std::min<int64_t>(n_steps, kChunk);
     CK(c, cudaMemsetAsync(c->d_plain_s.p, 0, sizeof(int), c->stream));
+    if (c->n_src > 0) {
+      CKI(c, src_amp_launch((const SrcDev*)c->d_srcs.p, c->n_src, (double*)c->d_amp.p, kChunk, ch,
+                            (const long long*)c->d_ndone.p, c->S, c->stream));
+      ++c->launches;
+    }
     for (int st = 0; st < ch; ++st) {
       const auto key = std::make_pair(-1, c->cur);
       auto it = c->graphs.find(key);
@@ -1406,10 +1417,10 @@ gfdtd_status gfdtd_step_plain(gfdtd_ctx* c, int64_t n_steps) {
         gfdtd_status cs = GFDTD_OK;
         for (int i = 0; i < c->n_inst && !cs; ++i) {
           PlainArgs<float> a;
-          a.inst = (const InstDev*)c->d_inst.p;
-          a.i = i;
+          a.I = c->h_inst[i];
           a.tb = tables_of(c);
           a.srcs = (const SrcDev*)c->d_srcs.p;
+          a.src_amp = (const double*)c->d_amp.p;
           a.prbs = (const PrbDev*)c->d_prbs.p;
           a.samples = (double*)c->d_samples.p;
           a.chunk_stride = kChunk;

@@ -261,9 +261,13 @@ __device__ __forceinline__ void coef_of(R S, R beta, R cb, R e, R m, R& cx, R& c
   }
 }
 
-template <int C, bool MATTER, bool ESIDE, typename R>
-__device__ __forceinline__ void lane_coefs(const InstDev& I, const Tables& tb, long long off,
-                                           int k0, int& li, R (&cx)[C], R (&cy)[C]) {
+// The material coefficients (x: S/eps or S/mu, y: coupling; y is not formed for
+// layers of a moving perturbation) of a lane's C cells k0 .. k0 + C - 1 at one
+// level, handed to f(c, x, y) cell by cell as they are formed, so that the
+// caller's update uses each at once and no per-cell array of them is kept.
+template <int C, bool MATTER, bool ESIDE, typename R, typename F>
+__device__ __forceinline__ void lane_apply(const InstDev& I, const Tables& tb, long long off,
+                                           int k0, int& li, F&& f) {
   const long long* __restrict__ zq = tb.zq + I.tab;
   const auto* __restrict__ tv = TabOf<R>::get(tb, ESIDE) + I.tab;
   if (I.flags & F_LINEAR) {
@@ -292,7 +296,9 @@ __device__ __forceinline__ void lane_coefs(const InstDev& I, const Tables& tb, l
         const R t = (R)c - (r ? mR : (R)0);
         const R e = (r ? aeR : aeL) + (r ? beR : beL) * t;
         const R m = (r ? amR : amL) + (r ? bmR : bmL) * t;
-        coef_of<MATTER, ESIDE>(S, beta, cb, e, m, cx[c], cy[c]);
+        R x, y;
+        coef_of<MATTER, ESIDE>(S, beta, cb, e, m, x, y);
+        f(c, x, y);
       }
     } else {
       // several knots among the lane's cells: walk them cell by cell
@@ -308,7 +314,9 @@ __device__ __forceinline__ void lane_coefs(const InstDev& I, const Tables& tb, l
           t0 = (R)c;
         }
         const R t = (R)c - t0;
-        coef_of<MATTER, ESIDE>(S, beta, cb, ae + be * t, am + bm * t, cx[c], cy[c]);
+        R x, y;
+        coef_of<MATTER, ESIDE>(S, beta, cb, ae + be * t, am + bm * t, x, y);
+        f(c, x, y);
       }
     }
     return;
@@ -324,8 +332,7 @@ __device__ __forceinline__ void lane_coefs(const InstDev& I, const Tables& tb, l
 #pragma unroll
     for (int c = 0; c < C; ++c) {
       const bool past = k0 + c >= K1;
-      cx[c] = past ? v1.x : v0.x;
-      if (MATTER) cy[c] = past ? v1.y : v0.y;
+      f(c, (R)(past ? v1.x : v0.x), MATTER ? (R)(past ? v1.y : v0.y) : (R)0);
     }
     return;
   }
@@ -337,8 +344,8 @@ __device__ __forceinline__ void lane_coefs(const InstDev& I, const Tables& tb, l
 #pragma unroll
     for (int c = 0; c < C; ++c) {
       const int k = k0 + c;
-      cx[c] = k >= K2 ? v2.x : (k >= K1 ? v1.x : v0.x);
-      if (MATTER) cy[c] = k >= K2 ? v2.y : (k >= K1 ? v1.y : v0.y);
+      f(c, (R)(k >= K2 ? v2.x : (k >= K1 ? v1.x : v0.x)),
+        MATTER ? (R)(k >= K2 ? v2.y : (k >= K1 ? v1.y : v0.y)) : (R)0);
     }
   } else {
     int idx = li;
@@ -347,10 +354,19 @@ __device__ __forceinline__ void lane_coefs(const InstDev& I, const Tables& tb, l
       const int k = k0 + c;
       while (idx < nb && node_of(__ldg(zq + idx), off) <= k) ++idx;
       const auto v = __ldg(tv + idx);
-      cx[c] = v.x;
-      if (MATTER) cy[c] = v.y;
+      f(c, (R)v.x, MATTER ? (R)v.y : (R)0);
     }
   }
+}
+
+// The same coefficients stored per cell.
+template <int C, bool MATTER, bool ESIDE, typename R>
+__device__ __forceinline__ void lane_coefs(const InstDev& I, const Tables& tb, long long off,
+                                           int k0, int& li, R (&cx)[C], R (&cy)[C]) {
+  lane_apply<C, MATTER, ESIDE, R>(I, tb, off, k0, li, [&](int c, R x, R y) {
+    cx[c] = x;
+    cy[c] = y;
+  });
 }
 
 template <int C, typename R>
@@ -483,15 +499,7 @@ __device__ __forceinline__ void run_tile(const BlockArgs<T>& A, const InstDev& I
       br1 = __shfl_down_sync(FULL, B[0], 1);
     }
     {
-      R se[C], cbe[C];
-      if (!eps_const) {
-        lane_coefs<C, MATTER, true>(I, A.tb, dq * (2 * n - 1), k0, liE, se, cbe);
-      } else {
-#pragma unroll
-        for (int c = 0; c < C; ++c) { se[c] = se0; cbe[c] = cbe0; }
-      }
-#pragma unroll
-      for (int c = 0; c < C; ++c) {
+      auto upd = [&](int c, R se, R cbe) {
         R bs;
         if (POS) {
           const R b1 = c >= 1 ? B[c - 1] : bl1;
@@ -500,8 +508,14 @@ __device__ __forceinline__ void run_tile(const BlockArgs<T>& A, const InstDev& I
         } else {
           bs = B[c] + (c + 1 < C ? B[c + 1] : br1);
         }
-        X[c] = se[c] * D[c] - (MATTER ? cbe[c] : cbe0) * bs;
+        X[c] = se * D[c] - (MATTER ? cbe : cbe0) * bs;
         if (EDGE) X[c] = ((unsigned)(k0 + c) < (unsigned)nz) ? X[c] : (R)0;
+      };
+      if (!eps_const) {
+        lane_apply<C, MATTER, true, R>(I, A.tb, dq * (2 * n - 1), k0, liE, upd);
+      } else {
+#pragma unroll
+        for (int c = 0; c < C; ++c) upd(c, se0, cbe0);
       }
     }
 
@@ -542,18 +556,16 @@ __device__ __forceinline__ void run_tile(const BlockArgs<T>& A, const InstDev& I
     // ---- H'^n = sm B - cb (D_j + D_{j+1})  (D at level n-1/2, material at level n)
     const R dr = __shfl_down_sync(FULL, D[0], 1);
     {
-      R sm[C], cbh[C];
+      auto upd = [&](int c, R sm, R cbh) {
+        const R d1 = c + 1 < C ? D[c + 1] : dr;
+        X[c] = sm * B[c] - (MATTER ? cbh : cbh0) * (D[c] + d1);
+        if (EDGE) X[c] = ((unsigned)(k0 + c) < (unsigned)nz) ? X[c] : (R)0;
+      };
       if (!mu_const) {
-        lane_coefs<C, MATTER, false>(I, A.tb, dq * (2 * n) - HALF_CELL, k0, liH, sm, cbh);
+        lane_apply<C, MATTER, false, R>(I, A.tb, dq * (2 * n) - HALF_CELL, k0, liH, upd);
       } else {
 #pragma unroll
-        for (int c = 0; c < C; ++c) { sm[c] = sm0; cbh[c] = cbh0; }
-      }
-#pragma unroll
-      for (int c = 0; c < C; ++c) {
-        const R d1 = c + 1 < C ? D[c + 1] : dr;
-        X[c] = sm[c] * B[c] - (MATTER ? cbh[c] : cbh0) * (D[c] + d1);
-        if (EDGE) X[c] = ((unsigned)(k0 + c) < (unsigned)nz) ? X[c] : (R)0;
+        for (int c = 0; c < C; ++c) upd(c, sm0, cbh0);
       }
     }
 
@@ -1087,8 +1099,17 @@ __device__ __forceinline__ void run_tile_fast(const BlockArgs<T>& A, const InstD
   store_cells<T, R, C>(A.Dout + I.off, k0, x0, hi, D);
 }
 
+// Blocks per SM the general kernel's registers are held to: runs of up to 8
+// cells in FP32 arithmetic fit in fewer registers, and the batches that
+// choose them are small (few warps), so occupancy pays there; wider runs,
+// FP64 arithmetic and the compensated tier keep the compiler's choice (0: no
+// bound).
+__host__ __device__ constexpr int general_min_blocks(int C, int real_bytes, bool kahan) {
+  return (kahan || real_bytes != 4) ? 0 : (C <= 4 ? 6 : (C <= 8 ? 4 : 0));
+}
+
 template <int C, int TB, bool MATTER, typename T, bool KAHAN = false>
-__global__ void __launch_bounds__(128) block_kernel(const BlockArgs<T> A) {
+__global__ void __launch_bounds__(128, general_min_blocks(C, sizeof(typename Real<T>::type), KAHAN)) block_kernel(const BlockArgs<T> A) {
   const int warps_per_block = blockDim.x >> 5;
   const int gw = blockIdx.x * warps_per_block + (threadIdx.x >> 5);
   const int nw = gridDim.x * warps_per_block;

@@ -195,10 +195,10 @@ struct BlockArgs {
 // Arguments of the plain kernel (one instance, one step).
 template <typename T>
 struct PlainArgs {
-  const InstDev* inst;
-  int i;                      // instance index
+  InstDev I;                  // the instance's record (in the launch parameters)
   Tables tb;
   const SrcDev* srcs;
+  const double* src_amp;      // source amplitudes of the chunk's steps (src_amp_launch)
   const PrbDev* prbs;
   double* samples;
   int chunk_stride;
@@ -271,6 +271,43 @@ struct SourceAdjArgs {
   double* gn;                 // [step][inst]
 };
 int adjoint_step_launch(const AdjArgs& a, cudaStream_t st);
+
+// Time-blocked transpose: kAdjBlockSteps reverse steps per launch, a warp per
+// tile of 32 x kAdjCells cells held in registers.  A tile's output range
+// [x0, x0 + adj_width) sits in its window [x0 - adj_margin, x0 - adj_margin +
+// 32 kAdjCells) with the margins one reverse step's stencil needs per step
+// (cells j - 1 .. j + 3 for v >= 0, j - 2 .. j + 1 for v < 0).
+constexpr int kAdjCells = 8;
+constexpr int kAdjBlockSteps = 8;
+__host__ __device__ constexpr int adj_margin(bool pos) { return pos ? kAdjBlockSteps : 2 * kAdjBlockSteps; }
+__host__ __device__ constexpr int adj_width(bool pos) {
+  return (32 * kAdjCells - adj_margin(pos) - (pos ? 3 * kAdjBlockSteps : kAdjBlockSteps)) / 4 * 4;
+}
+static_assert(adj_margin(true) % 4 == 0 && adj_margin(false) % 4 == 0, "windows start on 16-byte chunks");
+
+struct AdjBlockArgs {
+  const InstDev* inst;
+  const int2* tiles;          // (instance, first output cell), adj_width(v >= 0) apart
+  int n_tiles;
+  Tables tb;
+  const float* lBn;           // adjoint of B^{n_hi}, D^{n_hi+1/2}
+  const float* lDn;
+  float* lB;                  // adjoint of B^{n_hi-nsteps}, D^{n_hi-nsteps+1/2}
+  float* lD;
+  const float* dseg;          // D^{n+1/2} of the segment's step m (n = n_seg + m) at dseg + m * dseg_stride
+  long long dseg_stride;
+  long long n_seg;            // forward steps done at the segment's start
+  int m_hi;                   // segment step of the first step transposed (n_hi = n_seg + m_hi)
+  int nsteps;                 // steps transposed: m_hi, m_hi - 1, ..., m_hi - nsteps + 1 (<= kAdjBlockSteps)
+  const int* probe_node;      // per instance (-1: none)
+  const double* gn;           // dL/dF of segment step m for instance i at gn[(m - 1) n_inst + i]
+  int n_inst;
+  double* grad;               // as AdjArgs
+  int grad_copies;
+  long long grad_stride;
+};
+int adjoint_block_launch(const AdjBlockArgs& a, int grid, cudaStream_t st);
+int adjoint_block_occupancy(int* blocks_per_sm);
 // Advances the auxiliary grids of n one-way sources (FP64 or FP32 state, 2 kTfsfAuxPad
 // values each) by nsteps steps from step *n_done and writes each step's corrections
 // to corr ([source][chunk_stride][kTfsfCorr]).

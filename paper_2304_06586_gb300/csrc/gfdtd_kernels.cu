@@ -66,170 +66,196 @@ int block_shapes(int prec, int* C, int* TB, int* MB, int max) {
 // ------------------------------------------------------------ plain kernel
 //
 // One step of one instance per launch, fields in HBM: the throughput baseline
-// of the batched kernel.  A block of 256 threads stages the old B and D of its
-// 256 cells and a 4-cell halo on each side in shared memory, then forms each
-// intermediate value once: E' at the 259 nodes its B update reads, B' at 258
-// and H' at 257 half nodes, D' at its own 256 nodes (a barrier between the
-// stages).
-// The material comes from one coalesced pass of the whole block over the
-// profile positions and a short search in shared memory per node.
+// of the batched kernel.  Thread t of a block of 256 holds cell k0 - 4 + t:
+// it stages that cell's old B and D in shared memory, forms E' there (cells
+// k0 - 2 .. k0 + 250), then B' and, from its own B', H' (k0 - 2 .. k0 + 249
+// and k0 - 1 .. k0 + 248), then D' (k0 .. k0 + 248, the block's 249 output
+// cells; B' at k0 + 249 serves a probe's average at k0 + 248), a barrier
+// between the three stages, so that each intermediate value is formed once.  The instance record travels in the launch parameters.
+// The material: in one coalesced pass that waits on no other load, the block
+// reads the instance's profile (positions and both coefficient tables), keeps
+// its first kPlainP entries in shared memory and counts, for each of the two
+// levels, the positions left of its first staged cell and those left of its
+// last one; a cell then finds its entry by a binary search between those two
+// counts.  So the field loads and that pass are the only global reads before
+// the stores (entries past kPlainP, in longer profiles, are read from global
+// memory where a search reaches them).
+constexpr int kPlainP = 512;
+constexpr int kPlainThreads = 256, kPlainOut = kPlainThreads - 7;
 
-// The block's profile positions: how many lie at or left of its first staged
-// node at each level (counted by all threads at once, one coalesced pass), and
-// the next kPlainZ positions from the smaller count on, in shared memory, so
-// that each node finds its own count with a short search in shared memory.
-constexpr int kPlainZ = 64;
-
-struct PlainZ {
-  long long z[kPlainZ];   // zq[first .. first + kPlainZ) (FAR_AWAY past the end)
-  int first;              // index of z[0]
-  int cntE, cntH;         // positions at or left of the first staged node (E-side, H-side level)
+template <typename R>
+struct PlainProfile {
+  using V = typename TabOf<R>::V;
+  long long z[kPlainP];
+  V vE[kPlainP], vH[kPlainP];
+  int loE, hiE, loH, hiH;        // counts at the first and at the last staged cell
 };
 
-// Number of profile positions at or left of node k at offset `off`: the block's
-// window in shared memory first, then (past it) a walk in global memory.
-__device__ __forceinline__ int plain_count(const PlainZ& P, const long long* __restrict__ zq, int nbp,
-                                           long long off, int k, int lo) {
-  // positions [lo, first + kPlainZ) are in shared memory; count those <= k
-  int a = lo - P.first, b = kPlainZ;
-  while (a < b) {
-    const int m = (a + b) >> 1;
-    if (node_of(P.z[m], off) <= k) a = m + 1; else b = m;
+template <typename R>
+struct PlainTab {
+  using V = typename TabOf<R>::V;
+  const PlainProfile<R>& P;
+  const long long* __restrict__ zq;
+  const V* __restrict__ tE;
+  const V* __restrict__ tH;
+  __device__ __forceinline__ long long z(int i) const { return i < kPlainP ? P.z[i] : __ldg(zq + i); }
+  __device__ __forceinline__ V v(bool eside, int i) const {
+    if (i < kPlainP) return eside ? P.vE[i] : P.vH[i];
+    return __ldg((eside ? tE : tH) + i);
   }
-  int idx = P.first + a;
-  if (a == kPlainZ)
-    while (idx < nbp && node_of(__ldg(zq + idx), off) <= k) ++idx;
-  return idx;
-}
+  // number of positions at or left of node k, given that it lies in [lo, hi]
+  __device__ __forceinline__ int count(long long off, int k, int lo, int hi) const {
+    while (lo < hi) {
+      const int m = (lo + hi) >> 1;
+      if (node_of(z(m), off) <= k) lo = m + 1; else hi = m;
+    }
+    return lo;
+  }
+};
+
+template <typename R>
+struct PlainShared {
+  R B[kPlainThreads], D[kPlainThreads], E[kPlainThreads], Bn[kPlainThreads], H[kPlainThreads];
+  PlainProfile<R> P;
+};
 
 template <bool MATTER, bool ESIDE, typename R>
-__device__ __forceinline__ void plain_coef(const InstDev& I, const Tables& tb, const PlainZ& P, long long off, int k,
-                                           int lo, R& cx, R& cy) {
-  const long long* __restrict__ zq = tb.zq + I.tab;
-  const auto* __restrict__ tv = TabOf<R>::get(tb, ESIDE) + I.tab;
-  if (I.flags & F_LINEAR) {
-    linear_coef<MATTER, ESIDE>(I, zq, tv, plain_count(P, zq, I.n, off, k, lo), k, off, cx, cy);
+__device__ __forceinline__ void plain_coef(const InstDev& I, const PlainTab<R>& T, long long off, int k,
+                                           int idx, R& cx, R& cy) {
+  if (!(I.flags & F_LINEAR)) {
+    const auto v = T.v(ESIDE, idx);
+    cx = v.x;
+    cy = MATTER ? v.y : coef<R>(I.cb, I.cb32);
     return;
   }
-  const auto v = __ldg(tv + plain_count(P, zq, I.n - 1, off, k, lo));
-  cx = v.x;
-  cy = MATTER ? v.y : coef<R>(I.cb, I.cb32);
+  const int n = I.n;
+  R e, m;
+  if (idx <= 0 || idx >= n) {
+    const auto v = T.v(true, idx <= 0 ? 0 : n - 1);
+    e = v.x;
+    m = v.y;
+  } else {
+    const long long z0 = T.z(idx - 1), z1 = T.z(idx);
+    const long long xi = ((long long)k << 32) - off;
+    const R wgt = (R)(xi - z0) / (R)(z1 - z0);
+    const auto v0 = T.v(true, idx - 1), v1 = T.v(true, idx);
+    e = v0.x + wgt * (v1.x - v0.x);
+    m = v0.y + wgt * (v1.y - v0.y);
+  }
+  const R S = (R)I.S;
+  if (!MATTER) {
+    cx = S / (ESIDE ? e : m);
+    cy = coef<R>(I.cb, I.cb32);
+  } else {
+    const R b = (R)I.beta, g = (R)1 - b * b;
+    const R den = e * m - b * b;
+    cx = S * g * (ESIDE ? m : e) / den;
+    cy = (R)0.5 * S * b * g / den;
+  }
 }
 
 template <bool MATTER, typename T>
-__device__ void plain_block(const PlainArgs<T>& A, const InstDev& I) {
+__device__ void plain_block(const PlainArgs<T>& A, PlainShared<typename Real<T>::type>& sh) {
   using R = typename Real<T>::type;
-  constexpr int NT = 256, H = 4, M = NT + 2 * H;     // staged cells: k0 - 4 .. k0 + 259
-  __shared__ R sB[M], sD[M], sE[M], sBn[M], sH[M];
-  __shared__ PlainZ P;
+  constexpr int NT = kPlainThreads, H = 4;
+  PlainProfile<R>& P = sh.P;
+  const InstDev& I = A.I;
   const int nz = I.nz;
-  const int k0 = blockIdx.x * NT;
+  const int k0 = blockIdx.x * kPlainOut;
+  const int t = threadIdx.x;
+  const int k = k0 - H + t;                // this thread's cell
+  const bool in = k >= 0 && k < nz;
   const bool pos = (I.flags & F_POS) != 0;
   const R a = coef<R>(I.a, I.a32), cc = coef<R>(I.c, I.c32);
   const int sc = *A.s_dev;                 // step within the chunk
   const long long n = *A.n_done + sc + 1;
   const long long offE = I.dq * (2 * n - 1), offH = I.dq * (2 * n) - HALF_CELL;
-  const T* __restrict__ Bi = A.Bin + I.off;
-  const T* __restrict__ Di = A.Din + I.off;
-  auto cell = [&](int j) { return k0 - H + j; };
-  auto in = [&](int k) { return k >= 0 && k < nz; };
+  const PlainTab<R> tab{P, A.tb.zq + I.tab, TabOf<R>::get(A.tb, true) + I.tab, TabOf<R>::get(A.tb, false) + I.tab};
 
-  for (int j = threadIdx.x; j < M; j += NT) {
-    const int k = cell(j);
-    sB[j] = in(k) ? (R)Bi[k] : (R)0;
-    sD[j] = in(k) ? (R)Di[k] : (R)0;
-  }
+  sh.B[t] = in ? (R)A.Bin[I.off + k] : (R)0;
+  sh.D[t] = in ? (R)A.Din[I.off + k] : (R)0;
+  const int nbp = (I.flags & F_LINEAR) ? I.n : I.n - 1;   // positions (the tables hold I.n entries)
   {
-    const long long* __restrict__ zq = A.tb.zq + I.tab;
-    const int nbp = (I.flags & F_LINEAR) ? I.n : I.n - 1;
-    int cE = 0, cH = 0;
-    for (int j0 = 0; j0 < nbp; j0 += NT) {
-      const int jj = j0 + threadIdx.x;
-      bool pE = false, pH = false;
-      if (jj < nbp) {
-        const long long z = __ldg(zq + jj);
-        pE = node_of(z, offE) <= k0 - H;
-        pH = node_of(z, offH) <= k0 - H;
+    const int klo = k0 - H, khi = k0 - H + NT - 1;
+    int loE = 0, hiE = 0, loH = 0, hiH = 0;
+    for (int j0 = 0; j0 < I.n; j0 += NT) {
+      const int jj = j0 + t;
+      bool pl = false, ph = false, ql = false, qh = false;
+      if (jj < I.n && jj < kPlainP) {
+        P.vE[jj] = __ldg(tab.tE + jj);
+        P.vH[jj] = __ldg(tab.tH + jj);
       }
-      cE += __syncthreads_count(pE);
-      cH += __syncthreads_count(pH);
+      if (jj < nbp) {
+        const long long z = __ldg(tab.zq + jj);
+        if (jj < kPlainP) P.z[jj] = z;
+        const int kE = node_of(z, offE), kH = node_of(z, offH);
+        pl = kE <= klo;
+        ph = kE <= khi;
+        ql = kH <= klo;
+        qh = kH <= khi;
+      }
+      loE += __syncthreads_count(pl);
+      hiE += __syncthreads_count(ph);
+      loH += __syncthreads_count(ql);
+      hiH += __syncthreads_count(qh);
     }
-    const int first = min(cE, cH);
-    if (threadIdx.x < kPlainZ) {
-      const int jj = first + threadIdx.x;
-      P.z[threadIdx.x] = jj < nbp ? __ldg(zq + jj) : FAR_AWAY;
-    }
-    if (threadIdx.x == 0) {
-      P.first = first;
-      P.cntE = cE;
-      P.cntH = cH;
+    if (t == 0) {
+      P.loE = loE;
+      P.hiE = hiE;
+      P.loH = loH;
+      P.hiH = hiH;
     }
   }
   __syncthreads();
 
-  // E'^{n-1/2} at cells k0 - 2 .. k0 + 256 (B at level n-1)
-  for (int j = H - 2 + threadIdx.x; j <= H + NT; j += NT) {
-    const int k = cell(j);
+  // E'^{n-1/2} at cells k0 - 2 .. k0 + 250 (B at level n-1)
+  if (t >= 2 && t <= NT - 2) {
     R e = (R)0;
-    if (in(k)) {
+    if (in) {
       R se, cb;
-      plain_coef<MATTER, true>(I, A.tb, P, offE, k, P.cntE, se, cb);
-      const R bs = pos ? sB[j - 1] + sB[j - 2] : sB[j] + sB[j + 1];
-      e = se * sD[j] - cb * bs;
+      plain_coef<MATTER, true>(I, tab, offE, k, tab.count(offE, k, P.loE, P.hiE), se, cb);
+      const R bs = pos ? sh.B[t - 1] + sh.B[t - 2] : sh.B[t] + sh.B[t + 1];
+      e = se * sh.D[t] - cb * bs;
     }
-    sE[j] = e;
+    sh.E[t] = e;
   }
   __syncthreads();
 
-  // B^n at cells k0 - 2 .. k0 + 255 (absorbing layers damp after the update)
-  for (int j = H - 2 + threadIdx.x; j < H + NT; j += NT) {
-    const int k = cell(j);
-    R b = (R)0;
-    if (in(k)) {
-      const R bu = pos ? sB[j - 1] : sB[j + 1];
-      b = a * sB[j] + (cc * bu + (sE[j] - sE[j + 1]));
+  // B^n at cells k0 - 2 .. k0 + 249 (absorbing layers damp after the update), and
+  // from it H'^n at k0 - 1 .. k0 + 248 (D at level n-1/2)
+  if (t >= 2 && t <= NT - 3) {
+    R b = (R)0, h = (R)0;
+    if (in) {
+      const R bu = pos ? sh.B[t - 1] : sh.B[t + 1];
+      b = a * sh.B[t] + (cc * bu + (sh.E[t] - sh.E[t + 1]));
       if (I.abs_w > 0) b *= absorb_factor<R>(I, (R)k + (R)0.5);
+      if (t >= 3 && t <= NT - 4) {
+        R sm, cb;
+        plain_coef<MATTER, false>(I, tab, offH, k, tab.count(offH, k, P.loH, P.hiH), sm, cb);
+        h = sm * b - cb * (sh.D[t] + sh.D[t + 1]);
+      }
+      if (t >= H && t <= NT - 4) A.Bout[I.off + k] = (T)b;
     }
-    sBn[j] = b;
-    if (j >= H && in(k)) A.Bout[I.off + k] = (T)b;
+    sh.Bn[t] = b;
+    sh.H[t] = h;
   }
   __syncthreads();
 
-  // H'^n at cells k0 - 1 .. k0 + 255 (D at level n-1/2)
-  for (int j = H - 1 + threadIdx.x; j < H + NT; j += NT) {
-    const int k = cell(j);
-    R h = (R)0;
-    if (in(k)) {
-      R sm, cb;
-      plain_coef<MATTER, false>(I, A.tb, P, offH, k, P.cntH, sm, cb);
-      h = sm * sBn[j] - cb * (sD[j] + sD[j + 1]);
-    }
-    sH[j] = h;
-  }
-  __syncthreads();
-
-  // D^{n+1/2} at the block's own cells, sources and probes
-  const int j = H + threadIdx.x;
-  const int k = cell(j);
-  if (!in(k)) return;
-  const R du = pos ? sD[j - 1] : sD[j + 1];
-  R d = a * sD[j] + (cc * du + (sH[j - 1] - sH[j]));
+  // D^{n+1/2} at the block's output cells k0 .. k0 + 248, sources and probes
+  if (t < H || t > NT - 4 || !in) return;
+  const R du = pos ? sh.D[t - 1] : sh.D[t + 1];
+  R d = a * sh.D[t] + (cc * du + (sh.H[t - 1] - sh.H[t]));
   if (I.abs_w > 0) d *= absorb_factor<R>(I, (R)k);
-  const double t = (double)(2 * n + 1) * I.S * 0.5;
-  for (int q = 0; q < I.nsrc; ++q) {
-    const SrcDev sd = A.srcs[I.src0 + q];
-    if (sd.node == k) {
-      const double u = t - sd.t0;
-      d += (R)(sd.amp * sin(sd.omega0 * u) * exp(-(u / sd.tau) * (u / sd.tau)));
-    }
-  }
+  for (int q = 0; q < I.nsrc; ++q)   // amplitudes at t_{n+1/2}, formed once per chunk
+    if (A.srcs[I.src0 + q].node == k) d += (R)A.src_amp[(long long)(I.src0 + q) * A.chunk_stride + sc];
   for (int q = 0; q < I.nprb; ++q) {
     if (A.prbs[I.prb0 + q].node == k) {
+      const long long offP = I.dq * (2 * n + 1);
       R se, cb;
-      node_coef<MATTER, true>(I, A.tb, I.dq * (2 * n + 1), k, se, cb);
+      plain_coef<MATTER, true>(I, tab, offP, k, tab.count(offP, k, 0, nbp), se, cb);
       R F = d * se;
       if (MATTER) {
-        const R bbar = pos ? (R)0.5 * (sBn[j - 1] + sBn[j - 2]) : (R)0.5 * (sBn[j] + sBn[j + 1]);
+        const R bbar = pos ? (R)0.5 * (sh.Bn[t - 1] + sh.Bn[t - 2]) : (R)0.5 * (sh.Bn[t] + sh.Bn[t + 1]);
         F += ((R)I.beta * (R)I.S - (R)2 * cb) * bbar;
       }
       A.samples[(long long)(I.prb0 + q) * A.chunk_stride + sc] = (double)(F * (R)I.inv_S);
@@ -239,10 +265,10 @@ __device__ void plain_block(const PlainArgs<T>& A, const InstDev& I) {
 }
 
 template <typename T>
-__global__ void __launch_bounds__(256) plain_kernel(const PlainArgs<T> A) {
-  const InstDev I = A.inst[A.i];
-  if (I.flags & F_MATTER) plain_block<true>(A, I);
-  else plain_block<false>(A, I);
+__global__ void __launch_bounds__(kPlainThreads) plain_kernel(const PlainArgs<T> A) {
+  __shared__ PlainShared<typename Real<T>::type> sh;
+  if (A.I.flags & F_MATTER) plain_block<true>(A, sh);
+  else plain_block<false>(A, sh);
 }
 
 __global__ void plain_tick_kernel(int* s_dev) {
@@ -256,8 +282,7 @@ int plain_tick_launch(int* s_dev, cudaStream_t st) {
 
 template <typename T>
 static int plain_t(const void* args, int nz, cudaStream_t st) {
-  const int bs = 256;
-  plain_kernel<T><<<(nz + bs - 1) / bs, bs, 0, st>>>(*static_cast<const PlainArgs<T>*>(args));
+  plain_kernel<T><<<(nz + kPlainOut - 1) / kPlainOut, kPlainThreads, 0, st>>>(*static_cast<const PlainArgs<T>*>(args));
   return (int)cudaGetLastError();
 }
 
