@@ -728,8 +728,21 @@ def main():
             barrier()
             pms = p0.elapsed_time(p1)
             pv = cells * args.plain_steps / (pms / 1e3) / 1e9
+            # the same launch structure without the arithmetic: what one instance and one
+            # step per launch allow on this batch
+            sim.plain_floor(1)
+            barrier()
+            p0.record(stream)
+            sim.plain_floor(args.plain_steps)
+            p1.record(stream)
+            barrier()
+            fv = cells * args.plain_steps / (p0.elapsed_time(p1) / 1e3) / 1e9
             plain = {"value": pv, "unit": "Gcell-updates/s", "steps": args.plain_steps,
-                     "batched_over_plain": value / world / pv}
+                     "batched_over_plain": value / world / pv,
+                     "structure_floor": {"value": fv, "unit": "Gcell-updates/s", "plain_frac": pv / fv,
+                                         "note": "gfdtd_plain_floor: the plain path's launches (one per "
+                                                 "instance and step, same grids, in a CUDA graph) reading "
+                                                 "and writing back B and D without the arithmetic"}}
         sim.close()
         sweeps = None if args.no_sweeps else sweep_measurements(torch, gb, stream)
         adjoint = None if args.no_sweeps else adjoint_measurement(gb)

@@ -259,7 +259,12 @@ gfdtd_status gfdtd_stability(double S, double beta, double eps_r, double mu_r,
  * 8x16x4, 8x24x6); E_UNSUPPORTED if the shape is not built.  0, 0, 0 selects autotuning at the next step: every
  * built shape is timed on the batch (two interleaved passes of one warm-up
  * and three timed time blocks that follow one another in time) and the
- * fastest kept. */
+ * fastest kept.  Tiles outside the fast kernel's reach (moving matter,
+ * piecewise-linear or narrow-layer profiles, domain ends, one-way sources)
+ * either all run in the general kernel, or first pass through a lean kernel
+ * that steps those whose window sees one material value during the launch
+ * and queues the rest for the general kernel (the uniform-tile split); a
+ * shape set here takes the split, autotuning times both ways per shape. */
 gfdtd_status gfdtd_set_tuning(gfdtd_ctx* ctx, int cells_per_lane, int time_block, int blocks_per_sm);
 
 typedef struct {
@@ -313,6 +318,18 @@ typedef struct {
 } gfdtd_kernel_times;
 
 gfdtd_status gfdtd_profile_kernels(gfdtd_ctx* ctx, int64_t n_steps, gfdtd_kernel_times* out);
+
+/* Measurement hook (no counterpart in the paper): the launch structure of
+ * gfdtd_step_plain without its arithmetic, the throughput bound of the
+ * one-instance, one-step-per-launch form.  Enqueues n_steps replays of a CUDA
+ * graph holding, in instance order on the context's stream, one launch per
+ * instance with the plain kernel's grid, in which every thread reads its
+ * cell's B and D and the block's output cells are written back unchanged
+ * (16 bytes per cell in FP32, the plain kernel's algorithmic traffic), plus
+ * the plain path's per-step counter launch.  Fields, probes and the step count
+ * are left as they were.  Asynchronous: time it with events on the context's
+ * stream.  E_UNSUPPORTED where gfdtd_step_plain is. */
+gfdtd_status gfdtd_plain_floor(gfdtd_ctx* ctx, int64_t n_steps);
 
 /* ---- batched parameter sweeps (context-free, GPU, FP64) ----
  *

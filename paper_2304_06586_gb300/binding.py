@@ -57,6 +57,7 @@ SIGNATURES = {
     "gfdtd_add_probe": (C.c_int, [C.c_void_p, C.c_int, C.c_int64, C.c_int, _dp, C.POINTER(C.c_int)]),
     "gfdtd_step": (C.c_int, [C.c_void_p, C.c_int64]),
     "gfdtd_step_plain": (C.c_int, [C.c_void_p, C.c_int64]),
+    "gfdtd_plain_floor": (C.c_int, [C.c_void_p, C.c_int64]),
     "gfdtd_read_fields": (C.c_int, [C.c_void_p, C.c_int, C.c_int, _dp, C.c_int64]),
     "gfdtd_write_fields": (C.c_int, [C.c_void_p, C.c_int, C.c_int, _dp, C.c_int64]),
     "gfdtd_read_state": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_int64]),
@@ -314,6 +315,11 @@ class Simulation:
 
     def step_plain(self, n):
         self._check(self._L.gfdtd_step_plain(self._h, int(n)), "step_plain")
+
+    def plain_floor(self, n):
+        """The plain path's launch structure without its arithmetic (gfdtd_plain_floor):
+        n steps' worth of launches that read and write back B and D; the state is unchanged."""
+        self._check(self._L.gfdtd_plain_floor(self._h, int(n)), "plain_floor")
 
     def read_fields(self, inst, which=FIELD_D):
         out = np.empty(int(self.nz[inst]))

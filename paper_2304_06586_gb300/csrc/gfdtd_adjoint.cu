@@ -4,8 +4,8 @@
 // (B^n, D^{n+1/2}) (Sec. 4 with Table 1; the source adds a constant):
 //   E'_k = se_k D_k - cb Bsum_k,   B'_j = a B_j + c B_up(j) + E'_j - E'_{j+1},
 //   H'_j = sm_j B'_j - cb (D_j + D_{j+1}),   D'_k = a D_k + c D_up(k) + H'_{k-1} - H'_k,
-// with E' = S E*, H' = S H*.  adjoint_step applies the transpose, gathered per
-// cell, to the adjoint fields (lB', lD') of (B^n, D^{n+1/2}):
+// with E' = S E*, H' = S H*.  The reverse sweep applies the transpose, gathered
+// per cell, to the adjoint fields (lB', lD') of (B^n, D^{n+1/2}):
 //   lH_j  = lD'_{j+1} - lD'_j,          lBt_j = lB'_j + sm_j lH_j,
 //   lE_k  = lBt_k - lBt_{k-1},
 //   lD_k  = a lD'_k + c lD'_dn(k) - cb (lH_k + lH_{k-1}) + se_k lE_k,
@@ -21,8 +21,6 @@
 #include "gfdtd_block.cuh"
 
 namespace gfdtd {
-
-
 
 // Weights of eps at moving coordinate xi on the profile values: (i0, w0), (i1, w1).
 template <typename W>
@@ -57,211 +55,10 @@ __device__ __forceinline__ int positions_at_or_left(const long long* __restrict_
   return lo;
 }
 
-// The same count one cell further on, from the previous cell's count `idx`:
-// a short walk, else a fresh search.
-__device__ __forceinline__ int advance_positions(const long long* __restrict__ zq, int np, long long xi, int idx) {
-  for (int w = 0; w < 4; ++w) {
-    if (idx >= np || __ldg(zq + idx) > xi) return idx;
-    ++idx;
-  }
-  return positions_at_or_left(zq, np, xi);
-}
-
 // A non-negative 64-bit integer as FP32 from its two 32-bit halves (two 32-bit
 // conversions and one FMA instead of a 64-bit conversion).
 __device__ __forceinline__ float i64_to_f32(long long x) {
   return fmaf((float)(int)(x >> 32), 4294967296.0f, (float)(unsigned)x);
-}
-
-constexpr int kAdjThreads = 256;
-constexpr int kAdjCPT = 4;                           // consecutive cells per thread
-static_assert(kAdjThreads * kAdjCPT == kAdjTileCells, "adjoint tile size");
-constexpr int kAdjKeys = 1024;                       // profile values one block reduces in shared memory
-
-// One block transposes the step for kAdjTileCells consecutive cells of one
-// instance, four per thread, in FP32 like the forward step.  The material at
-// level n-1/2 comes from one position search per thread and a walk to its
-// next cells.  The permittivity gradient is merged per thread over equal
-// profile values (a warp of one value sums with shuffles), then per block in
-// shared memory, and added to the FP64 gradient with one atomic per profile
-// value per block.  FP64 arithmetic is kept out of the per-cell work: GB300's
-// FP64 pipe is narrow.
-__global__ void __launch_bounds__(kAdjThreads, 4) adjoint_step_kernel(const AdjArgs A) {
-  // cells x0 - 2 .. x0 + kAdjTileCells + 5, zero outside [0, nz)
-  __shared__ __align__(16) float s_lb[kAdjTileCells + 8];
-  __shared__ __align__(16) float s_ld[kAdjTileCells + 8];
-  __shared__ float s_g[kAdjKeys];
-  __shared__ int s_key[2];
-  const int2 tl = A.tiles[blockIdx.x];
-  const InstDev I = A.inst[tl.x];
-  const int x0 = tl.y, nz = I.nz, tid = threadIdx.x;
-  const float* __restrict__ lBn = A.lBn + I.off;
-  const float* __restrict__ lDn = A.lDn + I.off;
-  for (int i = tid; i < kAdjTileCells + 8; i += kAdjThreads) {
-    const int j = x0 - 2 + i;
-    const bool in = j >= 0 && j < nz;
-    s_lb[i] = in ? lBn[j] : 0.0f;
-    s_ld[i] = in ? lDn[j] : 0.0f;
-  }
-  for (int i = tid; i < kAdjKeys; i += kAdjThreads) s_g[i] = 0.0f;
-  const int k0 = x0 + kAdjCPT * tid;
-  const int nvalid = max(0, min(kAdjCPT, nz - k0));
-  const bool pos = (I.flags & F_POS) != 0;
-  const bool lin = (I.flags & F_LINEAR) != 0;
-  const float a = I.a32, c = I.c32, cb = I.cb32, inv_S = (float)I.inv_S, S32 = (float)I.S;
-  const long long n = A.n;
-  const long long offH = I.dq * (2 * n) - HALF_CELL, offE = I.dq * (2 * n - 1);
-  const bool mu_const = (I.flags & F_MU_CONST) != 0;
-  // global loads that need no staged value are issued before the barrier, so
-  // that their latency overlaps the staging: the first cell's position count
-  // and D^{n-1/2} of the thread's cells
-  const long long* __restrict__ zq = A.tb.zq + I.tab;
-  const int np = lin ? I.n : I.n - 1;          // profile positions
-  long long xi = ((long long)k0 << 32) - offE;
-  int idx = 0;
-  float Dold[kAdjCPT] = {0.0f, 0.0f, 0.0f, 0.0f};
-  if (nvalid > 0) {
-    idx = positions_at_or_left(zq, np, xi);
-    const float4 d = *reinterpret_cast<const float4*>(A.Dold + I.off + k0);   // padded to 32 cells
-    Dold[0] = d.x; Dold[1] = d.y; Dold[2] = d.z; Dold[3] = d.w;
-  }
-  __syncthreads();
-
-  int key0[kAdjCPT], key1[kAdjCPT];
-  float g0[kAdjCPT], g1[kAdjCPT];
-  if (nvalid > 0) {
-    // adjoint fields at cells k0 - 2 + q (LD up to q = 8)
-    float LB[8], LD[9];
-    {
-      const float4 b0 = *reinterpret_cast<const float4*>(s_lb + kAdjCPT * tid);
-      const float4 b1 = *reinterpret_cast<const float4*>(s_lb + kAdjCPT * tid + 4);
-      const float4 d0 = *reinterpret_cast<const float4*>(s_ld + kAdjCPT * tid);
-      const float4 d1 = *reinterpret_cast<const float4*>(s_ld + kAdjCPT * tid + 4);
-      LB[0] = b0.x; LB[1] = b0.y; LB[2] = b0.z; LB[3] = b0.w; LB[4] = b1.x; LB[5] = b1.y; LB[6] = b1.z; LB[7] = b1.w;
-      LD[0] = d0.x; LD[1] = d0.y; LD[2] = d0.z; LD[3] = d0.w; LD[4] = d1.x; LD[5] = d1.y; LD[6] = d1.z; LD[7] = d1.w;
-      LD[8] = s_ld[kAdjCPT * tid + 8];
-    }
-    // lH_j = lD'_{j+1} - lD'_j and lBt_j = lB'_j + sm_j lH_j for j = k0 - 2 + q
-    float lH[8], t[8];
-#pragma unroll
-    for (int q = 0; q < 8; ++q) {
-      const int j = k0 - 2 + q;
-      const bool in = j >= 0 && j < nz;
-      float sm = I.sm32;
-      if (!mu_const && in) {
-        float y;
-        node_coef<false, false>(I, A.tb, offH, j, sm, y);
-      }
-      lH[q] = in ? LD[q + 1] - LD[q] : 0.0f;
-      t[q] = in ? LB[q] + sm * lH[q] : 0.0f;
-    }
-    // material at level n-1/2 of the four cells
-    const float2* __restrict__ tv = A.tb.tabE32 + I.tab;
-    float oD[kAdjCPT], oB[kAdjCPT];
-#pragma unroll
-    for (int q = 0; q < kAdjCPT; ++q) {
-      if (q > 0) {
-        xi += 1LL << 32;
-        idx = advance_positions(zq, np, xi, idx);
-      }
-      float se, w1 = 0.0f;
-      if (lin) {
-        float e;
-        if (idx <= 0) { e = __ldg(tv).x; key0[q] = key1[q] = 0; }
-        else if (idx >= np) { e = __ldg(tv + np - 1).x; key0[q] = key1[q] = np - 1; }
-        else {
-          const long long z0 = __ldg(zq + idx - 1), z1 = __ldg(zq + idx);
-          w1 = i64_to_f32(xi - z0) / i64_to_f32(z1 - z0);
-          const float e0 = __ldg(tv + idx - 1).x, e1 = __ldg(tv + idx).x;
-          e = e0 + w1 * (e1 - e0);
-          key0[q] = idx - 1;
-          key1[q] = idx;
-        }
-        se = S32 / e;
-      } else {
-        se = __ldg(tv + idx).x;
-        key0[q] = key1[q] = idx;
-      }
-      const int k = k0 + q, p = q + 2;
-      const float lEk = t[p] - t[p - 1];
-      if (pos) {
-        const float lE1 = k + 1 < nz ? t[p + 1] - t[p] : 0.0f;
-        const float lE2 = k + 2 < nz ? t[p + 2] - t[p + 1] : 0.0f;
-        oD[q] = a * LD[p] + c * LD[p + 1] - cb * (lH[p] + lH[p - 1]) + se * lEk;
-        oB[q] = a * t[p] + c * t[p + 1] - cb * (lE1 + lE2);
-      } else {
-        const float lEm1 = k >= 1 ? t[p - 1] - t[p - 2] : 0.0f;
-        oD[q] = a * LD[p] + c * LD[p - 1] - cb * (lH[p] + lH[p - 1]) + se * lEk;
-        oB[q] = a * t[p] + c * t[p - 1] - cb * (lEk + lEm1);
-      }
-      // dL/deps_k = lE_k (-S D_k / eps_k^2) = lE_k (-se^2 D_k / S)
-      const float gE = q < nvalid ? lEk * (-se * se * Dold[q] * inv_S) : 0.0f;
-      g0[q] = gE * (1.0f - w1);
-      g1[q] = gE * w1;
-    }
-    float* oLD = A.lD + I.off + k0;
-    float* oLB = A.lB + I.off + k0;
-    if (nvalid == kAdjCPT) {
-      *reinterpret_cast<float4*>(oLD) = make_float4(oD[0], oD[1], oD[2], oD[3]);
-      *reinterpret_cast<float4*>(oLB) = make_float4(oB[0], oB[1], oB[2], oB[3]);
-    } else {
-#pragma unroll
-      for (int q = 0; q < kAdjCPT; ++q)
-        if (q < nvalid) { oLD[q] = oD[q]; oLB[q] = oB[q]; }
-    }
-    // keys grow with k: the block's first cell holds its smallest, its last valid cell its largest
-    if (tid == 0) s_key[0] = key0[0];
-    const int klast = min(x0 + kAdjTileCells, nz) - 1;
-#pragma unroll
-    for (int q = 0; q < kAdjCPT; ++q)
-      if (k0 + q == klast) s_key[1] = key1[q];
-  }
-  __syncthreads();
-  const int kmin = s_key[0], span = s_key[1] - kmin + 1;
-  const bool in_smem = span <= kAdjKeys;      // uniform over the block
-  // (blocks add into different copies of the gradient, so that the many blocks of one
-  // uniform region do not all queue on the same profile value's atomics)
-  double* grad = A.grad + (size_t)(blockIdx.x % A.grad_copies) * A.grad_stride + I.tab;
-  auto add = [&](int key, float v) {
-    if (v == 0.0f) return;
-    if (in_smem) atomicAdd(&s_g[key - kmin], v);
-    else atomicAdd(grad + key, (double)v);
-  };
-  // a warp whose cells all map to one profile value sums with shuffles
-  const int lo = nvalid > 0 ? key0[0] : INT_MAX;
-  int hi = INT_MIN;
-#pragma unroll
-  for (int q = 0; q < kAdjCPT; ++q)
-    if (q < nvalid) hi = key1[q];
-  const int wlo = __reduce_min_sync(FULL, lo), whi = __reduce_max_sync(FULL, hi);
-  if (wlo == whi) {
-    float v = 0.0f;
-#pragma unroll
-    for (int q = 0; q < kAdjCPT; ++q)
-      if (q < nvalid) v += g0[q] + g1[q];
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(FULL, v, o);
-    if ((tid & 31) == 0) add(wlo, v);
-  } else if (nvalid > 0) {
-    // contributions in the order key0[0], key1[0], key0[1], ...: runs of one key merge
-    int ck = key0[0];
-    float acc = 0.0f;
-#pragma unroll
-    for (int q = 0; q < kAdjCPT; ++q) {
-      if (q < nvalid) {
-        if (key0[q] != ck) { add(ck, acc); ck = key0[q]; acc = 0.0f; }
-        acc += g0[q];
-        if (key1[q] != ck) { add(ck, acc); ck = key1[q]; acc = 0.0f; }
-        acc += g1[q];
-      }
-    }
-    add(ck, acc);
-  }
-  if (in_smem) {
-    __syncthreads();
-    for (int i = tid; i < span; i += kAdjThreads)
-      if (s_g[i] != 0.0f) atomicAdd(grad + kmin + i, (double)s_g[i]);
-  }
 }
 
 // ------------------------------------------------ time-blocked reverse steps
@@ -553,31 +350,6 @@ int adjoint_block_occupancy(int* blocks_per_sm) {
   return (int)cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, adjoint_block_kernel, 128, 0);
 }
 
-// The probe term of step n: F_n = D^{n+1/2}_p se_p / S = D_p / eps_p (level
-// n+1/2) with dL/dF_n = g[inst]; adds g se_p / S to lD at the probe node and
-// g dF/deps = g (-D_p / eps_p^2) to dL/deps.  One thread per instance.
-
-
-__global__ void probe_adjoint_kernel(const ProbeAdjArgs A) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= A.n_inst) return;
-  const InstDev I = A.inst[i];
-  const int kp = A.probe_node[i];
-  const double g = A.gn[i];
-  if (kp < 0 || g == 0.0) return;
-  const long long off = I.dq * (2 * A.n + 1);
-  double se, cb;
-  node_coef<false, true>(I, A.tb, off, kp, se, cb);
-  A.lD[I.off + kp] += (float)(g * se / I.S);
-  // F = D / eps: dF/deps = -D / eps^2 = -D se^2 / S^2
-  const double gE = g * (-(double)A.Dnew[I.off + kp] * se * se / (I.S * I.S));
-  int i0, i1;
-  double w0, w1;
-  eps_weights(I, A.tb.zq + I.tab, ((long long)kp << 32) - off, i0, w0, i1, w1);
-  atomicAdd(A.grad + I.tab + i0, gE * w0);
-  if (I.flags & F_LINEAR) atomicAdd(A.grad + I.tab + i1, gE * w1);
-}
-
 // dL/dF_n per instance for one segment: 2 S sum_f (Re X_f cos(w t) + Im X_f sin(w t)).
 
 
@@ -597,11 +369,6 @@ __global__ void loss_source_kernel(const SourceAdjArgs A) {
   A.gn[(long long)s * A.n_inst + i] = 2.0 * A.S * g;
 }
 
-int adjoint_step_launch(const AdjArgs& a, cudaStream_t st) {
-  adjoint_step_kernel<<<a.n_tiles, kAdjThreads, 0, st>>>(a);
-  return (int)cudaGetLastError();
-}
-
 __global__ void sum_copies_kernel(const double* __restrict__ copies, long long n_copies, long long stride,
                                   long long n, double* __restrict__ out) {
   const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -615,11 +382,6 @@ int sum_copies_launch(const double* copies, long long n_copies, long long stride
                       cudaStream_t st) {
   if (n == 0) return 0;
   sum_copies_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(copies, n_copies, stride, n, out);
-  return (int)cudaGetLastError();
-}
-
-int probe_adjoint_launch(const ProbeAdjArgs& a, cudaStream_t st) {
-  probe_adjoint_kernel<<<(a.n_inst + 127) / 128, 128, 0, st>>>(a);
   return (int)cudaGetLastError();
 }
 

@@ -119,6 +119,14 @@ struct gfdtd_ctx {
   long long valid_cells[3] = {0, 0, 0}; // exact output cells of each list's tiles per step
   int n_fast_damped = 0;                // the last ones of the fast list reach absorbing layers
   int grid[3] = {0, 0, 0};
+  // uniform-tile queues of the general lists: counters (entries, warps done) of queues
+  // 0, 1 (lists 0, 1 in gfdtd_step) and 2, 3 (lists 0, 2 in the adjoint's recomputation),
+  // then the queues themselves
+  DevBuf d_queue;
+  int queue_off[4] = {0, 0, 0, 0};
+  int ugrid[3] = {0, 0, 0};            // uniform_kernel grid per list (the context's precision)
+  int ugrid_f32[3] = {0, 0, 0};        // the same in FP32 (the adjoint's recomputation)
+  bool split = true;                   // general lists: uniform_kernel first (autotuned)
   int num_sms = 0;
 
   // adjoint work buffers (allocated on first use)
@@ -374,12 +382,41 @@ static gfdtd_status set_tiles(gfdtd_ctx* c, int C, int TB, int MB) {
     const int want = (c->n_tiles[k] + (kBlock / 32) - 1) / (kBlock / 32);
     c->grid[k] = std::max(1, std::min(c->num_sms * nb, want));
   }
+  // uniform-tile queues (int entries): 16 counters, then lists 0, 1 and, for the
+  // adjoint's recomputation, lists 0 and 2
+  {
+    const int sizes[4] = {c->n_tiles[0], c->n_tiles[1], c->n_tiles[0], c->n_tiles[2]};
+    int off = 16;
+    for (int q = 0; q < 4; ++q) {
+      c->queue_off[q] = off;
+      off += (sizes[q] + 3) / 4 * 4;
+    }
+    if ((s = dalloc(c, c->d_queue, (size_t)off * sizeof(int)))) return s;
+    CK(c, cudaMemsetAsync(c->d_queue.p, 0, (size_t)off * sizeof(int), c->stream));
+    for (int k = 0; k < 3; ++k) {
+      c->ugrid[k] = c->ugrid_f32[k] = 0;
+      const int want = std::max(1, (c->n_tiles[k] + (kBlock / 32) - 1) / (kBlock / 32));
+      int nb = 0;
+      if (c->prec != GFDTD_F32_KAHAN) {
+        CKI(c, block_occupancy(c->prec, 4, C, TB, MB, kBlock, &nb));
+        c->ugrid[k] = std::max(1, std::min(c->num_sms * std::max(nb, 1), want));
+      }
+      if (c->prec == GFDTD_F32 || c->prec == GFDTD_F32_KAHAN) {
+        CKI(c, block_occupancy(GFDTD_F32, 4, C, TB, MB, kBlock, &nb));
+        c->ugrid_f32[k] = std::max(1, std::min(c->num_sms * std::max(nb, 1), want));
+      }
+    }
+  }
   c->C = C;
   c->TB = TB;
   c->MB = MB;
   drop_graphs(c);
   return GFDTD_OK;
 }
+
+// Queue q of the uniform-tile split (its counters and entries).
+static int* queue_counts(gfdtd_ctx* c, int q) { return (int*)c->d_queue.p + 2 * q; }
+static int* queue_entries(gfdtd_ctx* c, int q) { return (int*)c->d_queue.p + c->queue_off[q]; }
 
 static gfdtd_status finalize(gfdtd_ctx* c) {
   if (!c->dirty) return GFDTD_OK;
@@ -581,6 +618,16 @@ static gfdtd_status enqueue_block(gfdtd_ctx* c, cudaStream_t st, int from, int s
     a.nsteps = nsteps;
     a.record = record ? 1 : 0;
     a.stall = c->stall;
+    a.queue = nullptr;
+    a.qcount = nullptr;
+    if (k < 2 && c->split && c->prec != GFDTD_F32_KAHAN) {
+      // tiles that see one material value over the launch step in uniform_kernel, the others
+      // are queued for the general kernel
+      a.queue = queue_entries(c, k);
+      a.qcount = queue_counts(c, k);
+      CKI(c, block_launch(c->prec, 4, c->C, c->TB, c->MB, &a, c->ugrid[k], kBlock, st));
+      ++c->launches;
+    }
     if (k == 2 && c->n_fast_damped > 0) {
       // the tiles that reach an absorbing layer, at the end of the list, get their own launch
       const int nd = c->n_fast_damped, nn = c->n_tiles[2] - nd;
@@ -683,7 +730,8 @@ static gfdtd_status run_chunk(gfdtd_ctx* c, int nsteps) {
     it = c->graphs.emplace(key, ex).first;
   }
   CK(c, cudaGraphLaunch(it->second, c->stream));
-  const int kinds = (c->n_tiles[0] > 0) + (c->n_tiles[1] > 0) + (c->n_tiles[2] > c->n_fast_damped) +
+  const int split = c->split && c->prec != GFDTD_F32_KAHAN ? 2 : 1;   // uniform_kernel + block_kernel per general list
+  const int kinds = split * ((c->n_tiles[0] > 0) + (c->n_tiles[1] > 0)) + (c->n_tiles[2] > c->n_fast_damped) +
                     (c->n_fast_damped > 0);
   c->launches += (long long)m * kinds + (c->n_src > 0) + (c->n_tfsf > 0) + (c->n_bins > 0) +
                  (c->n_watchblk > 0) + 1;
@@ -697,6 +745,26 @@ static gfdtd_status run_chunk(gfdtd_ctx* c, int nsteps) {
 // launches of a shape follow one another in time (s0 advances by a time block)
 // so that, as in a real run, each finds the boundary trackers the previous one
 // saved; set_tiles resets them for the shape finally kept.
+// Device time per step of the current tiles over a few time blocks (reads the
+// current buffer, writes the other, records nothing; the blocks follow one
+// another in time so that each finds the boundary trackers the previous one saved).
+static gfdtd_status time_blocks(gfdtd_ctx* c, int TB, cudaEvent_t e0, cudaEvent_t e1, double* per_step) {
+  gfdtd_status s = enqueue_block(c, c->stream, c->cur, 0, TB, false, false, -1, true);
+  if (s) return s;
+  CK(c, cudaEventRecord(e0, c->stream));
+  const int reps = 3;
+  for (int r = 1; r <= reps; ++r) {
+    s = enqueue_block(c, c->stream, c->cur, r * TB, TB, false, false, -1, true);
+    if (s) return s;
+  }
+  CK(c, cudaEventRecord(e1, c->stream));
+  CK(c, cudaEventSynchronize(e1));
+  float ms = 0.f;
+  CK(c, cudaEventElapsedTime(&ms, e0, e1));
+  *per_step = (double)ms / (reps * TB);
+  return GFDTD_OK;
+}
+
 static gfdtd_status autotune(gfdtd_ctx* c) {
   int Cs[16], TBs[16], MBs[16];
   const int n = block_shapes(c->prec, Cs, TBs, MBs, 16);
@@ -707,32 +775,32 @@ static gfdtd_status autotune(gfdtd_ctx* c) {
   CK(c, cudaEventCreate(&e1));
   // two passes over the candidates, each candidate keeping its faster pass, so
   // that a clock or cache transient during one timing does not decide alone
-  double per_step[16];
-  for (int i = 0; i < n; ++i) per_step[i] = 1e300;
+  // candidates: every shape, with and without the uniform-tile split of the general lists
+  // where there are general tiles to split
+  double per_step[16][2];
+  bool general = false;
+  for (int i = 0; i < n; ++i) per_step[i][0] = per_step[i][1] = 1e300;
   for (int pass = 0; pass < 2; ++pass) {
     for (int i = 0; i < n; ++i) {
       gfdtd_status s = set_tiles(c, Cs[i], TBs[i], MBs[i]);
       if (s) return s;
-      s = enqueue_block(c, c->stream, c->cur, 0, TBs[i], false, false, -1, true);
-      if (s) return s;
-      CK(c, cudaEventRecord(e0, c->stream));
-      const int reps = 3;
-      for (int r = 1; r <= reps; ++r) {
-        s = enqueue_block(c, c->stream, c->cur, r * TBs[i], TBs[i], false, false, -1, true);
+      general = (c->n_tiles[0] + c->n_tiles[1] > 0) && c->prec != GFDTD_F32_KAHAN;
+      for (int sp = 0; sp < (general ? 2 : 1); ++sp) {
+        c->split = sp == 0;
+        double t = 0.0;
+        s = time_blocks(c, TBs[i], e0, e1, &t);
         if (s) return s;
+        per_step[i][sp] = std::min(per_step[i][sp], t);
       }
-      CK(c, cudaEventRecord(e1, c->stream));
-      CK(c, cudaEventSynchronize(e1));
-      float ms = 0.f;
-      CK(c, cudaEventElapsedTime(&ms, e0, e1));
-      per_step[i] = std::min(per_step[i], (double)ms / (reps * TBs[i]));
     }
   }
-  int bi = 0;
-  for (int i = 1; i < n; ++i)
-    if (per_step[i] < per_step[bi]) bi = i;
+  int bi = 0, bs = 0;
+  for (int i = 0; i < n; ++i)
+    for (int sp = 0; sp < 2; ++sp)
+      if (per_step[i][sp] < per_step[bi][bs]) { bi = i; bs = sp; }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
+  c->split = bs == 0;
   return set_tiles(c, Cs[bi], TBs[bi], MBs[bi]);
 }
 
@@ -788,6 +856,14 @@ static gfdtd_status enqueue_segment_block(gfdtd_ctx* c, const void* Bin, void* B
     a.record = 0;
     a.dseg = (float*)dseg;
     a.dseg_stride = (long long)(fb / sizeof(float));
+    if (c->split) {
+      // uniform tiles first (queue 2 or 3), the rest in the general kernel
+      const int q = k == 0 ? 2 : 3;
+      a.queue = queue_entries(c, q);
+      a.qcount = queue_counts(c, q);
+      CKI(c, block_launch(GFDTD_F32, 4, c->C, c->TB, c->MB, &a, c->ugrid_f32[k], kBlock, st));
+      ++c->launches;
+    }
     const int grid = std::min(c->grid[0] > 0 ? c->grid[0] : c->num_sms, (a.n_tiles + 3) / 4);
     CKI(c, block_launch(GFDTD_F32, 0, c->C, c->TB, c->MB, &a, std::max(grid, 1), kBlock, st));
     ++c->launches;
@@ -1456,6 +1532,49 @@ gfdtd_status gfdtd_step_plain(gfdtd_ctx* c, int64_t n_steps) {
   return GFDTD_OK;
 }
 
+gfdtd_status gfdtd_plain_floor(gfdtd_ctx* c, int64_t n_steps) {
+  if (!c) return GFDTD_E_ARG;
+  if (c->prec == GFDTD_F32_KAHAN)
+    return fail(c, GFDTD_E_UNSUPPORTED, "the plain kernel has no compensated tier");
+  if (n_steps < 0) return fail(c, GFDTD_E_ARG, "n_steps < 0");
+  gfdtd_status s = finalize(c);
+  if (s) return s;
+  if (c->n_tfsf > 0) return fail(c, GFDTD_E_UNSUPPORTED, "one-way sources run in gfdtd_step only");
+  if (!c->d_plain_s.p) {
+    s = dalloc(c, c->d_plain_s, 16);
+    if (s) return s;
+  }
+  const auto key = std::make_pair(-2, c->cur);
+  auto it = c->graphs.find(key);
+  if (it == c->graphs.end()) {
+    cudaGraph_t g = nullptr;
+    CK(c, cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal));
+    gfdtd_status cs = GFDTD_OK;
+    for (int i = 0; i < c->n_inst && !cs; ++i) {
+      char* Bp = (char*)c->B[c->cur].p + (size_t)c->off[i] * c->eb;
+      char* Dp = (char*)c->D[c->cur].p + (size_t)c->off[i] * c->eb;
+      if (plain_floor_launch(c->eb, Bp, Dp, (int)c->nz[i], (const int*)c->d_plain_s.p, c->cap_stream) != 0)
+        cs = fail(c, GFDTD_E_CUDA, "floor launch failed");
+    }
+    if (!cs && plain_tick_launch((int*)c->d_plain_s.p, c->cap_stream) != 0)
+      cs = fail(c, GFDTD_E_CUDA, "step counter launch failed");
+    cudaError_t e = cudaStreamEndCapture(c->cap_stream, &g);
+    if (cs) { if (g) cudaGraphDestroy(g); return cs; }
+    CK(c, e);
+    cudaGraphExec_t ex = nullptr;
+    e = cudaGraphInstantiate(&ex, g, 0);
+    cudaGraphDestroy(g);
+    CK(c, e);
+    it = c->graphs.emplace(key, ex).first;
+  }
+  CK(c, cudaMemsetAsync(c->d_plain_s.p, 0, sizeof(int), c->stream));
+  for (int64_t st = 0; st < n_steps; ++st) {
+    CK(c, cudaGraphLaunch(it->second, c->stream));
+    c->launches += c->n_inst + 1;
+  }
+  return GFDTD_OK;
+}
+
 gfdtd_status gfdtd_read_fields(gfdtd_ctx* c, int inst, gfdtd_field which, double* dst, int64_t n) {
   gfdtd_status s = check_inst(c, inst);
   if (s) return s;
@@ -1575,6 +1694,7 @@ gfdtd_status gfdtd_set_tuning(gfdtd_ctx* c, int cells_per_lane, int time_block, 
         (blocks_per_sm == 0 || MBs[i] == blocks_per_sm)) {
       gfdtd_status s = finalize(c);
       if (s) return s;
+      c->split = true;
       return set_tiles(c, Cs[i], TBs[i], MBs[i]);
     }
   }
@@ -1648,7 +1768,7 @@ void gfdtd_destroy(gfdtd_ctx* c) {
                     &c->d_wB[1][0], &c->d_wB[1][1], &c->d_amp2[0], &c->d_amp2[1], &c->d_lB[0],
                     &c->d_lB[1], &c->d_lD[0], &c->d_lD[1], &c->d_grad, &c->d_gn, &c->d_adjn[0], &c->d_adjn[1],
                     &c->d_Xre, &c->d_Xim, &c->d_bin0, &c->d_pnode, &c->d_acc0_re, &c->d_acc0_im,
-                    &c->d_adj_tiles, &c->d_tfsf, &c->d_tfaux, &c->d_tfcorr, &c->d_watch, &c->d_watchblk, &c->d_plain_s};
+                    &c->d_adj_tiles, &c->d_tfsf, &c->d_tfaux, &c->d_tfcorr, &c->d_watch, &c->d_watchblk, &c->d_plain_s, &c->d_queue};
   for (DevBuf* b : bufs) dfree(c, *b);
   if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
   delete c;

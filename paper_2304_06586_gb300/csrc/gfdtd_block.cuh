@@ -388,6 +388,37 @@ __device__ __forceinline__ void kahan_add(R& x, R& cmp, R d) {
   x = t;
 }
 
+// Which sides of a window [base, base + span) see a single material value over
+// a launch of nsteps steps from n0 (E side: integer nodes at half levels
+// 2n - 1; H side: half nodes at levels 2n): a uniform side of the instance, or
+// a window that lies, over the whole launch, before the first profile position
+// or after the last one (positions move monotonically, so the launch's first
+// and last levels decide), with the table entry of that value in rE / rH.
+// (Layers tables hold the coefficients themselves; a linear moving-matter
+// profile would need them formed from (eps, mu), so it is never uniform here.)
+__device__ __forceinline__ void uniform_sides(const InstDev& I, const Tables& tb, int base, int span, long long n0,
+                                              int nsteps, bool& eps_const, bool& mu_const, int& rE, int& rH) {
+  eps_const = (I.flags & F_EPS_CONST) != 0;
+  mu_const = (I.flags & F_MU_CONST) != 0;
+  rE = rH = 0;
+  const bool lin = (I.flags & F_LINEAR) != 0;
+  const int np = lin ? I.n : I.n - 1;                  // profile positions
+  if ((!(I.flags & F_MATTER) || !lin) && np > 0 && (!eps_const || !mu_const)) {
+    const long long* __restrict__ zq = tb.zq + I.tab;
+    const long long zf = __ldg(zq), zl = __ldg(zq + np - 1);
+    const int last = base + span - 1;
+    const long long dq = I.dq;
+    auto one_side = [&](long long off_a, long long off_b, int& r) {
+      if (last < node_of(zf, off_a) && last < node_of(zf, off_b)) { r = 0; return true; }
+      if (base >= node_of(zl, off_a) && base >= node_of(zl, off_b)) { r = lin ? np - 1 : np; return true; }
+      return false;
+    };
+    const long long n1 = n0 + 1, n2 = n0 + nsteps;
+    if (!eps_const && one_side(dq * (2 * n1 - 1), dq * (2 * n2 - 1), rE)) eps_const = true;
+    if (!mu_const && one_side(dq * (2 * n1) - HALF_CELL, dq * (2 * n2) - HALF_CELL, rH)) mu_const = true;
+  }
+}
+
 template <int C, int TB, bool POS, bool MATTER, bool EDGE, typename T, bool KAHAN = false>
 __device__ __forceinline__ void run_tile(const BlockArgs<T>& A, const InstDev& I, int x0, int W,
                                          long long n0) {
@@ -409,31 +440,11 @@ __device__ __forceinline__ void run_tile(const BlockArgs<T>& A, const InstDev& I
 
   const R a = coef<R>(I.a, I.a32), cc = coef<R>(I.c, I.c32);
   const bool damp = window_absorbs(I, base, 32 * C);   // the tile reaches an absorbing layer
-  bool eps_const = (I.flags & F_EPS_CONST) != 0;
-  bool mu_const = (I.flags & F_MU_CONST) != 0;
+  bool eps_const, mu_const;
+  int rE, rH;                                          // table entries of the uniform values
+  uniform_sides(I, A.tb, base, 32 * C, n0, A.nsteps, eps_const, mu_const, rE, rH);
   const long long dq = I.dq;
   const bool lin = (I.flags & F_LINEAR) != 0;
-  // A tile whose window lies, over the whole launch, before the first profile
-  // position or after the last one sees a single material value on that side
-  // (positions move monotonically, so the launch's first and last half levels
-  // decide): it takes the uniform path with that value.  (Layers tables hold
-  // the coefficients themselves; a linear moving-matter profile would need
-  // them formed from (eps, mu), so it keeps the general path.)
-  int rE = 0, rH = 0;                                  // table entries of the uniform values
-  const int np = lin ? I.n : I.n - 1;                  // profile positions
-  if ((!MATTER || !lin) && np > 0 && (!eps_const || !mu_const)) {
-    const long long* __restrict__ zq = A.tb.zq + I.tab;
-    const long long zf = __ldg(zq), zl = __ldg(zq + np - 1);
-    const int last = base + 32 * C - 1;
-    auto one_side = [&](long long off_a, long long off_b, int& r) {
-      if (last < node_of(zf, off_a) && last < node_of(zf, off_b)) { r = 0; return true; }
-      if (base >= node_of(zl, off_a) && base >= node_of(zl, off_b)) { r = lin ? np - 1 : np; return true; }
-      return false;
-    };
-    const long long n1 = n0 + 1, n2 = n0 + A.nsteps;
-    if (!eps_const && one_side(dq * (2 * n1 - 1), dq * (2 * n2 - 1), rE)) eps_const = true;
-    if (!mu_const && one_side(dq * (2 * n1) - HALF_CELL, dq * (2 * n2) - HALF_CELL, rH)) mu_const = true;
-  }
   const auto e0 = __ldg(TabOf<R>::get(A.tb, true) + I.tab + rE);
   const auto h0 = __ldg(TabOf<R>::get(A.tb, false) + I.tab + rH);
   // (uniform values: LINEAR tables hold raw (eps, mu), LAYERS tables the coefficients)
@@ -1114,7 +1125,9 @@ __global__ void __launch_bounds__(128, general_min_blocks(C, sizeof(typename Rea
   const int gw = blockIdx.x * warps_per_block + (threadIdx.x >> 5);
   const int nw = gridDim.x * warps_per_block;
   const long long n0 = *A.n_done + A.s0;
-  for (int t = gw; t < A.n_tiles; t += nw) {
+  const int nt = A.queue ? *(volatile int*)A.qcount : A.n_tiles;
+  for (int i = gw; i < nt; i += nw) {
+    const int t = A.queue ? A.queue[i] : i;
     const int2 tl = A.tiles[t];
     const InstDev I = A.inst[tl.x];
     const int x0 = tl.y;
@@ -1130,6 +1143,156 @@ __global__ void __launch_bounds__(128, general_min_blocks(C, sizeof(typename Rea
       if (base < 0 || base + 32 * C > I.nz) run_tile<C, TB, false, MATTER, true, T, KAHAN>(A, I, x0, W, n0);
       else run_tile<C, TB, false, MATTER, false, T, KAHAN>(A, I, x0, W, n0);
     }
+  }
+  if (A.queue) {
+    // the last block out empties the queue for the next launch (every warp has read
+    // its length by then)
+    __syncthreads();
+    if (threadIdx.x == 0 && atomicAdd(A.qcount + 1, 1) == (int)gridDim.x - 1) {
+      atomicExch(A.qcount, 0);
+      atomicExch(A.qcount + 1, 0);
+    }
+  }
+}
+
+// ------------------------------------------------ uniform tiles of the general lists
+//
+// A tile of the general lists whose window lies inside the domain, sees one ε
+// value and one μ value over the whole launch (uniform_sides) and holds no
+// absorbing layer, no recorded probe and no one-way source's correction cells
+// steps in uniform_kernel with E' and H' substituted, the regrouping of the
+// fast kernel here with the couplings cbe, cbh of the two uniform values (for
+// moving perturbation both are cb):
+//   v >= 0:  B'_j = (a + cbe) B_j + c B_{j-1} - cbe B_{j-2} + se (D_j - D_{j+1})
+//            D'_k = a D_k + (c - cbh) D_{k-1} + cbh D_{k+1} + sm (B'_{k-1} - B'_k)
+//   v <  0:  B'_j = (a - cbe) B_j + c B_{j+1} + cbe B_{j+2} + se (D_j - D_{j+1})
+//            D'_k = a D_k + (c + cbh) D_{k+1} - cbh D_{k-1} + sm (B'_{k-1} - B'_k)
+// (with the FP32 weights of reading R16 the sums a + cbe, c - cbh, ... are
+// exact).  It appends every other tile to the queue that block_kernel then
+// takes, so the general kernel's registers and code serve only the tiles that
+// need them.  Returns whether the tile was stepped.
+template <int C, int TB, bool POS, typename T>
+__device__ __forceinline__ bool run_tile_uniform(const BlockArgs<T>& A, const InstDev& I, int x0, int W,
+                                                 long long n0) {
+  using R = typename Real<T>::type;
+  const int lane = threadIdx.x & 31;
+  constexpr int L = tile_margin(TB, POS, 16 / sizeof(T));
+  constexpr int SPAN = 32 * C;
+  const int base = x0 - L;
+  if (base < 0 || base + SPAN > I.nz || window_absorbs(I, base, SPAN)) return false;
+  if (A.record)
+    for (int q = 0; q < I.nprb; ++q) {
+      const int node = A.prbs[I.prb0 + q].node;
+      if (node >= x0 && node < x0 + W) return false;
+    }
+  if (A.n_tfsf > 0)
+    for (int q = 0; q < I.ntf; ++q) {
+      const int node = A.tfsf[I.tf0 + q].node;
+      if (node + 1 >= base && node - 2 < base + SPAN) return false;
+    }
+  bool eps_const, mu_const;
+  int rE, rH;
+  uniform_sides(I, A.tb, base, SPAN, n0, A.nsteps, eps_const, mu_const, rE, rH);
+  if (!eps_const || !mu_const) return false;
+
+  const bool lin = (I.flags & F_LINEAR) != 0, matter = (I.flags & F_MATTER) != 0;
+  const auto e0 = __ldg(TabOf<R>::get(A.tb, true) + I.tab + rE);
+  const auto h0 = __ldg(TabOf<R>::get(A.tb, false) + I.tab + rH);
+  // (uniform values: LINEAR tables hold raw (eps, mu), LAYERS tables the coefficients)
+  const R se = lin ? (R)I.S / e0.x : e0.x, sm = lin ? (R)I.S / h0.y : h0.x;
+  const R cb = coef<R>(I.cb, I.cb32);
+  const R cbe = matter ? (R)e0.y : cb, cbh = matter ? (R)h0.y : cb;
+  const R a = coef<R>(I.a, I.a32), cc = coef<R>(I.c, I.c32);
+  const R kb0 = POS ? a + cbe : a - cbe;     // B_j
+  const R kb2 = POS ? -cbe : cbe;            // B_{j-2} (v >= 0) or B_{j+2} (v < 0)
+  const R kdu = POS ? cc - cbh : cc + cbh;   // upwind D neighbour
+  const R kdd = POS ? cbh : -cbh;            // downwind D neighbour
+  const int k0 = base + lane * C;
+
+  unsigned smask = 0;
+  if (A.src_amp)
+    for (int q = 0; q < I.nsrc && q < 32; ++q) {
+      const int node = A.srcs[I.src0 + q].node;
+      if (node >= base && node < base + SPAN) smask |= 1u << q;
+    }
+
+  R B[C], D[C];
+  load_cells<T, R, C>(A.Bin + I.off, k0, I.nz_pad, B);
+  load_cells<T, R, C>(A.Din + I.off, k0, I.nz_pad, D);
+  for (int s = 0; s < A.nsteps; ++s) {
+    // ---- B^n
+    const R dr = __shfl_down_sync(FULL, D[0], 1);
+    if (POS) {
+      const R bl1 = __shfl_up_sync(FULL, B[C - 1], 1), bl2 = __shfl_up_sync(FULL, B[C - 2], 1);
+#pragma unroll
+      for (int c = C - 1; c >= 0; --c) {
+        const R b1 = c >= 1 ? B[c - 1] : bl1;
+        const R b2 = c >= 2 ? B[c - 2] : (c == 1 ? bl1 : bl2);
+        const R d1 = c + 1 < C ? D[c + 1] : dr;
+        B[c] = kb0 * B[c] + (cc * b1 + (kb2 * b2 + se * (D[c] - d1)));
+      }
+    } else {
+      const R br1 = __shfl_down_sync(FULL, B[0], 1), br2 = __shfl_down_sync(FULL, B[1], 1);
+#pragma unroll
+      for (int c = 0; c < C; ++c) {
+        const R b1 = c + 1 < C ? B[c + 1] : br1;
+        const R b2 = c + 2 < C ? B[c + 2] : (c + 2 == C ? br1 : br2);
+        const R d1 = c + 1 < C ? D[c + 1] : dr;
+        B[c] = kb0 * B[c] + (cc * b1 + (kb2 * b2 + se * (D[c] - d1)));
+      }
+    }
+    // ---- D^{n+1/2}
+    {
+      const R bl = __shfl_up_sync(FULL, B[C - 1], 1), dl = __shfl_up_sync(FULL, D[C - 1], 1);
+      R Dn[C];
+#pragma unroll
+      for (int c = 0; c < C; ++c) {
+        const R dm = c >= 1 ? D[c - 1] : dl, dp = c + 1 < C ? D[c + 1] : dr;
+        const R bm = c >= 1 ? B[c - 1] : bl;
+        Dn[c] = a * D[c] + ((POS ? kdu * dm + kdd * dp : kdu * dp + kdd * dm) + sm * (bm - B[c]));
+      }
+#pragma unroll
+      for (int c = 0; c < C; ++c) D[c] = Dn[c];
+    }
+    // ---- soft sources at t_{n+1/2}
+    for (unsigned m = smask; m; m &= m - 1) {
+      const int q = __ffs(m) - 1;
+      const int rel = A.srcs[I.src0 + q].node - base;
+      const R amp = (R)A.src_amp[(long long)(I.src0 + q) * A.chunk_stride + A.s0 + s];
+      if (lane == rel / C) {
+        const int cs = rel % C;
+#pragma unroll
+        for (int c = 0; c < C; ++c) D[c] += (c == cs) ? amp : (R)0;
+      }
+    }
+    // ---- D^{n+1/2} of every step, for the adjoint's segment recomputation
+    if (A.dseg)
+      store_cells<T, R, C>(A.dseg + (long long)(A.s0 + s + 1) * A.dseg_stride + I.off, k0, x0, x0 + W, D);
+  }
+  store_cells<T, R, C>(A.Bout + I.off, k0, x0, x0 + W, B);
+  store_cells<T, R, C>(A.Dout + I.off, k0, x0, x0 + W, D);
+  return true;
+}
+
+// Blocks per SM the uniform kernel's registers are held to.
+__host__ __device__ constexpr int uniform_min_blocks(int C, int real_bytes) {
+  return real_bytes != 4 ? 0 : (C <= 8 ? 8 : (C <= 16 ? 6 : 4));
+}
+
+template <int C, int TB, typename T>
+__global__ void __launch_bounds__(128, uniform_min_blocks(C, sizeof(typename Real<T>::type)))
+    uniform_kernel(const BlockArgs<T> A) {
+  constexpr int V = 16 / sizeof(T);
+  const int wib = __shfl_sync(FULL, (int)(threadIdx.x >> 5), 0), lane = threadIdx.x & 31;
+  const int gw = blockIdx.x * 4 + wib, nw = gridDim.x * 4;
+  const long long n0 = *A.n_done + A.s0;
+  for (int t = gw; t < A.n_tiles; t += nw) {
+    const int2 tl = A.tiles[t];
+    const InstDev I = A.inst[tl.x];
+    const bool done = (I.flags & F_POS)
+                          ? run_tile_uniform<C, TB, true, T>(A, I, tl.y, tile_width(C, TB, true, V), n0)
+                          : run_tile_uniform<C, TB, false, T>(A, I, tl.y, tile_width(C, TB, false, V), n0);
+    if (!done && lane == 0) A.queue[atomicAdd(A.qcount, 1)] = t;
   }
 }
 
@@ -1221,6 +1384,7 @@ int launch_block_shape(int variant, const void* args, int grid, int block, cudaS
   const BlockArgs<T>& a = *static_cast<const BlockArgs<T>*>(args);
   if (variant == 2 && !KAHAN) fast_kernel<C, TB, T, MB><<<grid, block, 0, st>>>(a);
   else if (variant == 3 && !KAHAN) fast_kernel<C, TB, T, MB, true><<<grid, block, 0, st>>>(a);
+  else if (variant == 4 && !KAHAN) uniform_kernel<C, TB, T><<<grid, block, 0, st>>>(a);
   else if (variant == 1) block_kernel<C, TB, true, T, KAHAN><<<grid, block, 0, st>>>(a);
   else if (variant == 0) block_kernel<C, TB, false, T, KAHAN><<<grid, block, 0, st>>>(a);
   else return (int)cudaErrorInvalidValue;
@@ -1241,6 +1405,8 @@ int occupancy_block_shape(int variant, int block, int* nb) {
     if (e3 != cudaSuccess) return (int)e3;
     return (int)cudaOccupancyMaxActiveBlocksPerMultiprocessor(nb, fast_kernel<C, TB, T, MB>, block, 0);
   }
+  if (variant == 4 && !KAHAN)
+    return (int)cudaOccupancyMaxActiveBlocksPerMultiprocessor(nb, uniform_kernel<C, TB, T>, block, 0);
   if (variant == 1)
     return (int)cudaOccupancyMaxActiveBlocksPerMultiprocessor(nb, block_kernel<C, TB, true, T, KAHAN>,
                                                               block, 0);

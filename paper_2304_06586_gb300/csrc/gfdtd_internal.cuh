@@ -190,6 +190,9 @@ struct BlockArgs {
   const double* tf_corr;      // [source][step in chunk (chunk_stride)][kTfsfCorr] additive corrections
   int stall;                  // fast kernel, test hook: arm each tile barrier but start no copy,
                               //   so that every bounded wait runs out (0 in normal operation)
+  int* queue;                 // general lists: uniform_kernel appends the tiles it does not take
+  int* qcount;                //   (indices into `tiles`) and block_kernel takes them; qcount[0]:
+                              //   entries, qcount[1]: blocks done (NULL: block_kernel takes every tile)
 };
 
 // Arguments of the plain kernel (one instance, one step).
@@ -211,6 +214,8 @@ struct PlainArgs {
 };
 // Advances the plain path's step-within-chunk counter by one (after a step's launches).
 int plain_tick_launch(int* s_dev, cudaStream_t st);
+// gfdtd_plain_floor's launch: one instance's B and D read, output cells written back unchanged.
+int plain_floor_launch(int elem_bytes, void* B, void* D, int nz, const int* s_dev, cudaStream_t st);
 
 struct FoldArgs {
   const PrbDev* prbs;
@@ -228,36 +233,6 @@ struct FoldArgs {
 };
 
 // Adjoint (gfdtd_adjoint.cu).
-constexpr int kAdjTileCells = 1024;   // cells one block of the adjoint step transposes
-
-struct AdjArgs {
-  const InstDev* inst;
-  const int2* tiles;          // (instance, first cell) of kAdjTileCells-cell blocks
-  int n_tiles;
-  Tables tb;
-  const float* lBn;           // adjoint of B^n, D^{n+1/2}
-  const float* lDn;
-  float* lB;                  // adjoint of B^{n-1}, D^{n-1/2}
-  float* lD;
-  const float* Dold;          // D^{n-1/2}
-  long long n;                // the forward step being transposed
-  double* grad;               // dL/d(profile value), indexed by the instance's table offset
-  int grad_copies;            // copies of grad, grad_stride apart: block b adds into copy b % copies
-  long long grad_stride;
-};
-
-struct ProbeAdjArgs {
-  const InstDev* inst;
-  int n_inst;
-  Tables tb;
-  const int* probe_node;      // per instance
-  const double* gn;           // per instance: dL/dF_n
-  float* lD;
-  const float* Dnew;          // D^{n+1/2}
-  long long n;
-  double* grad;
-};
-
 struct SourceAdjArgs {
   int n_inst;
   const int* bin0;            // per instance: first bin of the loss band in the arrays below
@@ -270,7 +245,6 @@ struct SourceAdjArgs {
   double S;
   double* gn;                 // [step][inst]
 };
-int adjoint_step_launch(const AdjArgs& a, cudaStream_t st);
 
 // Time-blocked transpose: kAdjBlockSteps reverse steps per launch, a warp per
 // tile of 32 x kAdjCells cells held in registers.  A tile's output range
@@ -287,7 +261,7 @@ static_assert(adj_margin(true) % 4 == 0 && adj_margin(false) % 4 == 0, "windows 
 
 struct AdjBlockArgs {
   const InstDev* inst;
-  const int2* tiles;          // (instance, first output cell), adj_width(v >= 0) apart
+  const int2* tiles;          // (instance, first output cell), adj_width(v >= 0) cells apart
   int n_tiles;
   Tables tb;
   const float* lBn;           // adjoint of B^{n_hi}, D^{n_hi+1/2}
@@ -302,8 +276,8 @@ struct AdjBlockArgs {
   const int* probe_node;      // per instance (-1: none)
   const double* gn;           // dL/dF of segment step m for instance i at gn[(m - 1) n_inst + i]
   int n_inst;
-  double* grad;               // as AdjArgs
-  int grad_copies;
+  double* grad;               // dL/d(profile value), indexed by the instance's table offset
+  int grad_copies;            // copies of grad, grad_stride apart: block b adds into copy b % copies
   long long grad_stride;
 };
 int adjoint_block_launch(const AdjBlockArgs& a, int grid, cudaStream_t st);
@@ -315,7 +289,6 @@ int tfsf_aux_launch(const TfsfDev* tf, int n, void* aux, bool fp64, double* corr
                     const long long* n_done, int nsteps, cudaStream_t st);
 int sum_copies_launch(const double* copies, long long n_copies, long long stride, long long n, double* out,
                       cudaStream_t st);
-int probe_adjoint_launch(const ProbeAdjArgs& a, cudaStream_t st);
 int loss_source_launch(const SourceAdjArgs& a, cudaStream_t st);
 
 // Kernel launchers (gfdtd_kernels.cu).

@@ -271,6 +271,34 @@ __global__ void __launch_bounds__(kPlainThreads) plain_kernel(const PlainArgs<T>
   else plain_block<false>(A, sh);
 }
 
+// The launch structure of the plain path without its arithmetic (gfdtd_plain_floor):
+// the plain kernel's grid, every thread reads its cell's B and D, the block's
+// output cells are written back unchanged (U: an unsigned type of the element's size).
+template <typename U>
+__global__ void __launch_bounds__(kPlainThreads) plain_floor_kernel(U* B, U* D, int nz, const int* s_dev) {
+  const int t = threadIdx.x;
+  const int k = blockIdx.x * kPlainOut - 4 + t;
+  if (*s_dev < 0 || k < 0 || k >= nz) return;
+  volatile U* vB = B;
+  volatile U* vD = D;
+  const U b = vB[k], d = vD[k];
+  if (t >= 4 && t <= kPlainThreads - 4) {
+    vB[k] = b;
+    vD[k] = d;
+  }
+}
+
+int plain_floor_launch(int elem_bytes, void* B, void* D, int nz, const int* s_dev, cudaStream_t st) {
+  const int grid = (nz + kPlainOut - 1) / kPlainOut;
+  switch (elem_bytes) {
+    case 2: plain_floor_kernel<unsigned short><<<grid, kPlainThreads, 0, st>>>((unsigned short*)B, (unsigned short*)D, nz, s_dev); break;
+    case 4: plain_floor_kernel<unsigned><<<grid, kPlainThreads, 0, st>>>((unsigned*)B, (unsigned*)D, nz, s_dev); break;
+    case 8: plain_floor_kernel<unsigned long long><<<grid, kPlainThreads, 0, st>>>((unsigned long long*)B, (unsigned long long*)D, nz, s_dev); break;
+    default: return (int)cudaErrorInvalidValue;
+  }
+  return (int)cudaGetLastError();
+}
+
 __global__ void plain_tick_kernel(int* s_dev) {
   if (threadIdx.x == 0 && blockIdx.x == 0) *s_dev += 1;
 }

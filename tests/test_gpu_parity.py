@@ -133,6 +133,24 @@ def test_plain_kernel_matches_oracle(kind):
     _compare(wl, sim, orcs, TOL32)
 
 
+def test_plain_floor_leaves_the_state_alone():
+    """gfdtd_plain_floor (the plain path's launches without the arithmetic) leaves
+    fields, spectra and the step count as they were, bit for bit."""
+    wl = _mixed_workload(seed=12)
+    sim = make_sim(wl)
+    orcs = make_oracle(wl)
+    _seed_fields(wl, sim, orcs)
+    sim.step_plain(5)
+    before = [(sim.read_fields(k, gb.FIELD_B), sim.read_fields(k, gb.FIELD_D)) for k in range(len(wl.instances))]
+    n = sim.steps_done()
+    sim.plain_floor(7)
+    sim.synchronize()
+    assert sim.steps_done() == n
+    for k, (B, D) in enumerate(before):
+        assert np.array_equal(sim.read_fields(k, gb.FIELD_B), B)
+        assert np.array_equal(sim.read_fields(k, gb.FIELD_D), D)
+
+
 def test_deterministic_and_chunking_independent():
     """The same calls give the same bits; grouping steps into different calls,
     chunks or tile shapes (which moves cells between the fused interior path
