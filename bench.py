@@ -210,8 +210,10 @@ def example_measurements(gb, torch):
         sim.synchronize()
         dt = time.perf_counter() - t0
         cells = sum(i.nz for i in wl.instances)
+        st = sim.stats()
         out[name] = {"value": cells * steps / dt / 1e9, "unit": "Gcell-updates/s", "steps": steps,
-                     "seconds": dt}
+                     "seconds": dt, "tile": [st["cells_per_lane"], st["time_block"], st["blocks_per_sm"]],
+                     "uniform_split": bool(st["uniform_split"])}
         sim.close()
     torch.cuda.synchronize()
     return out
@@ -321,6 +323,8 @@ def run_case(args):
         wl = w.config5(n_steps=T)
         sim = gb.Simulation([i.nz for i in wl.instances], wl.S, gb.F32)
         configure(sim, wl, gb)
+        if args.tile:
+            sim.set_tuning(*[int(x) for x in args.tile.split(",")])
         nv = [len(i.eps) for i in wl.instances]
         sim.adjoint(64, 0, 0, 16, nv)
         t0 = time.perf_counter()
@@ -367,7 +371,8 @@ def run_case(args):
     torch.cuda.synchronize()
     print(json.dumps({"case": args.case, "workload": wl.description, "steps": T, "seconds": dt,
                       "value": cells * T / dt / 1e9, "unit": "Gcell-updates/s",
-                      "tile": [st["cells_per_lane"], st["time_block"], st["blocks_per_sm"]]}), flush=True)
+                      "tile": [st["cells_per_lane"], st["time_block"], st["blocks_per_sm"]],
+                      "uniform_split": bool(st["uniform_split"])}), flush=True)
 
 
 E2E_PARTS = 4

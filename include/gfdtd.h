@@ -274,6 +274,7 @@ typedef struct {
     int64_t n_tiles;           /* tiles per time block for the whole batch */
     int64_t kernel_launches;   /* library kernels launched so far (graph nodes counted) */
     int64_t cells;             /* sum of nz */
+    int uniform_split;         /* 1: the general lists take the uniform-tile split */
 } gfdtd_stats;
 
 gfdtd_status gfdtd_get_stats(const gfdtd_ctx* ctx, gfdtd_stats* out);

@@ -34,7 +34,7 @@ FREE_FN = C.CFUNCTYPE(None, C.c_void_p, C.c_size_t, C.c_void_p, C.c_void_p)
 class Stats(C.Structure):
     _fields_ = [("cells_per_lane", C.c_int), ("time_block", C.c_int), ("blocks_per_sm", C.c_int),
                 ("n_tiles", C.c_int64),
-                ("kernel_launches", C.c_int64), ("cells", C.c_int64)]
+                ("kernel_launches", C.c_int64), ("cells", C.c_int64), ("uniform_split", C.c_int)]
 
 
 class KernelTimes(C.Structure):

@@ -170,11 +170,20 @@ __device__ __forceinline__ void adjoint_tile(const AdjBlockArgs& A, const InstDe
 
   GradRun run{-1, 0.0f};
   float gu = 0.0f;                                   // the single value's sum (ku >= 0)
+  // D^{n-1/2} of the step being transposed (the forward's field after segment step m - 1),
+  // loaded one step ahead
+  float Dv[C];
+  load_cells<float, float, C>(A.dseg + (long long)(A.m_hi - 1) * A.dseg_stride + I.off, k0, I.nz_pad, Dv);
   for (int s = 0; s < A.nsteps; ++s) {
     const int m = A.m_hi - s;                        // segment step transposed: n = n_seg + m
     const long long n = A.n_seg + m;
-    float Dv[C];                                     // D^{n-1/2}: the forward's field after step m - 1
-    load_cells<float, float, C>(A.dseg + (long long)(m - 1) * A.dseg_stride + I.off, k0, I.nz_pad, Dv);
+    float Dnext[C];
+    if (s + 1 < A.nsteps) {
+      load_cells<float, float, C>(A.dseg + (long long)(m - 2) * A.dseg_stride + I.off, k0, I.nz_pad, Dnext);
+    } else {
+#pragma unroll
+      for (int c = 0; c < C; ++c) Dnext[c] = 0.0f;
+    }
 
     // probe term of step n (level n+1/2) into lD'
     if (lane == lp) {
@@ -306,6 +315,7 @@ __device__ __forceinline__ void adjoint_tile(const AdjBlockArgs& A, const InstDe
     for (int c = 0; c < C; ++c) {
       LB[c] = nB[c];
       LD[c] = nD[c];
+      Dv[c] = Dnext[c];
     }
   }
 

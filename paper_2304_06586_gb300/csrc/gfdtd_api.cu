@@ -1712,6 +1712,7 @@ gfdtd_status gfdtd_get_stats(const gfdtd_ctx* c, gfdtd_stats* out) {
   long long cells = 0;
   for (long long v : c->nz) cells += v;
   out->cells = cells;
+  out->uniform_split = c->split && c->prec != GFDTD_F32_KAHAN ? 1 : 0;
   return GFDTD_OK;
 }
 
