@@ -107,71 +107,41 @@ __device__ __forceinline__ void grad_add(GradRun& r, int key, float v, float* sa
   r.acc += v;
 }
 
-template <bool POS>
-__device__ __forceinline__ void adjoint_tile(const AdjBlockArgs& A, const InstDev& I, int inst, int x0,
-                                             float* sacc, double* grad, int lane) {
+// The state of one tile of the time-blocked transpose between its setup and its store.
+struct AdjTile {
+  float LB[kAdjCells], LD[kAdjCells];   // lambda B, lambda D of the lane's cells
+  int base, k0, x0, out_hi, nz;
+  int kb, li, liH, ku;                  // gradient key base; position counts; single key (-1: none)
+  float seu;                            // the single value's S/eps (ku >= 0)
+  int kp, lp, cp;                       // probe node, its lane and cell (lp = -1: not in the window)
+  bool probe_out;
+  GradRun run;
+  float gacc;                           // sum of lambdaE D over the output cells (ku >= 0)
+};
+
+// The reverse steps of one tile.  INSIDE: the window lies inside [0, nz), so no
+// cell needs the zero of the domain's ghosts; UNI: one permittivity value over
+// the window and the launch (key ku), whose gradient is -se^2 / S times the
+// sum of lambdaE D over the output cells.
+template <bool POS, bool INSIDE, bool UNI>
+__device__ __forceinline__ void adjoint_steps(const AdjBlockArgs& A, const InstDev& I, int inst, AdjTile& T,
+                                              float* sacc, double* grad, int lane) {
   constexpr int C = kAdjCells;
-  const int base = x0 - adj_margin(POS);
-  const int k0 = base + C * lane;
-  const int nz = I.nz;
-  const int out_hi = min(x0 + adj_width(POS), nz);   // output cells [x0, out_hi)
-  float LB[C], LD[C];
-  load_cells<float, float, C>(A.lBn + I.off, k0, I.nz_pad, LB);
-  load_cells<float, float, C>(A.lDn + I.off, k0, I.nz_pad, LD);
-#pragma unroll
-  for (int c = 0; c < C; ++c) {   // (padding cells past nz are not necessarily written)
-    const bool in = (unsigned)(k0 + c) < (unsigned)nz;
-    LB[c] = in ? LB[c] : 0.0f;
-    LD[c] = in ? LD[c] : 0.0f;
-  }
+  float (&LB)[C] = T.LB;
+  float (&LD)[C] = T.LD;
+  const int k0 = T.k0, nz = T.nz;
   const float a = I.a32, cc = I.c32, cb = I.cb32, S = (float)I.S, inv_S = (float)I.inv_S;
   const bool lin = (I.flags & F_LINEAR) != 0;
   const bool mu_const = (I.flags & F_MU_CONST) != 0;
   const long long dq = I.dq;
   const long long* __restrict__ zq = A.tb.zq + I.tab;
   const float2* __restrict__ tv = A.tb.tabE32 + I.tab;
-  const int np = lin ? I.n : I.n - 1;                  // profile positions
-  const long long n_hi = A.n_seg + A.m_hi, n_lo = n_hi - A.nsteps + 1;
+  const int np = lin ? I.n : I.n - 1;
+  // the lane's cells against the output range: all in, some in (a domain end), none
+  const bool out_all = k0 >= T.x0 && k0 + C <= T.out_hi;
+  const bool out_some = !out_all && k0 + C > T.x0 && k0 < T.out_hi;
+  auto in = [&](int c) { return INSIDE || (unsigned)(k0 + c) < (unsigned)nz; };
 
-  // a single permittivity value over the window and the launch (key ku), else ku = -1
-  int ku = -1;
-  float seu = 0.0f;
-  {
-    const int last = base + 32 * C - 1;
-    const long long oa = dq * (2 * n_lo - 1), ob = dq * (2 * n_hi - 1);
-    if (np == 0) {
-      ku = 0;
-    } else {
-      const long long zf = __ldg(zq), zl = __ldg(zq + np - 1);
-      if (last < node_of(zf, oa) && last < node_of(zf, ob)) ku = 0;
-      else if (base >= node_of(zl, oa) && base >= node_of(zl, ob)) ku = lin ? np - 1 : np;
-    }
-    if (ku >= 0) {
-      const float2 v = __ldg(tv + ku);
-      seu = lin ? S / v.x : v.x;
-    }
-  }
-  int kb = 0, li = 0, liH = 0;
-  if (ku < 0) {
-    // the smallest value the window meets in the launch: one below the count at its first cell
-    const long long xa = ((long long)base << 32) - dq * (2 * n_lo - 1);
-    const long long xb = ((long long)base << 32) - dq * (2 * n_hi - 1);
-    kb = max(0, positions_at_or_left(zq, np, min(xa, xb)) - 1);
-    for (int i = lane; i < kAdjKeysW; i += 32) sacc[i] = 0.0f;
-    __syncwarp();
-    li = positions_at_or_left(zq, np, ((long long)k0 << 32) - dq * (2 * n_hi - 1));
-  }
-  if (!mu_const) liH = count_at_or_left(zq, np, dq * (2 * n_hi) - HALF_CELL, k0);
-  // the probe
-  const int kp = A.probe_node[inst];
-  const bool probe_in = kp >= 0 && kp < nz && kp >= base && kp < base + 32 * C;
-  const bool probe_out = probe_in && kp >= x0 && kp < out_hi;
-  const int lp = probe_in ? (kp - base) / C : -1, cp = probe_in ? (kp - base) % C : 0;
-
-  GradRun run{-1, 0.0f};
-  float gu = 0.0f;                                   // the single value's sum (ku >= 0)
-  // D^{n-1/2} of the step being transposed (the forward's field after segment step m - 1),
-  // loaded one step ahead
   float Dv[C];
   load_cells<float, float, C>(A.dseg + (long long)(A.m_hi - 1) * A.dseg_stride + I.off, k0, I.nz_pad, Dv);
   for (int s = 0; s < A.nsteps; ++s) {
@@ -186,22 +156,22 @@ __device__ __forceinline__ void adjoint_tile(const AdjBlockArgs& A, const InstDe
     }
 
     // probe term of step n (level n+1/2) into lD'
-    if (lane == lp) {
+    if (lane == T.lp) {
       const double g = A.gn[(long long)(m - 1) * A.n_inst + inst];
       if (g != 0.0) {
         const long long off = dq * (2 * n + 1);
         double se, y;
-        node_coef<false, true>(I, A.tb, off, kp, se, y);
+        node_coef<false, true>(I, A.tb, off, T.kp, se, y);
         const float add = (float)(g * se / I.S);
 #pragma unroll
-        for (int c = 0; c < C; ++c) LD[c] += (c == cp) ? add : 0.0f;
-        if (probe_out) {
+        for (int c = 0; c < C; ++c) LD[c] += (c == T.cp) ? add : 0.0f;
+        if (T.probe_out) {
           // F = D / eps: dF/deps = -D / eps^2 = -D se^2 / S^2
-          const double Dp = A.dseg[(long long)m * A.dseg_stride + I.off + kp];
+          const double Dp = A.dseg[(long long)m * A.dseg_stride + I.off + T.kp];
           const double gE = g * (-Dp * se * se / (I.S * I.S));
           int i0, i1;
           double w0, w1;
-          eps_weights(I, zq, ((long long)kp << 32) - off, i0, w0, i1, w1);
+          eps_weights(I, zq, ((long long)T.kp << 32) - off, i0, w0, i1, w1);
           atomicAdd(grad + i0, gE * w0);
           if (lin) atomicAdd(grad + i1, gE * w1);
         }
@@ -210,7 +180,7 @@ __device__ __forceinline__ void adjoint_tile(const AdjBlockArgs& A, const InstDe
 
     // lH_j = lD'_{j+1} - lD'_j and lBt_j = lB'_j + sm_j lH_j
     const float dn1 = __shfl_down_sync(FULL, LD[0], 1);
-    float lH[C], T[C];
+    float lH[C], Tt[C];
     {
       float smv[C];
       if (mu_const) {
@@ -218,47 +188,40 @@ __device__ __forceinline__ void adjoint_tile(const AdjBlockArgs& A, const InstDe
         for (int c = 0; c < C; ++c) smv[c] = I.sm32;
       } else {
         float tmp[C];
-        lane_coefs<C, false, false, float>(I, A.tb, dq * (2 * n) - HALF_CELL, k0, liH, smv, tmp);
+        lane_coefs<C, false, false, float>(I, A.tb, dq * (2 * n) - HALF_CELL, k0, T.liH, smv, tmp);
       }
 #pragma unroll
       for (int c = 0; c < C; ++c) {
-        const bool in = (unsigned)(k0 + c) < (unsigned)nz;
-        lH[c] = in ? (c + 1 < C ? LD[c + 1] : dn1) - LD[c] : 0.0f;
-        T[c] = in ? LB[c] + smv[c] * lH[c] : 0.0f;
+        lH[c] = in(c) ? (c + 1 < C ? LD[c + 1] : dn1) - LD[c] : 0.0f;
+        Tt[c] = in(c) ? LB[c] + smv[c] * lH[c] : 0.0f;
       }
     }
     // lE_k = lBt_k - lBt_{k-1}
-    const float tl1 = __shfl_up_sync(FULL, T[C - 1], 1);
+    const float tl1 = __shfl_up_sync(FULL, Tt[C - 1], 1);
     float lE[C];
 #pragma unroll
-    for (int c = 0; c < C; ++c) {
-      const bool in = (unsigned)(k0 + c) < (unsigned)nz;
-      lE[c] = in ? T[c] - (c > 0 ? T[c - 1] : tl1) : 0.0f;
-    }
+    for (int c = 0; c < C; ++c) lE[c] = in(c) ? Tt[c] - (c > 0 ? Tt[c - 1] : tl1) : 0.0f;
     const float hl1 = __shfl_up_sync(FULL, lH[C - 1], 1);
     const float dl1 = __shfl_up_sync(FULL, LD[C - 1], 1);
-    const float tn1 = __shfl_down_sync(FULL, T[0], 1);
+    const float tn1 = __shfl_down_sync(FULL, Tt[0], 1);
     const float en1 = __shfl_down_sync(FULL, lE[0], 1);
     const float en2 = __shfl_down_sync(FULL, lE[1], 1);
     const float el1 = __shfl_up_sync(FULL, lE[C - 1], 1);
 
     // the permittivity at level n-1/2 of each cell, with the profile values it weighs
-    const long long offE = dq * (2 * n - 1);
-    const long long xi0 = ((long long)k0 << 32) - offE;
-    if (ku < 0) {
-      while (li < np && __ldg(zq + li) <= xi0) ++li;
-      while (li > 0 && __ldg(zq + li - 1) > xi0) --li;
+    const long long xi0 = ((long long)k0 << 32) - dq * (2 * n - 1);
+    if (!UNI) {
+      while (T.li < np && __ldg(zq + T.li) <= xi0) ++T.li;
+      while (T.li > 0 && __ldg(zq + T.li - 1) > xi0) --T.li;
     }
-    int idx = li;
+    int idx = T.li;
     float nD[C], nB[C];
 #pragma unroll
     for (int c = 0; c < C; ++c) {
-      const int k = k0 + c;
-      const bool in = (unsigned)k < (unsigned)nz;
       float se, w1 = 0.0f;
-      int key0 = ku, key1 = ku;
-      if (ku >= 0) {
-        se = seu;
+      int key0 = T.ku, key1 = T.ku;
+      if (UNI) {
+        se = T.seu;
       } else {
         const long long xi = xi0 + ((long long)c << 32);
         while (idx < np && __ldg(zq + idx) <= xi) ++idx;
@@ -287,28 +250,27 @@ __device__ __forceinline__ void adjoint_tile(const AdjBlockArgs& A, const InstDe
       // lD_k = a lD'_k + c lD'_dn(k) - cb (lH_k + lH_{k-1}) + se_k lE_k
       const float ldn = POS ? (c + 1 < C ? LD[c + 1] : dn1) : (c > 0 ? LD[c - 1] : dl1);
       const float hm1 = c > 0 ? lH[c - 1] : hl1;
-      nD[c] = in ? a * LD[c] + cc * ldn - cb * (lH[c] + hm1) + se * lE[c] : 0.0f;
+      nD[c] = in(c) ? a * LD[c] + cc * ldn - cb * (lH[c] + hm1) + se * lE[c] : 0.0f;
       // lB_j = a lBt_j + c lBt_dn(j) - cb (lE_{j+1} + lE_{j+2})  (v >= 0)
       //                                 - cb (lE_j + lE_{j-1})      (v < 0)
       if (POS) {
-        const float tdn = c + 1 < C ? T[c + 1] : tn1;
+        const float tdn = c + 1 < C ? Tt[c + 1] : tn1;
         const float e1 = c + 1 < C ? lE[c + 1] : en1;
         const float e2 = c + 2 < C ? lE[c + 2] : (c + 2 == C ? en1 : en2);
-        nB[c] = in ? a * T[c] + cc * tdn - cb * (e1 + e2) : 0.0f;
+        nB[c] = in(c) ? a * Tt[c] + cc * tdn - cb * (e1 + e2) : 0.0f;
       } else {
-        const float tdn = c > 0 ? T[c - 1] : tl1;
+        const float tdn = c > 0 ? Tt[c - 1] : tl1;
         const float em1 = c > 0 ? lE[c - 1] : el1;
-        nB[c] = in ? a * T[c] + cc * tdn - cb * (lE[c] + em1) : 0.0f;
+        nB[c] = in(c) ? a * Tt[c] + cc * tdn - cb * (lE[c] + em1) : 0.0f;
       }
       // dL/deps_k = lE_k (-S D_k / eps_k^2) = lE_k (-se^2 D_k / S), output cells only
-      if (k >= x0 && k < out_hi) {
+      const bool out = out_all || (out_some && k0 + c >= T.x0 && k0 + c < T.out_hi);
+      if (UNI) {
+        if (out) T.gacc += lE[c] * Dv[c];
+      } else if (out) {
         const float gE = lE[c] * (-se * se * Dv[c] * inv_S);
-        if (ku >= 0) {
-          gu += gE;
-        } else {
-          grad_add(run, key0, gE * (1.0f - w1), sacc, kb, grad);
-          grad_add(run, key1, gE * w1, sacc, kb, grad);
-        }
+        grad_add(T.run, key0, gE * (1.0f - w1), sacc, T.kb, grad);
+        grad_add(T.run, key1, gE * w1, sacc, T.kb, grad);
       }
     }
 #pragma unroll
@@ -318,19 +280,97 @@ __device__ __forceinline__ void adjoint_tile(const AdjBlockArgs& A, const InstDe
       Dv[c] = Dnext[c];
     }
   }
+}
+
+template <bool POS>
+__device__ __forceinline__ void adjoint_tile(const AdjBlockArgs& A, const InstDev& I, int inst, int x0,
+                                             float* sacc, double* grad, int lane) {
+  constexpr int C = kAdjCells;
+  AdjTile T;
+  T.base = x0 - adj_margin(POS);
+  T.k0 = T.base + C * lane;
+  T.x0 = x0;
+  T.nz = I.nz;
+  T.out_hi = min(x0 + adj_width(POS), I.nz);          // output cells [x0, out_hi)
+  const int base = T.base, k0 = T.k0, nz = T.nz;
+  load_cells<float, float, C>(A.lBn + I.off, k0, I.nz_pad, T.LB);
+  load_cells<float, float, C>(A.lDn + I.off, k0, I.nz_pad, T.LD);
+#pragma unroll
+  for (int c = 0; c < C; ++c) {   // (padding cells past nz are not necessarily written)
+    const bool in = (unsigned)(k0 + c) < (unsigned)nz;
+    T.LB[c] = in ? T.LB[c] : 0.0f;
+    T.LD[c] = in ? T.LD[c] : 0.0f;
+  }
+  const bool lin = (I.flags & F_LINEAR) != 0;
+  const long long dq = I.dq;
+  const long long* __restrict__ zq = A.tb.zq + I.tab;
+  const float2* __restrict__ tv = A.tb.tabE32 + I.tab;
+  const int np = lin ? I.n : I.n - 1;                  // profile positions
+  const long long n_hi = A.n_seg + A.m_hi, n_lo = n_hi - A.nsteps + 1;
+
+  // a single permittivity value over the window and the launch (key ku), else ku = -1
+  T.ku = -1;
+  T.seu = 0.0f;
+  {
+    const int last = base + 32 * C - 1;
+    const long long oa = dq * (2 * n_lo - 1), ob = dq * (2 * n_hi - 1);
+    if (np == 0) {
+      T.ku = 0;
+    } else {
+      const long long zf = __ldg(zq), zl = __ldg(zq + np - 1);
+      if (last < node_of(zf, oa) && last < node_of(zf, ob)) T.ku = 0;
+      else if (base >= node_of(zl, oa) && base >= node_of(zl, ob)) T.ku = lin ? np - 1 : np;
+    }
+    if (T.ku >= 0) {
+      const float2 v = __ldg(tv + T.ku);
+      T.seu = lin ? (float)I.S / v.x : v.x;
+    }
+  }
+  T.kb = 0;
+  T.li = 0;
+  T.liH = 0;
+  if (T.ku < 0) {
+    // the smallest value the window meets in the launch: one below the count at its first cell
+    const long long xa = ((long long)base << 32) - dq * (2 * n_lo - 1);
+    const long long xb = ((long long)base << 32) - dq * (2 * n_hi - 1);
+    T.kb = max(0, positions_at_or_left(zq, np, min(xa, xb)) - 1);
+    for (int i = lane; i < kAdjKeysW; i += 32) sacc[i] = 0.0f;
+    __syncwarp();
+    T.li = positions_at_or_left(zq, np, ((long long)k0 << 32) - dq * (2 * n_hi - 1));
+  }
+  if (!(I.flags & F_MU_CONST)) T.liH = count_at_or_left(zq, np, dq * (2 * n_hi) - HALF_CELL, k0);
+  // the probe
+  T.kp = A.probe_node[inst];
+  const bool probe_in = T.kp >= 0 && T.kp < nz && T.kp >= base && T.kp < base + 32 * C;
+  T.probe_out = probe_in && T.kp >= x0 && T.kp < T.out_hi;
+  T.lp = probe_in ? (T.kp - base) / C : -1;
+  T.cp = probe_in ? (T.kp - base) % C : 0;
+  T.run = GradRun{-1, 0.0f};
+  T.gacc = 0.0f;
+
+  const bool inside = base >= 0 && base + 32 * C <= nz;
+  if (T.ku >= 0) {
+    if (inside) adjoint_steps<POS, true, true>(A, I, inst, T, sacc, grad, lane);
+    else adjoint_steps<POS, false, true>(A, I, inst, T, sacc, grad, lane);
+  } else {
+    if (inside) adjoint_steps<POS, true, false>(A, I, inst, T, sacc, grad, lane);
+    else adjoint_steps<POS, false, false>(A, I, inst, T, sacc, grad, lane);
+  }
 
   const int hi = min(x0 + adj_width(POS), I.nz_pad);
-  store_cells<float, float, C>(A.lB + I.off, k0, x0, hi, LB);
-  store_cells<float, float, C>(A.lD + I.off, k0, x0, hi, LD);
-  if (ku >= 0) {
+  store_cells<float, float, C>(A.lB + I.off, k0, x0, hi, T.LB);
+  store_cells<float, float, C>(A.lD + I.off, k0, x0, hi, T.LD);
+  if (T.ku >= 0) {
+    // dL/deps = -se^2 / S times the sum of lambdaE D over the output cells and steps
+    float g = T.gacc;
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) gu += __shfl_xor_sync(FULL, gu, o);
-    if (lane == 0 && gu != 0.0f) atomicAdd(grad + ku, (double)gu);
+    for (int o = 16; o > 0; o >>= 1) g += __shfl_xor_sync(FULL, g, o);
+    if (lane == 0 && g != 0.0f) atomicAdd(grad + T.ku, (double)g * (-(double)T.seu * T.seu / I.S));
   } else {
-    grad_flush(run, sacc, kb, grad);
+    grad_flush(T.run, sacc, T.kb, grad);
     __syncwarp();
     for (int i = lane; i < kAdjKeysW; i += 32)
-      if (sacc[i] != 0.0f) atomicAdd(grad + kb + i, (double)sacc[i]);
+      if (sacc[i] != 0.0f) atomicAdd(grad + T.kb + i, (double)sacc[i]);
     __syncwarp();
   }
 }
