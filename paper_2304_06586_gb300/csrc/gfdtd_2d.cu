@@ -65,6 +65,32 @@ struct Args2D {
   int s0, nsteps;
 };
 
+// A lane's C consecutive values to and from shared memory in 16-byte pieces
+// (C x sizeof(R) is a multiple of 16 and the row starts are 16-byte aligned).
+template <int C, typename R>
+__device__ __forceinline__ void st_run(R* p, const R (&x)[C]) {
+  constexpr int V = 16 / sizeof(R);
+#pragma unroll
+  for (int j = 0; j < C; j += V) {
+    if constexpr (V == 4) *reinterpret_cast<float4*>(p + j) = make_float4(x[j], x[j + 1], x[j + 2], x[j + 3]);
+    else *reinterpret_cast<double2*>(p + j) = make_double2(x[j], x[j + 1]);
+  }
+}
+template <int C, typename R>
+__device__ __forceinline__ void ld_run(const R* p, R (&x)[C]) {
+  constexpr int V = 16 / sizeof(R);
+#pragma unroll
+  for (int j = 0; j < C; j += V) {
+    if constexpr (V == 4) {
+      const float4 v = *reinterpret_cast<const float4*>(p + j);
+      x[j] = v.x; x[j + 1] = v.y; x[j + 2] = v.z; x[j + 3] = v.w;
+    } else {
+      const double2 v = *reinterpret_cast<const double2*>(p + j);
+      x[j] = v.x; x[j + 1] = v.y;
+    }
+  }
+}
+
 // NXMAX: the largest column count the instantiation serves (its threads per
 // block bound the registers a thread may use).
 template <int C, int TB, bool POS, typename T, int NXMAX>
@@ -86,7 +112,7 @@ __global__ void __launch_bounds__(32 * NXMAX) te2d_kernel(const Args2D<T> A) {
   const int k0 = base + lane * C;
   const long long row = (long long)col * A.stride;
 
-  R Bx[C], Bz[C], D[C], X[C];
+  R Bx[C], Bz[C], D[C], X[C], hz[C];
   load_cells<T, R, C>(A.Bx_in + row, k0, (int)A.stride, Bx);
   load_cells<T, R, C>(A.Bz_in + row, k0, (int)A.stride, Bz);
   load_cells<T, R, C>(A.D_in + row, k0, (int)A.stride, D);
@@ -114,17 +140,9 @@ __global__ void __launch_bounds__(32 * NXMAX) te2d_kernel(const Args2D<T> A) {
 
     // ---- E'^{n-1/2} = se D + cb Bsum (B_x at level n-1), into registers and shared memory
     {
-      R se[C], cbe[C];
-      if (!eps_const) {
-        lane_coefs<C, false, true>(I, A.tb, dq * (2 * n - 1) + sxE, k0, liE, se, cbe);
-      } else {
-#pragma unroll
-        for (int c = 0; c < C; ++c) se[c] = e0.x;
-      }
       const R bl1 = __shfl_up_sync(FULL, Bx[C - 1], 1), bl2 = __shfl_up_sync(FULL, Bx[C - 2], 1);
       const R br1 = __shfl_down_sync(FULL, Bx[0], 1);
-#pragma unroll
-      for (int c = 0; c < C; ++c) {
+      auto upd = [&](int c, R se, R) {
         R bs;
         if (POS) {
           const R b1 = c >= 1 ? Bx[c - 1] : bl1;
@@ -133,9 +151,15 @@ __global__ void __launch_bounds__(32 * NXMAX) te2d_kernel(const Args2D<T> A) {
         } else {
           bs = Bx[c] + (c + 1 < C ? Bx[c + 1] : br1);
         }
-        X[c] = inside(c) ? se[c] * D[c] + cb * bs : (R)0;
-        sE[col * CELLS + lane * C + c] = X[c];
+        X[c] = inside(c) ? se * D[c] + cb * bs : (R)0;
+      };
+      if (!eps_const) {
+        lane_apply<C, false, true, R>(I, A.tb, dq * (2 * n - 1) + sxE, k0, liE, upd);
+      } else {
+#pragma unroll
+        for (int c = 0; c < C; ++c) upd(c, (R)e0.x, (R)0);
       }
+      st_run<C, R>(sE + col * CELLS + lane * C, X);
     }
     __syncthreads();
 
@@ -144,7 +168,8 @@ __global__ void __launch_bounds__(32 * NXMAX) te2d_kernel(const Args2D<T> A) {
       const R er = __shfl_down_sync(FULL, X[0], 1);
       const R bxl = __shfl_up_sync(FULL, Bx[C - 1], 1), bxr = __shfl_down_sync(FULL, Bx[0], 1);
       const R bzl = __shfl_up_sync(FULL, Bz[C - 1], 1), bzr = __shfl_down_sync(FULL, Bz[0], 1);
-      const R* eR = sE + colR * CELLS + lane * C;
+      R eR[C];
+      ld_run<C, R>(sE + colR * CELLS + lane * C, eR);
       if (POS) {
 #pragma unroll
         for (int c = C - 1; c >= 0; --c) {
@@ -183,8 +208,9 @@ __global__ void __launch_bounds__(32 * NXMAX) te2d_kernel(const Args2D<T> A) {
       for (int c = 0; c < C; ++c) {
         const R d1 = c + 1 < C ? D[c + 1] : dr;
         X[c] = inside(c) ? smx[c] * Bx[c] + cb * (D[c] + d1) : (R)0;
-        sH[col * CELLS + lane * C + c] = inside(c) ? smz[c] * Bz[c] : (R)0;
+        hz[c] = inside(c) ? smz[c] * Bz[c] : (R)0;
       }
+      st_run<C, R>(sH + col * CELLS + lane * C, hz);
     }
     __syncthreads();
 
@@ -192,14 +218,14 @@ __global__ void __launch_bounds__(32 * NXMAX) te2d_kernel(const Args2D<T> A) {
     {
       const R hl = __shfl_up_sync(FULL, X[C - 1], 1);
       const R dl = __shfl_up_sync(FULL, D[C - 1], 1), dr = __shfl_down_sync(FULL, D[0], 1);
-      const R* hC = sH + col * CELLS + lane * C;
-      const R* hL = sH + colL * CELLS + lane * C;
+      R hL[C];
+      ld_run<C, R>(sH + colL * CELLS + lane * C, hL);
       if (POS) {
 #pragma unroll
         for (int c = C - 1; c >= 0; --c) {
           const R hp = c >= 1 ? X[c - 1] : hl;
           const R du = c >= 1 ? D[c - 1] : dl;
-          D[c] = a * D[c] + (cc * du + ((X[c] - hp) - rdx * (hC[c] - hL[c])));
+          D[c] = a * D[c] + (cc * du + ((X[c] - hp) - rdx * (hz[c] - hL[c])));
           if (!inside(c)) D[c] = (R)0;
         }
       } else {
@@ -207,7 +233,7 @@ __global__ void __launch_bounds__(32 * NXMAX) te2d_kernel(const Args2D<T> A) {
         for (int c = 0; c < C; ++c) {
           const R hp = c >= 1 ? X[c - 1] : hl;
           const R du = c + 1 < C ? D[c + 1] : dr;
-          D[c] = a * D[c] + (cc * du + ((X[c] - hp) - rdx * (hC[c] - hL[c])));
+          D[c] = a * D[c] + (cc * du + ((X[c] - hp) - rdx * (hz[c] - hL[c])));
           if (!inside(c)) D[c] = (R)0;
         }
       }
