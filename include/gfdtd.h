@@ -469,12 +469,13 @@ gfdtd_status gfdtd2d_set_medium(gfdtd2d_ctx* ctx, double beta, double slope, int
 /* Soft line source at z node k: after the D update of step n,
  * D_y(i, k) += amp sin(omega0 (t - t0)) exp(-((t - t0)/tau)^2) cos(kx i dx),
  * t = (n + 1/2) S (Eq. spectrum_incident with a transverse wavenumber kx:
- * waves at the angles +-asin(kx / (n omega))). */
+ * waves at the angles +-asin(kx / (n omega))).  E_ARG past 32 sources. */
 gfdtd_status gfdtd2d_add_source(gfdtd2d_ctx* ctx, int64_t k, double kx, double omega0, double tau, double t0,
                                 double amp);
 
 /* DFT probe of E_y = D_y / eps at node (i, k): every step adds
- * E_y exp(+i omega t) S to each of its n_bins bins (FP64), t = (n + 1/2) S. */
+ * E_y exp(+i omega t) S to each of its n_bins bins (FP64), t = (n + 1/2) S.
+ * E_ARG past 32 probes. */
 gfdtd_status gfdtd2d_add_probe(gfdtd2d_ctx* ctx, int i, int64_t k, int n_bins, const double* omega,
                                int* probe_id);
 

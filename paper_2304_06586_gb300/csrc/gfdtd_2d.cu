@@ -44,7 +44,8 @@ struct Args2D {
   Tables tb;
   int nx;                  // columns (= warps of a CTA)
   long long stride;        // elements between columns (nz rounded up to a multiple of 32)
-  double dx, slope;
+  double inv_dx;           // 1 / dx
+  const long long* sx;     // per column i: the slant at x_i and at x_{i+1/2}, round(x slope 2^32)
   const T* Bx_in;
   const T* Bz_in;
   const T* D_in;
@@ -54,7 +55,7 @@ struct Args2D {
   const int* tiles;        // first output cell (z) of every tile
   int n_tiles;
   const SrcDev* srcs;      // line sources: node = z node
-  const double* src_kx;    // their transverse wavenumbers
+  const double* src_cos;   // cos(kx x_i) of source q at column i: src_cos[q nx + i]
   int nsrc;
   const double* src_amp;   // [source][step in chunk]
   const int2* prb;         // probes: (column, z node)
@@ -118,10 +119,9 @@ __global__ void __launch_bounds__(32 * NXMAX) te2d_kernel(const Args2D<T> A) {
   load_cells<T, R, C>(A.D_in + row, k0, (int)A.stride, D);
 
   const R a = coef<R>(I.a, I.a32), cc = coef<R>(I.c, I.c32), cb = coef<R>(I.cb, I.cb32);
-  const R rdx = (R)(1.0 / A.dx);
+  const R rdx = (R)A.inv_dx;
   // the slant: a node at x samples the profile shifted by round(x slope 2^32)
-  const long long sxE = llround(ldexp((double)col * A.dx * A.slope, 32));
-  const long long sxZ = llround(ldexp(((double)col + 0.5) * A.dx * A.slope, 32));
+  const long long sxE = A.sx[2 * col], sxZ = A.sx[2 * col + 1];
   const bool eps_const = (I.flags & F_EPS_CONST) != 0, mu_const = (I.flags & F_MU_CONST) != 0;
   const auto e0 = __ldg(TabOf<R>::get(A.tb, true) + I.tab);
   const auto h0 = __ldg(TabOf<R>::get(A.tb, false) + I.tab);
@@ -134,6 +134,16 @@ __global__ void __launch_bounds__(32 * NXMAX) te2d_kernel(const Args2D<T> A) {
     liZ = count_at_or_left(A.tb.zq + I.tab, I.n - 1, dq * (2 * n0 + 2) + sxZ, k0);
   }
   auto inside = [&](int c) { return (unsigned)(k0 + c) < (unsigned)nz; };
+  // the line sources in the window and this column's probes in the output range (bit masks)
+  unsigned smask = 0, pmask = 0;
+  for (int q = 0; q < A.nsrc && q < 32; ++q) {
+    const int rel = A.srcs[q].node - base;
+    if (rel >= 0 && rel < CELLS) smask |= 1u << q;
+  }
+  for (int q = 0; q < A.nprb && q < 32; ++q) {
+    const int2 p = A.prb[q];
+    if (p.x == col && p.y >= x0 && p.y < x0 + W) pmask |= 1u << q;
+  }
 
   for (int s = 0; s < A.nsteps; ++s) {
     const long long n = n0 + s + 1;   // B^{n-1} -> B^n, D^{n-1/2} -> D^{n+1/2}
@@ -240,11 +250,11 @@ __global__ void __launch_bounds__(32 * NXMAX) te2d_kernel(const Args2D<T> A) {
     }
 
     // ---- line sources at t_{n+1/2}: D_{i,ks} += amp s(t) cos(kx x_i)
-    for (int q = 0; q < A.nsrc; ++q) {
+    for (unsigned m = smask; m; m &= m - 1) {
+      const int q = __ffs(m) - 1;
       const int rel = A.srcs[q].node - base;
-      if (rel >= 0 && rel < CELLS && lane == rel / C) {
-        const R amp = (R)(A.src_amp[(long long)q * A.chunk_stride + A.s0 + s] *
-                          cos(A.src_kx[q] * (double)col * A.dx));
+      if (lane == rel / C) {
+        const R amp = (R)(A.src_amp[(long long)q * A.chunk_stride + A.s0 + s] * A.src_cos[q * A.nx + col]);
         const int cs = rel % C;
 #pragma unroll
         for (int c = 0; c < C; ++c) D[c] += (c == cs) ? amp : (R)0;
@@ -252,10 +262,11 @@ __global__ void __launch_bounds__(32 * NXMAX) te2d_kernel(const Args2D<T> A) {
     }
 
     // ---- probes: E_y = D_y / eps at level n+1/2
-    for (int q = 0; q < A.nprb; ++q) {
+    for (unsigned m = pmask; m; m &= m - 1) {
+      const int q = __ffs(m) - 1;
       const int2 p = A.prb[q];
       const int rel = p.y - base;
-      if (p.x == col && p.y >= x0 && p.y < x0 + W && lane == rel / C) {
+      if (lane == rel / C) {
         R sep, cbp;
         node_coef<false, true>(I, A.tb, dq * (2 * n + 1) + sxE, p.y, sep, cbp);
         A.samples[(long long)q * A.chunk_stride + A.s0 + s] = (double)(pick(D, rel % C) * sep * (R)I.inv_S);
@@ -345,8 +356,8 @@ struct gfdtd2d_ctx {
   Buf2 f[2][3];            // [parity][Bx, Bz, D]
   int cur = 0;
   long long n_done = 0;
-  Buf2 d_ndone, d_inst, d_zq, d_tabE, d_tabH, d_tabE32, d_tabH32, d_srcs, d_kx, d_amp, d_prb, d_prbdev,
-      d_samples, d_omega, d_binprb, d_acc_re, d_acc_im, d_tiles;
+  Buf2 d_ndone, d_inst, d_zq, d_tabE, d_tabH, d_tabE32, d_tabH32, d_srcs, d_amp, d_prb, d_prbdev,
+      d_samples, d_omega, d_binprb, d_acc_re, d_acc_im, d_tiles, d_sx, d_srccos;
   int n_bins = 0;
   int C = 0, TB = 0;
   bool pos = true;
@@ -445,11 +456,21 @@ gfdtd_status finalize2(gfdtd2d_ctx* c) {
   gfdtd_status s;
   if ((s = upload2(c, c->d_inst, iv)) || (s = upload2(c, c->d_zq, zq)) || (s = upload2(c, c->d_tabE, tE)) ||
       (s = upload2(c, c->d_tabH, tH)) || (s = upload2(c, c->d_tabE32, tE32)) || (s = upload2(c, c->d_tabH32, tH32)) ||
-      (s = upload2(c, c->d_srcs, c->srcs)) || (s = upload2(c, c->d_kx, c->kx)) || (s = upload2(c, c->d_prb, prb)) ||
+      (s = upload2(c, c->d_srcs, c->srcs)) || (s = upload2(c, c->d_prb, prb)) ||
       (s = upload2(c, c->d_prbdev, pd)) || (s = upload2(c, c->d_omega, omega)) ||
       (s = upload2(c, c->d_binprb, binprb)) || (s = upload2(c, c->d_acc_re, acc_re)) ||
       (s = upload2(c, c->d_acc_im, acc_im)))
     return s;
+  // per column: the slant offsets of its nodes and half nodes, and each source's cos(kx x_i)
+  std::vector<long long> sx(2 * (size_t)c->nx);
+  for (int i = 0; i < c->nx; ++i) {
+    sx[2 * i] = llround(ldexp((double)i * c->dx * c->slope, 32));
+    sx[2 * i + 1] = llround(ldexp(((double)i + 0.5) * c->dx * c->slope, 32));
+  }
+  std::vector<double> sc(std::max<size_t>(1, c->srcs.size() * c->nx));
+  for (size_t q = 0; q < c->srcs.size(); ++q)
+    for (int i = 0; i < c->nx; ++i) sc[q * c->nx + i] = std::cos(c->kx[q] * (double)i * c->dx);
+  if ((s = upload2(c, c->d_sx, sx)) || (s = upload2(c, c->d_srccos, sc))) return s;
   if ((s = alloc2(c, c->d_amp, c->srcs.size() * kChunk2D * sizeof(double))) ||
       (s = alloc2(c, c->d_samples, c->probes.size() * kChunk2D * sizeof(double))))
     return s;
@@ -496,8 +517,8 @@ gfdtd_status step_chunk2d(gfdtd2d_ctx* c, int nsteps) {
     a.tb.tabH32 = (const float2*)c->d_tabH32.p;
     a.nx = c->nx;
     a.stride = c->stride;
-    a.dx = c->dx;
-    a.slope = c->slope;
+    a.inv_dx = 1.0 / c->dx;
+    a.sx = (const long long*)c->d_sx.p;
     a.Bx_in = (const T*)c->f[c->cur][0].p;
     a.Bz_in = (const T*)c->f[c->cur][1].p;
     a.D_in = (const T*)c->f[c->cur][2].p;
@@ -507,7 +528,7 @@ gfdtd_status step_chunk2d(gfdtd2d_ctx* c, int nsteps) {
     a.tiles = (const int*)c->d_tiles.p;
     a.n_tiles = c->n_tiles;
     a.srcs = (const SrcDev*)c->d_srcs.p;
-    a.src_kx = (const double*)c->d_kx.p;
+    a.src_cos = (const double*)c->d_srccos.p;
     a.nsrc = (int)c->srcs.size();
     a.src_amp = (const double*)c->d_amp.p;
     a.prb = (const int2*)c->d_prb.p;
@@ -615,6 +636,7 @@ gfdtd_status gfdtd2d_add_source(gfdtd2d_ctx* c, int64_t k, double kx, double ome
   if (k < 0 || k >= c->nz || !(tau > 0.0) || !std::isfinite(kx) || !std::isfinite(omega0) || !std::isfinite(t0) ||
       !std::isfinite(amp))
     return fail2(c, GFDTD_E_ARG, "bad line source");
+  if (c->srcs.size() >= 32) return fail2(c, GFDTD_E_ARG, "at most 32 line sources");
   SrcDev s{};
   s.inst = 0;
   s.node = (int)k;
@@ -632,6 +654,7 @@ gfdtd_status gfdtd2d_add_probe(gfdtd2d_ctx* c, int i, int64_t k, int n_bins, con
   if (!c) return GFDTD_E_ARG;
   if (i < 0 || i >= c->nx || k < 0 || k >= c->nz || n_bins < 1 || !omega || !probe_id)
     return fail2(c, GFDTD_E_ARG, "bad probe");
+  if (c->probes.size() >= 32) return fail2(c, GFDTD_E_ARG, "at most 32 probes");
   Probe2 p;
   p.i = i;
   p.k = k;
@@ -729,8 +752,8 @@ void gfdtd2d_destroy(gfdtd2d_ctx* c) {
   if (!c) return;
   cudaStreamSynchronize(c->stream);
   Buf2* bufs[] = {&c->d_ndone, &c->d_inst, &c->d_zq, &c->d_tabE, &c->d_tabH, &c->d_tabE32, &c->d_tabH32,
-                  &c->d_srcs, &c->d_kx, &c->d_amp, &c->d_prb, &c->d_prbdev, &c->d_samples, &c->d_omega,
-                  &c->d_binprb, &c->d_acc_re, &c->d_acc_im, &c->d_tiles};
+                  &c->d_srcs, &c->d_amp, &c->d_prb, &c->d_prbdev, &c->d_samples, &c->d_omega,
+                  &c->d_binprb, &c->d_acc_re, &c->d_acc_im, &c->d_tiles, &c->d_sx, &c->d_srccos};
   for (Buf2* b : bufs)
     if (b->p) cudaFree(b->p);
   for (auto& p : c->f)
