@@ -92,23 +92,19 @@ __device__ __forceinline__ void ld_run(const R* p, R (&x)[C]) {
   }
 }
 
-// NXMAX: the largest column count the instantiation serves (its threads per
-// block bound the registers a thread may use).
-template <int C, int TB, bool POS, typename T, int NXMAX>
-__global__ void __launch_bounds__(32 * NXMAX) te2d_kernel(const Args2D<T> A) {
+// One z-tile of every column.  EDGE: the window reaches a z end of the domain,
+// so cells outside [0, nz) are held at zero after each update.
+template <int C, int TB, bool POS, typename T, bool EDGE>
+__device__ __forceinline__ void te2d_tile(const Args2D<T>& A, const InstDev& I, int x0,
+                                          typename Real<T>::type* sE, typename Real<T>::type* sH) {
   using R = typename Real<T>::type;
   constexpr int V = 16 / sizeof(T);
   constexpr int L = tile_margin(TB, POS, V);
   constexpr int W = tile_width(C, TB, POS, V);
   constexpr int CELLS = 32 * C;
-  extern __shared__ __align__(16) unsigned char smem2d[];
-  R* sE = reinterpret_cast<R*>(smem2d);            // [column][cell] E'
-  R* sH = sE + A.nx * CELLS;                         // [column][cell] H'z
   const int col = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int colR = col + 1 == A.nx ? 0 : col + 1, colL = col == 0 ? A.nx - 1 : col - 1;
-  const InstDev I = *A.inst;
   const int nz = I.nz;
-  const int x0 = A.tiles[blockIdx.x];
   const int base = x0 - L;
   const int k0 = base + lane * C;
   const long long row = (long long)col * A.stride;
@@ -133,7 +129,7 @@ __global__ void __launch_bounds__(32 * NXMAX) te2d_kernel(const Args2D<T> A) {
     liX = count_at_or_left(A.tb.zq + I.tab, I.n - 1, dq * (2 * n0 + 2) - HALF_CELL + sxE, k0);
     liZ = count_at_or_left(A.tb.zq + I.tab, I.n - 1, dq * (2 * n0 + 2) + sxZ, k0);
   }
-  auto inside = [&](int c) { return (unsigned)(k0 + c) < (unsigned)nz; };
+  auto inside = [&](int c) { return !EDGE || (unsigned)(k0 + c) < (unsigned)nz; };
   // the line sources in the window and this column's probes in the output range (bit masks)
   unsigned smask = 0, pmask = 0;
   for (int q = 0; q < A.nsrc && q < 32; ++q) {
@@ -280,6 +276,23 @@ __global__ void __launch_bounds__(32 * NXMAX) te2d_kernel(const Args2D<T> A) {
   store_cells<T, R, C>(A.Bx_out + row, k0, x0, hi, Bx);
   store_cells<T, R, C>(A.Bz_out + row, k0, x0, hi, Bz);
   store_cells<T, R, C>(A.D_out + row, k0, x0, hi, D);
+}
+
+// NXMAX: the largest column count the instantiation serves (its threads per
+// block bound the registers a thread may use).
+template <int C, int TB, bool POS, typename T, int NXMAX>
+__global__ void __launch_bounds__(32 * NXMAX) te2d_kernel(const Args2D<T> A) {
+  using R = typename Real<T>::type;
+  constexpr int V = 16 / sizeof(T);
+  constexpr int CELLS = 32 * C;
+  extern __shared__ __align__(16) unsigned char smem2d[];
+  R* sE = reinterpret_cast<R*>(smem2d);            // [column][cell] E'
+  R* sH = sE + A.nx * CELLS;                         // [column][cell] H'z
+  const InstDev I = *A.inst;
+  const int x0 = A.tiles[blockIdx.x];
+  const int base = x0 - tile_margin(TB, POS, V);
+  if (base < 0 || base + CELLS > I.nz) te2d_tile<C, TB, POS, T, true>(A, I, x0, sE, sH);
+  else te2d_tile<C, TB, POS, T, false>(A, I, x0, sE, sH);
 }
 
 template <int C, int TB, typename T, int NXMAX>

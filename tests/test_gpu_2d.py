@@ -141,4 +141,11 @@ def test_argument_errors():
         g.set_tuning(16, 16)
     with pytest.raises(gb.GfdtdError):
         g.add_probe(4, 10, [0.1])
+    for q in range(32):                                    # at most 32 line sources and 32 probes
+        g.add_source(10 + q, 0.0, 0.3, 20.0, 60.0)
+        g.add_probe(q % 4, 20 + q, [0.3])
+    with pytest.raises(gb.GfdtdError):
+        g.add_source(60, 0.0, 0.3, 20.0, 60.0)
+    with pytest.raises(gb.GfdtdError):
+        g.add_probe(0, 60, [0.3])
     g.close()
