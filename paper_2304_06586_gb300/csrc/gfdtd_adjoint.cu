@@ -107,6 +107,31 @@ __device__ __forceinline__ void grad_add(GradRun& r, int key, float v, float* sa
   r.acc += v;
 }
 
+// Asynchronous 16-byte copy global -> shared (zero-filled when `valid` is false;
+// the source address is then not read), and the waits on its groups.
+__device__ __forceinline__ void cp_async16(void* sdst, const void* gsrc, bool valid) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(smem_u32(sdst)), "l"(gsrc),
+               "r"(valid ? 16 : 0)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
+// Wait until at most `pending` (0 .. 7) of this thread's copy groups are still in flight.
+__device__ __forceinline__ void cp_async_wait_upto(int pending) {
+  switch (pending) {
+    case 0: cp_async_wait<0>(); break;
+    case 1: cp_async_wait<1>(); break;
+    case 2: cp_async_wait<2>(); break;
+    case 3: cp_async_wait<3>(); break;
+    case 4: cp_async_wait<4>(); break;
+    case 5: cp_async_wait<5>(); break;
+    case 6: cp_async_wait<6>(); break;
+    default: cp_async_wait<7>(); break;
+  }
+}
+static_assert(kAdjBlockSteps <= 8, "cp_async_wait_upto covers up to 8 groups");
+
 // The state of one tile of the time-blocked transpose between its setup and its store.
 struct AdjTile {
   float LB[kAdjCells], LD[kAdjCells];   // lambda B, lambda D of the lane's cells
@@ -125,7 +150,7 @@ struct AdjTile {
 // sum of lambdaE D over the output cells.
 template <bool POS, bool INSIDE, bool UNI>
 __device__ __forceinline__ void adjoint_steps(const AdjBlockArgs& A, const InstDev& I, int inst, AdjTile& T,
-                                              float* sacc, double* grad, int lane) {
+                                              float* sacc, float* sD, double* grad, int lane) {
   constexpr int C = kAdjCells;
   float (&LB)[C] = T.LB;
   float (&LD)[C] = T.LD;
@@ -142,17 +167,31 @@ __device__ __forceinline__ void adjoint_steps(const AdjBlockArgs& A, const InstD
   const bool out_some = !out_all && k0 + C > T.x0 && k0 < T.out_hi;
   auto in = [&](int c) { return INSIDE || (unsigned)(k0 + c) < (unsigned)nz; };
 
-  float Dv[C];
-  load_cells<float, float, C>(A.dseg + (long long)(A.m_hi - 1) * A.dseg_stride + I.off, k0, I.nz_pad, Dv);
+  // D^{n-1/2} of every step of the launch (the forward's field after segment step m - 1),
+  // copied asynchronously into this lane's part of the warp's buffer, one group per step
+  float* myD = sD + lane * C;
+  for (int s = 0; s < A.nsteps; ++s) {
+    const float* src = A.dseg + (long long)(A.m_hi - 1 - s) * A.dseg_stride + I.off;
+#pragma unroll
+    for (int j = 0; j < C; j += 4) {
+      const int kc = k0 + j;
+      const bool ok = kc >= 0 && kc < I.nz_pad;
+      cp_async16(myD + s * 32 * C + j, src + (ok ? kc : 0), ok);
+    }
+    cp_async_commit();
+  }
   for (int s = 0; s < A.nsteps; ++s) {
     const int m = A.m_hi - s;                        // segment step transposed: n = n_seg + m
     const long long n = A.n_seg + m;
-    float Dnext[C];
-    if (s + 1 < A.nsteps) {
-      load_cells<float, float, C>(A.dseg + (long long)(m - 2) * A.dseg_stride + I.off, k0, I.nz_pad, Dnext);
-    } else {
+    float Dv[C];
+    cp_async_wait_upto(A.nsteps - 1 - s);
 #pragma unroll
-      for (int c = 0; c < C; ++c) Dnext[c] = 0.0f;
+    for (int j = 0; j < C; j += 4) {
+      const float4 v = *reinterpret_cast<const float4*>(myD + s * 32 * C + j);
+      Dv[j] = v.x;
+      Dv[j + 1] = v.y;
+      Dv[j + 2] = v.z;
+      Dv[j + 3] = v.w;
     }
 
     // probe term of step n (level n+1/2) into lD'
@@ -277,14 +316,13 @@ __device__ __forceinline__ void adjoint_steps(const AdjBlockArgs& A, const InstD
     for (int c = 0; c < C; ++c) {
       LB[c] = nB[c];
       LD[c] = nD[c];
-      Dv[c] = Dnext[c];
     }
   }
 }
 
 template <bool POS>
 __device__ __forceinline__ void adjoint_tile(const AdjBlockArgs& A, const InstDev& I, int inst, int x0,
-                                             float* sacc, double* grad, int lane) {
+                                             float* sacc, float* sD, double* grad, int lane) {
   constexpr int C = kAdjCells;
   AdjTile T;
   T.base = x0 - adj_margin(POS);
@@ -350,11 +388,11 @@ __device__ __forceinline__ void adjoint_tile(const AdjBlockArgs& A, const InstDe
 
   const bool inside = base >= 0 && base + 32 * C <= nz;
   if (T.ku >= 0) {
-    if (inside) adjoint_steps<POS, true, true>(A, I, inst, T, sacc, grad, lane);
-    else adjoint_steps<POS, false, true>(A, I, inst, T, sacc, grad, lane);
+    if (inside) adjoint_steps<POS, true, true>(A, I, inst, T, sacc, sD, grad, lane);
+    else adjoint_steps<POS, false, true>(A, I, inst, T, sacc, sD, grad, lane);
   } else {
-    if (inside) adjoint_steps<POS, true, false>(A, I, inst, T, sacc, grad, lane);
-    else adjoint_steps<POS, false, false>(A, I, inst, T, sacc, grad, lane);
+    if (inside) adjoint_steps<POS, true, false>(A, I, inst, T, sacc, sD, grad, lane);
+    else adjoint_steps<POS, false, false>(A, I, inst, T, sacc, sD, grad, lane);
   }
 
   const int hi = min(x0 + adj_width(POS), I.nz_pad);
@@ -378,6 +416,7 @@ __device__ __forceinline__ void adjoint_tile(const AdjBlockArgs& A, const InstDe
 __global__ void __launch_bounds__(128, 4) adjoint_block_kernel(const AdjBlockArgs A) {
   constexpr int WPB = 4;
   __shared__ float s_acc[WPB][kAdjKeysW];
+  __shared__ __align__(16) float s_D[WPB][kAdjBlockSteps * 32 * kAdjCells];   // D rows of the warp's tile
   const int wib = __shfl_sync(FULL, (int)(threadIdx.x >> 5), 0), lane = threadIdx.x & 31;
   const int gw = blockIdx.x * WPB + wib, nw = gridDim.x * WPB;
   // (blocks add into different copies of the gradient, so that the many warps of one
@@ -386,8 +425,8 @@ __global__ void __launch_bounds__(128, 4) adjoint_block_kernel(const AdjBlockArg
   for (int t = gw; t < A.n_tiles; t += nw) {
     const int2 tl = A.tiles[t];
     const InstDev I = A.inst[tl.x];
-    if (I.flags & F_POS) adjoint_tile<true>(A, I, tl.x, tl.y, s_acc[wib], gcopy + I.tab, lane);
-    else adjoint_tile<false>(A, I, tl.x, tl.y, s_acc[wib], gcopy + I.tab, lane);
+    if (I.flags & F_POS) adjoint_tile<true>(A, I, tl.x, tl.y, s_acc[wib], s_D[wib], gcopy + I.tab, lane);
+    else adjoint_tile<false>(A, I, tl.x, tl.y, s_acc[wib], s_D[wib], gcopy + I.tab, lane);
   }
 }
 
