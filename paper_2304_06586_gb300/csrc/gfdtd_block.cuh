@@ -240,7 +240,7 @@ __device__ __forceinline__ void lin_piece(const long long* __restrict__ zq, cons
   }
   const long long z0 = __ldg(zq + j - 1), z1 = __ldg(zq + j);
   const auto v0 = __ldg(raw + j - 1), v1 = __ldg(raw + j);
-  const R inv = (R)1 / fixed_to_real<R>(z1 - z0);
+  const R inv = quick_div((R)1, fixed_to_real<R>(z1 - z0));
   const R w = fixed_to_real<R>(xi - z0) * inv, dw = (R)4294967296.0 * inv;
   const R de = (R)v1.x - (R)v0.x, dm = (R)v1.y - (R)v0.y;
   ae = (R)v0.x + w * de; be = dw * de;
