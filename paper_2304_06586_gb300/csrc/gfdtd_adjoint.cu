@@ -413,7 +413,7 @@ __device__ __forceinline__ void adjoint_tile(const AdjBlockArgs& A, const InstDe
   }
 }
 
-__global__ void __launch_bounds__(128, 4) adjoint_block_kernel(const AdjBlockArgs A) {
+__global__ void __launch_bounds__(128, 5) adjoint_block_kernel(const AdjBlockArgs A) {
   constexpr int WPB = 4;
   __shared__ float s_acc[WPB][kAdjKeysW];
   __shared__ __align__(16) float s_D[WPB][kAdjBlockSteps * 32 * kAdjCells];   // D rows of the warp's tile
