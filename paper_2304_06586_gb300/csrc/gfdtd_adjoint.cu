@@ -107,29 +107,6 @@ __device__ __forceinline__ void grad_add(GradRun& r, int key, float v, float* sa
   r.acc += v;
 }
 
-// Asynchronous 16-byte copy global -> shared (zero-filled when `valid` is false;
-// the source address is then not read), and the waits on its groups.
-__device__ __forceinline__ void cp_async16(void* sdst, const void* gsrc, bool valid) {
-  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(smem_u32(sdst)), "l"(gsrc),
-               "r"(valid ? 16 : 0)
-               : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
-template <int N>
-__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
-// Wait until at most `pending` (0 .. 7) of this thread's copy groups are still in flight.
-__device__ __forceinline__ void cp_async_wait_upto(int pending) {
-  switch (pending) {
-    case 0: cp_async_wait<0>(); break;
-    case 1: cp_async_wait<1>(); break;
-    case 2: cp_async_wait<2>(); break;
-    case 3: cp_async_wait<3>(); break;
-    case 4: cp_async_wait<4>(); break;
-    case 5: cp_async_wait<5>(); break;
-    case 6: cp_async_wait<6>(); break;
-    default: cp_async_wait<7>(); break;
-  }
-}
 static_assert(kAdjBlockSteps <= 8, "cp_async_wait_upto covers up to 8 groups");
 
 // The state of one tile of the time-blocked transpose between its setup and its store.

@@ -726,6 +726,29 @@ __device__ __forceinline__ bool mbar_wait_bounded(unsigned long long* bar, unsig
   return false;
 }
 
+// Asynchronous 16-byte copy global -> shared (zero-filled when `valid` is false;
+// the source address is then not read), and the waits on its groups.
+__device__ __forceinline__ void cp_async16(void* sdst, const void* gsrc, bool valid) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(smem_u32(sdst)), "l"(gsrc),
+               "r"(valid ? 16 : 0)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
+// Wait until at most `pending` (0 .. 7) of this thread's copy groups are still in flight.
+__device__ __forceinline__ void cp_async_wait_upto(int pending) {
+  switch (pending) {
+    case 0: cp_async_wait<0>(); break;
+    case 1: cp_async_wait<1>(); break;
+    case 2: cp_async_wait<2>(); break;
+    case 3: cp_async_wait<3>(); break;
+    case 4: cp_async_wait<4>(); break;
+    case 5: cp_async_wait<5>(); break;
+    case 6: cp_async_wait<6>(); break;
+    default: cp_async_wait<7>(); break;
+  }
+}
 // ------------------------------------------------ fast tile (common case)
 //
 // Moving perturbation, uniform mu, layered eps whose layers are wider than a
@@ -1171,29 +1194,37 @@ __global__ void __launch_bounds__(128, general_min_blocks(C, sizeof(typename Rea
 // exact).  It appends every other tile to the queue that block_kernel then
 // takes, so the general kernel's registers and code serve only the tiles that
 // need them.  Returns whether the tile was stepped.
-template <int C, int TB, bool POS, typename T>
+// `pre`: the window's B and D (32 C elements each), already copied into shared memory;
+// `refill` is called once on every path, as soon as `pre` has been read or is not needed.
+template <int C, int TB, bool POS, typename T, typename Refill>
 __device__ __forceinline__ bool run_tile_uniform(const BlockArgs<T>& A, const InstDev& I, int x0, int W,
-                                                 long long n0) {
+                                                 long long n0, const T* pre, Refill&& refill) {
   using R = typename Real<T>::type;
   const int lane = threadIdx.x & 31;
   constexpr int L = tile_margin(TB, POS, 16 / sizeof(T));
   constexpr int SPAN = 32 * C;
   const int base = x0 - L;
-  if (base < 0 || base + SPAN > I.nz || window_absorbs(I, base, SPAN)) return false;
-  if (A.record)
+  bool take = !(base < 0 || base + SPAN > I.nz || window_absorbs(I, base, SPAN));
+  if (take && A.record)
     for (int q = 0; q < I.nprb; ++q) {
       const int node = A.prbs[I.prb0 + q].node;
-      if (node >= x0 && node < x0 + W) return false;
+      if (node >= x0 && node < x0 + W) take = false;
     }
-  if (A.n_tfsf > 0)
+  if (take && A.n_tfsf > 0)
     for (int q = 0; q < I.ntf; ++q) {
       const int node = A.tfsf[I.tf0 + q].node;
-      if (node + 1 >= base && node - 2 < base + SPAN) return false;
+      if (node + 1 >= base && node - 2 < base + SPAN) take = false;
     }
-  bool eps_const, mu_const;
-  int rE, rH;
-  uniform_sides(I, A.tb, base, SPAN, n0, A.nsteps, eps_const, mu_const, rE, rH);
-  if (!eps_const || !mu_const) return false;
+  bool eps_const = false, mu_const = false;
+  int rE = 0, rH = 0;
+  if (take) {
+    uniform_sides(I, A.tb, base, SPAN, n0, A.nsteps, eps_const, mu_const, rE, rH);
+    take = eps_const && mu_const;
+  }
+  if (!take) {
+    refill();
+    return false;
+  }
 
   const bool lin = (I.flags & F_LINEAR) != 0, matter = (I.flags & F_MATTER) != 0;
   const auto e0 = __ldg(TabOf<R>::get(A.tb, true) + I.tab + rE);
@@ -1217,8 +1248,15 @@ __device__ __forceinline__ bool run_tile_uniform(const BlockArgs<T>& A, const In
     }
 
   R B[C], D[C];
-  load_cells<T, R, C>(A.Bin + I.off, k0, I.nz_pad, B);
-  load_cells<T, R, C>(A.Din + I.off, k0, I.nz_pad, D);
+  {
+    constexpr int V = 16 / sizeof(T);
+#pragma unroll
+    for (int j = 0; j < C / V; ++j) {
+      unpack(*reinterpret_cast<const uint4*>(pre + lane * C + j * V), &B[j * V], T());
+      unpack(*reinterpret_cast<const uint4*>(pre + SPAN + lane * C + j * V), &D[j * V], T());
+    }
+  }
+  refill();
   for (int s = 0; s < A.nsteps; ++s) {
     // ---- B^n
     const R dr = __shfl_down_sync(FULL, D[0], 1);
@@ -1282,16 +1320,39 @@ __host__ __device__ constexpr int uniform_min_blocks(int C, int real_bytes) {
 template <int C, int TB, typename T>
 __global__ void __launch_bounds__(128, uniform_min_blocks(C, sizeof(typename Real<T>::type)))
     uniform_kernel(const BlockArgs<T> A) {
-  constexpr int V = 16 / sizeof(T);
+  constexpr int V = 16 / sizeof(T), SPAN = 32 * C;
+  // per warp: the window's B and D of the tile being stepped, copied asynchronously while
+  // the warp steps the tile before it (each lane copies and reads only its own cells)
+  __shared__ __align__(16) T ubuf[4][2 * SPAN];
   const int wib = __shfl_sync(FULL, (int)(threadIdx.x >> 5), 0), lane = threadIdx.x & 31;
   const int gw = blockIdx.x * 4 + wib, nw = gridDim.x * 4;
   const long long n0 = *A.n_done + A.s0;
+  T* buf = ubuf[wib];
+  auto prefetch = [&](int t) {
+    if (t >= A.n_tiles) return;
+    const int2 tl = A.tiles[t];
+    const InstDev& J = A.inst[tl.x];
+    const int base = tl.y - ((J.flags & F_POS) ? tile_margin(TB, true, V) : tile_margin(TB, false, V));
+#pragma unroll
+    for (int j = 0; j < C / V; ++j) {
+      const int kc = base + lane * C + j * V;
+      const bool ok = kc >= 0 && kc < J.nz_pad;
+      const long long e = J.off + (ok ? kc : 0);
+      cp_async16(buf + lane * C + j * V, A.Bin + e, ok);
+      cp_async16(buf + SPAN + lane * C + j * V, A.Din + e, ok);
+    }
+    cp_async_commit();
+  };
+  prefetch(gw);
   for (int t = gw; t < A.n_tiles; t += nw) {
     const int2 tl = A.tiles[t];
     const InstDev I = A.inst[tl.x];
+    cp_async_wait<0>();
+    auto refill = [&]() { prefetch(t + nw); };
     const bool done = (I.flags & F_POS)
-                          ? run_tile_uniform<C, TB, true, T>(A, I, tl.y, tile_width(C, TB, true, V), n0)
-                          : run_tile_uniform<C, TB, false, T>(A, I, tl.y, tile_width(C, TB, false, V), n0);
+                          ? run_tile_uniform<C, TB, true, T>(A, I, tl.y, tile_width(C, TB, true, V), n0, buf, refill)
+                          : run_tile_uniform<C, TB, false, T>(A, I, tl.y, tile_width(C, TB, false, V), n0, buf,
+                                                              refill);
     if (!done && lane == 0) A.queue[atomicAdd(A.qcount, 1)] = t;
   }
 }
